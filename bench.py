@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the SBP nodal sweep on one GB300 (or N replicas).
+
+Metric: vertex proposals/s per nodal sweep = N / t_sweep, where a step is
+one asynchronous-Gibbs nodal pass over all vertices (proposal, Delta DL,
+Hastings test) plus the rebuild of M, block degrees and DL from the new
+assignment.  Inputs are synthetic directed DCSBM graphs (seeded generator),
+standing in for the paper's datasets.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config dcsbm_1m] [--scale 1.0]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+replica on its own GPU (the path has no cross-GPU exchange on one box); the
+timed region is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth.dcsbm import CONFIGS, make_config, perturb  # noqa: E402
+
+METRIC = "vertex proposals/s per nodal sweep"
+UNIT = "proposals/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name: str, scale: float):
+    g = make_config(name, seed=0, scale=scale)
+    B = CONFIGS[name]["n_blocks"]
+    b0 = perturb(g.planted, B, 0.3, seed=0)
+    return g, B, b0
+
+
+def describe(name, g, B, scale):
+    c = CONFIGS[name]
+    return {
+        "workload": f"{name}: directed DCSBM N={g.n:,} E={g.m:,}, {B} planted {c['sizes']} blocks, "
+        f"degree exponent {c['gamma']} clipped [{c['kmin']},{c['kmax']}], intra:inter {c['ratio']:g}:1, "
+        f"nodal sweeps at B={B} from planted labels with 30% reassigned, FP64 Delta DL, beta=3",
+        "n": g.n,
+        "e": g.m,
+        "B": B,
+        "scale": scale,
+        "l2": "inputs larger than L2 (CSR out+in with offsets = %.0f MB > 129 MB)" % ((16 * g.m + 8 * (g.n + 1)) / 1e6),
+    }
+
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = []
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 7:
+                try:
+                    rows.append((float(p[0]), float(p[1]), p[3:7]))
+                except ValueError:
+                    pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def algorithmic_bytes(n, m, B):
+    """Per-sweep bytes the method has to move (each gather at its element
+    size): decide = offsets 8(N+1) + adjacency 8E + block gathers 8E + b read
+    and b_new write 8N; rebuild = adjacency 4E + gathers 8E (both ends) +
+    edge sources 4E + zeroing and prefix of M 12 B^2.  Blockmodel lookups
+    (L2-resident at this B) are not counted."""
+    decide = 8 * (n + 1) + 8 * m + 8 * m + 8 * n
+    rebuild = 4 * m + 8 * m + 4 * m + 12 * B * B
+    return decide, rebuild
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2305_18663_gb300 as P
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    P.load()
+    g, B, b0 = workload(args.config, args.scale)
+    stream = torch.cuda.current_stream(dev)
+    graph = P.Graph(g.n, g.src, g.dst)
+    params = P.Params.default(seed=args.seed)
+    model = P.Model(graph, B, b0, params, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    sweep_id = 0
+    for _ in range(args.warmup):
+        P.sbp_nodal_decide(model.h, sweep_id, 0, g.n)
+        P.sbp_commit(model.h, stats=False)
+        sweep_id += 1
+    P.sbp_sync(model.h)
+    torch.cuda.synchronize(dev)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        P.sbp_nodal_decide(model.h, sweep_id, 0, g.n)
+        ev[k][1].record(stream)
+        P.sbp_commit(model.h, stats=False)
+        ev[k][2].record(stream)
+        sweep_id += 1
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    P.sbp_sync(model.h)
+    total_ms = t_start.elapsed_time(t_end)
+    decide_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    commit_ms = [e[1].elapsed_time(e[2]) for e in ev]
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the C ABI with host buffers: upload b, sweep (with
+    # stats read back), download b
+    host_b = np.ascontiguousarray(model.assignment())
+    out_b = np.empty_like(host_b)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        P.sbp_set_assignment(model.h, B, host_b)
+        P.sbp_nodal_sweep(model.h, sweep_id, 0, g.n, stats=True)
+        P.sbp_get_assignment(model.h, out_b)
+        sweep_id += 1
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    st = P.sbp_nodal_sweep(model.h, sweep_id, 0, g.n, stats=True)
+
+    res = None
+    if rank == 0:
+        hbm, hbm_kind = peaks()
+        dec_b, reb_b = algorithmic_bytes(g.n, g.m, B)
+        dec_avg = statistics.mean(decide_ms)
+        achieved = dec_b / (dec_avg * 1e-3) / 1e9
+        ms_step = total_ms / args.steps
+        value = g.n * args.steps * world / (total_ms * 1e-3)
+        res = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic (seeded directed DCSBM generator; the paper's graphs are not available)",
+            "config": describe(args.config, g, B, args.scale),
+            "impl": "ours",
+            "e2e": {"value": g.n * e2e_steps * world / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * g.n, "d2h_bytes_per_step": 4 * g.n + 48},
+            "gpu_launches": 6 * args.steps,
+            "roofline": {"kernel": "nodal decide pass (k_decide_warp + k_decide_cta)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_kind": hbm_kind, "algorithmic_bytes": dec_b, "traffic": None},
+            "breakdown_ms": {"decide": dec_avg, "commit": statistics.mean(commit_ms),
+                             "decide_min": min(decide_ms), "commit_bytes": reb_b},
+            "last_sweep": st.as_dict(),
+            "clocks": ck,
+        }
+    return res
+
+
+def run_cpu_oracle(args, name, scale, steps=1, warmup=0):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    nodal decisions for a window of vertices plus the full rebuild of M,
+    scaled to proposals per second of a whole sweep."""
+    import oracle as O
+
+    g, B, b0 = workload(name, scale)
+    nt = O.max_threads()
+    G = O.Graph(g.n, g.src, g.dst)
+    t0 = time.perf_counter()
+    om = O.Model(G, B, b0)
+    t_rebuild = time.perf_counter() - t0
+    S = min(g.n, args.oracle_sample)
+    vals = []
+    for k in range(warmup + steps):
+        lo = (k * S) % g.n
+        hi = min(g.n, lo + S)
+        t0 = time.perf_counter()
+        om.nodal_decide(args.seed, k, 3.0, lo, hi, nthreads=nt)
+        dt = time.perf_counter() - t0
+        per_sweep = dt * g.n / (hi - lo) + t_rebuild
+        if k >= warmup:
+            vals.append(g.n / per_sweep)
+    return {"value": statistics.median(vals), "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"nodal decisions for {S:,} of {g.n:,} vertices per step (OpenMP, {nt} threads) "
+                      f"+ one full rebuild of M ({t_rebuild:.2f} s, single-threaded), scaled to a whole sweep"}, g, B
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="dcsbm_1m", choices=list(CONFIGS))
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--oracle-sample", type=int, default=50_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb, g, B = run_cpu_oracle(args, args.config, args.scale, steps=args.steps, warmup=args.warmup)
+        res = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * g.n / cb["value"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": describe(args.config, g, B, args.scale), "impl": "reference", "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            cb, _, _ = run_cpu_oracle(args, args.config, args.scale)
+            res["cpu_baseline"] = cb
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * sbp.h -- C ABI of libsbp, a single-GPU (sm_103a) implementation of the
+ * hot path of stochastic block partitioning (SBP) on directed graphs under
+ * the degree-corrected stochastic blockmodel (DCSBM).
+ *
+ * Method (Wanye, Gleyzer, Kao, Feng, "Exact Distributed Stochastic Block
+ * Partitioning", Section II):
+ *   - blockmodel M[r][s] = number of edges from block r to block s, with
+ *     block degrees dout_r = sum_s M[r][s] and din_s = sum_r M[r][s];
+ *   - log-likelihood L (Eq. 1) and description length DL (Eq. 2);
+ *   - MCMC phase (Alg. 2) run as an asynchronous-Gibbs pass: every vertex
+ *     proposes a block against a frozen blockmodel, the change in DL is
+ *     computed over the affected rows and columns only (Section III-A (c)),
+ *     a Hastings-corrected Metropolis test decides, then M is rebuilt from
+ *     the new assignments (Alg. 5: apply all moves, then the blockmodel is
+ *     consistent again);
+ *   - block merge phase (Alg. 1, Alg. 4): per block, x merge proposals,
+ *     keep the best Delta DL, sort, merge until C is reduced;
+ *   - golden-ratio search over the number of blocks C (Section II-B).
+ *
+ * Conventions shared by every call:
+ *   - return value: SBP_OK (0) or a negative SBP_E* code; the message of
+ *     the last failure on the calling thread is read with sbp_last_error();
+ *   - handles are opaque; the library owns every device allocation it makes
+ *     and frees it in sbp_free_model / sbp_free_graph;
+ *   - input arrays are borrowed for the duration of the call only;
+ *   - a pointer documented "host or device" may be either; the library asks
+ *     the CUDA runtime which one it is;
+ *   - device work runs on the stream given to sbp_build_blockmodel (0 = the
+ *     legacy default stream); calls that return values to the host
+ *     synchronise that stream, the others only enqueue work;
+ *   - no call is thread-safe on the same handle; different handles are
+ *     independent;
+ *   - vertex ids are int32 in [0, n); edge count m < 2^30.
+ */
+#ifndef SBP_H
+#define SBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBP_OK 0
+#define SBP_EINVAL (-1)    /* bad argument: size, range, label, pointer kind */
+#define SBP_ENOMEM (-2)    /* device or host allocation failed */
+#define SBP_EHASHFULL (-3) /* a hash table ran out of slots */
+#define SBP_EPROBE (-4)    /* a bounded probe or wait gave up */
+#define SBP_ECUDA (-5)     /* a CUDA runtime call failed */
+#define SBP_ESTATE (-6)    /* call not valid in the handle's current state */
+
+typedef struct sbp_graph sbp_graph_t;
+typedef struct sbp_model sbp_model_t;
+
+/* Run parameters.  beta: inverse temperature of the Metropolis test;
+ * merge_proposals: x of Alg. 1; reduction: share of blocks merged per merge
+ * phase before the golden-ratio bracket exists; t_pre / t_post: convergence
+ * threshold t of Alg. 2 before / after the bracket exists; max_sweeps: x of
+ * Alg. 2; dense_max_B: largest B held as a dense B x B matrix. */
+typedef struct sbp_params {
+    uint64_t seed;
+    double beta;
+    int32_t merge_proposals;
+    int32_t max_sweeps;
+    double reduction;
+    double t_pre;
+    double t_post;
+    int32_t dense_max_B;
+    int32_t reserved;
+} sbp_params;
+
+/* Counters of one nodal pass.  n_proposed: vertices with at least one edge
+ * (they draw a proposal); n_moves: proposals with s != current block;
+ * n_accepted: moves taken; n_margin: proposals whose log acceptance ratio
+ * lies within 1e-9 * max(|logA|, 1) of log(u) (decided, and reported so a
+ * comparison with another FP64 implementation can excuse them);
+ * dl_before / dl_after: DL (Eq. 2) before and after the rebuild. */
+typedef struct sbp_sweep_stats {
+    int64_t n_proposed;
+    int64_t n_moves;
+    int64_t n_accepted;
+    int64_t n_margin;
+    double dl_before;
+    double dl_after;
+} sbp_sweep_stats;
+
+/* Optional per-vertex outputs of a nodal decision pass: each member is NULL
+ * or a DEVICE pointer to n elements; entries outside [v_begin, v_end) are
+ * left untouched.  s: proposed block (current block when there was no
+ * proposal); flags: bit 0 proposed, bit 1 accepted, bit 2 margin case;
+ * dH: Delta DL of the proposed move (0 when s equals the current block);
+ * logA: log acceptance ratio -beta*dH + ln(p_bwd / p_fwd). */
+typedef struct sbp_vertex_trace {
+    int32_t *s;
+    int32_t *flags;
+    double *dH;
+    double *logA;
+} sbp_vertex_trace;
+
+/* Copies the message of the last failure on this thread (NUL-terminated,
+ * truncated to len) and returns its full length. */
+size_t sbp_last_error(char *buf, size_t len);
+
+/* Fills p with the defaults: seed 0, beta 3, 10 merge proposals, 100
+ * sweeps, reduction 0.5, t 5e-4 / 1e-4, dense_max_B 4096. */
+int sbp_default_params(sbp_params *p);
+
+/* Loads a directed graph given as COO (src[e] -> dst[e], e < m; host or
+ * device pointers) onto the current CUDA device: CSR of out-edges and CSR
+ * of in-edges, each row ascending by neighbour id, duplicates kept,
+ * self-loops kept (listed in both rows of their vertex).  The graph is the
+ * "Graph G" input of Alg. 1-2.  Errors: SBP_EINVAL for n < 1, m < 0,
+ * m >= 2^30 or an id outside [0, n); SBP_ENOMEM. */
+int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, sbp_graph_t **out);
+
+int sbp_graph_info(const sbp_graph_t *g, int64_t *n, int64_t *m);
+void sbp_free_graph(sbp_graph_t *g);
+
+/* Creates a blockmodel handle for assignment b (n labels in [0, B), host or
+ * device) and builds M, block degrees and DL (Eq. 1-2, Section II-A).
+ * stream: a cudaStream_t (may be NULL) that every later call on this model
+ * uses.  p may be NULL (defaults).  The graph must outlive the model.
+ * Errors: SBP_EINVAL for B < 1, B > n or a label outside [0, B);
+ * SBP_ENOMEM. */
+int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32_t *b, const sbp_params *p, void *stream,
+                         sbp_model_t **out);
+
+/* Replaces the assignment of an existing model (labels in [0, B), host or
+ * device) and rebuilds M and DL. Same errors as sbp_build_blockmodel. */
+int sbp_set_assignment(sbp_model_t *m, int32_t B, const int32_t *b);
+
+/* One asynchronous-Gibbs nodal pass restricted to the vertices of
+ * [v_begin, v_end) (Alg. 2 / Alg. 5 with one rank per vertex): each of them
+ * proposes a block and is accepted or rejected against the frozen (b, M);
+ * then b takes the decisions and M, the block degrees and DL are rebuilt.
+ * sweep_id keys the random draws (Philox4x64-10 counter (sweep_id, v)).
+ * stats may be NULL: the call then only enqueues work.  Errors: SBP_EINVAL
+ * for a bad range; SBP_EHASHFULL / SBP_EPROBE from the kernels' bounded
+ * tables (reported when stats are read). */
+int sbp_nodal_sweep(sbp_model_t *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, sbp_sweep_stats *stats);
+
+/* The decision half of sbp_nodal_sweep: decides [v_begin, v_end) into the
+ * model's pending assignment without changing (b, M).  Several calls on
+ * disjoint ranges followed by sbp_commit give exactly sbp_nodal_sweep over
+ * their union (the per-rank pass and exchange of Alg. 5).  trace may be
+ * NULL. */
+int sbp_nodal_decide(sbp_model_t *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
+
+/* Applies the pending assignment, rebuilds M and DL, and resets the pending
+ * assignment to the new b.  stats may be NULL (counters accumulated by the
+ * decide calls since the previous commit). */
+int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats);
+
+/* Merge proposals of Alg. 1 / Alg. 4: for every block r, x proposals s != r
+ * (x = merge_proposals), each scored by the Delta DL of merging r into s;
+ * the best (smallest score, earliest proposal on a tie at 2^-20 nats) is
+ * written to best_s[r], best_dDL[r] (B entries each, host or device).
+ * round_id keys the draws.  Requires B >= 2. */
+int sbp_merge_proposals(sbp_model_t *m, uint64_t round_id, int32_t *best_s, double *best_dDL);
+
+/* Merge phase (Alg. 1): proposals, then merges in ascending (score, r)
+ * order, each linking r's group under s's group unless they are already
+ * one, until n_merges links are made; a further proposal round (next
+ * round_id) runs when the list is exhausted first.  Blocks are relabelled
+ * densely by their smallest member and M is rebuilt.  *rounds_used (may be
+ * NULL) receives the number of round_ids consumed.  Requires
+ * 1 <= n_merges < B. */
+int sbp_merge_blocks(sbp_model_t *m, uint64_t round_id, int32_t n_merges, int32_t *B_out, int32_t *rounds_used);
+
+/* Drops labels that no vertex holds and renumbers the rest densely in
+ * ascending order; rebuilds M.  *B_out receives the new B. */
+int sbp_compact(sbp_model_t *m, int32_t *B_out);
+
+/* Full run (Fig. 1, Section II-B): start with one block per vertex,
+ * alternate merge and MCMC phases under the golden-ratio search until the
+ * bracket closes.  Writes the best assignment (n labels, host or device),
+ * its B and DL.  p may be NULL (defaults).  stream as in
+ * sbp_build_blockmodel. *n_sweeps (may be NULL) receives the number of
+ * nodal passes run. */
+int sbp_partition(const sbp_graph_t *g, const sbp_params *p, void *stream, int32_t *b_out, int32_t *B_out,
+                  double *dl_out, int64_t *n_sweeps);
+
+/* Read-back.  b_out: n labels; M_out: B*B row-major counts (dense models
+ * only, SBP_ESTATE otherwise); dout/din: B entries each.  Host or device
+ * pointers; these calls synchronise the model's stream and report any
+ * error a kernel recorded since the last check. */
+int sbp_get_assignment(const sbp_model_t *m, int32_t *b_out);
+int sbp_get_B(const sbp_model_t *m, int32_t *B_out);
+int sbp_get_dl(const sbp_model_t *m, double *dl_out);
+int sbp_get_blockmodel_dense(const sbp_model_t *m, int32_t *M_out);
+int sbp_get_degrees(const sbp_model_t *m, int32_t *dout, int32_t *din);
+int sbp_sync(const sbp_model_t *m);
+void sbp_free_model(sbp_model_t *m);
+
+/* Philox4x64-10 of the device code, for known-answer tests: writes 4*count
+ * words for counters (c0 + i, c1, c2, c3), i < count, under key (k0, k1);
+ * out is a host pointer. */
+int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1, int32_t count,
+                     uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBP_H */

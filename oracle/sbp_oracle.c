@@ -260,9 +260,13 @@ double og_model_L(const og_model *md) {
 
 /* Eq. 2: DL = E h(C^2/E) + V ln C - L, h(x) = (1+x) ln(1+x) - x ln x. */
 double og_dl(int64_t E, int64_t V, int64_t C, double L) {
-    double x = (double)C * (double)C / (double)E;
-    double h = (1.0 + x) * log1p(x) - x * log(x);
-    return (double)E * h + (double)V * log((double)C) - L;
+    /* with no edges the model term E h(C^2/E) is taken at its limit 0 */
+    double model = 0.0;
+    if (E > 0) {
+        double x = (double)C * (double)C / (double)E;
+        model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
+    }
+    return model + (double)V * log((double)C) - L;
 }
 
 double og_model_dl(const og_model *md) { return og_dl(md->g->m, md->g->n, md->B, og_model_L(md)); }

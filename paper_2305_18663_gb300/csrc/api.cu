@@ -1,0 +1,528 @@
+// api.cu -- the C ABI of libsbp: handles, passes, merge phase and driver.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sbp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SBP_ENOMEM : SBP_ECUDA;
+}
+
+int check_status(const sbp_model *m) {
+    int32_t st = 0;
+    SBP_CUDA(cudaMemcpyAsync(&st, m->status, 4, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    if (st != 0) {
+        SBP_CUDA(cudaMemsetAsync(m->status, 0, 4, m->stream));
+        return fail(st, "a kernel recorded status " + std::to_string(st) +
+                             (st == SBP_EHASHFULL ? " (neighbour table full)" : ""));
+    }
+    return SBP_OK;
+}
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_to_dev(const void *src) {
+    return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_dev(const void *dst) {
+    return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+int validate_params(const sbp_params &p) {
+    if (!std::isfinite(p.beta) || p.beta < 0) return fail(SBP_EINVAL, "params: beta must be finite and >= 0");
+    if (p.merge_proposals < 1) return fail(SBP_EINVAL, "params: merge_proposals must be >= 1");
+    if (p.max_sweeps < 1) return fail(SBP_EINVAL, "params: max_sweeps must be >= 1");
+    if (!(p.reduction > 0 && p.reduction < 1)) return fail(SBP_EINVAL, "params: reduction must be in (0, 1)");
+    if (!(p.t_pre > 0) || !(p.t_post > 0)) return fail(SBP_EINVAL, "params: thresholds must be > 0");
+    if (p.dense_max_B < 1 || p.dense_max_B > 16384) return fail(SBP_EINVAL, "params: dense_max_B must be in [1, 16384]");
+    return SBP_OK;
+}
+
+struct Stats {
+    DevCounters c;
+    double dl[2];
+    int32_t status;
+};
+
+int read_stats(sbp_model *m, sbp_sweep_stats *out) {
+    Stats *h = static_cast<Stats *>(m->pinned);
+    SBP_CUDA(cudaMemcpyAsync(&h->c, m->counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaMemcpyAsync(h->dl, m->dl, 16, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaMemcpyAsync(&h->status, m->status, 4, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    if (h->status != 0) {
+        const int st = h->status;
+        SBP_CUDA(cudaMemsetAsync(m->status, 0, 4, m->stream));
+        return fail(st, "a kernel recorded status " + std::to_string(st));
+    }
+    out->n_proposed = (int64_t)h->c.proposed;
+    out->n_moves = (int64_t)h->c.moves;
+    out->n_accepted = (int64_t)h->c.accepted;
+    out->n_margin = (int64_t)h->c.margin;
+    out->dl_after = h->dl[0];
+    out->dl_before = h->dl[1];
+    return SBP_OK;
+}
+
+int upload_assignment(sbp_model *m, int32_t B, const int32_t *b) {
+    const int64_t n = m->g->n;
+    if (B < 1 || B > n) return fail(SBP_EINVAL, "B must be in [1, n]");
+    if (!b) return fail(SBP_EINVAL, "assignment pointer is NULL");
+    // validate labels on the host copy
+    std::vector<int32_t> hb((size_t)n);
+    SBP_CUDA(cudaMemcpy(hb.data(), b, (size_t)n * 4, is_device_ptr(b) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    for (int64_t v = 0; v < n; ++v)
+        if (hb[(size_t)v] < 0 || hb[(size_t)v] >= B)
+            return fail(SBP_EINVAL, "label out of [0, B) at vertex " + std::to_string(v));
+    SBP_TRY(ensure_capacity(m, B));
+    m->B = B;
+    SBP_CUDA(cudaMemcpyAsync(m->b, hb.data(), (size_t)n * 4, cudaMemcpyHostToDevice, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    return rebuild_blockmodel(m);
+}
+
+int64_t merge_key(double d) { return (int64_t)std::floor(d * 1048576.0 + 0.5); }
+
+// Alg. 1 "sort best_merges", "pop, merge c into c'": links in ascending
+// (key, r), pointer-based union (Section III-A (d)), stops at n_merges.
+// map[c] = new dense label, groups numbered by their smallest member.
+int64_t apply_merges(int32_t B, const std::vector<int32_t> &bs, const std::vector<double> &bd, int64_t n_merges,
+                     std::vector<int32_t> &map, int32_t &B_new) {
+    std::vector<std::pair<int64_t, int32_t>> it((size_t)B);
+    for (int32_t r = 0; r < B; ++r) it[(size_t)r] = {merge_key(bd[(size_t)r]), r};
+    std::sort(it.begin(), it.end());
+    std::vector<int32_t> parent((size_t)B);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int32_t x) {
+        while (parent[(size_t)x] != x) {
+            parent[(size_t)x] = parent[(size_t)parent[(size_t)x]];
+            x = parent[(size_t)x];
+        }
+        return x;
+    };
+    int64_t done = 0;
+    for (size_t k = 0; k < it.size() && done < n_merges; ++k) {
+        const int32_t r = it[k].second, s = bs[(size_t)r];
+        if (s < 0) continue;
+        const int32_t a = find(r), c = find(s);
+        if (a == c) continue;
+        parent[(size_t)a] = c;
+        ++done;
+    }
+    std::vector<int32_t> label((size_t)B, -1);
+    map.assign((size_t)B, 0);
+    int32_t next = 0;
+    for (int32_t c = 0; c < B; ++c) {
+        const int32_t root = find(c);
+        if (label[(size_t)root] < 0) label[(size_t)root] = next++;
+        map[(size_t)c] = label[(size_t)root];
+    }
+    B_new = next;
+    return done;
+}
+
+int relabel_and_rebuild(sbp_model *m, const std::vector<int32_t> &map, int32_t B_new) {
+    SBP_CUDA(cudaMemcpyAsync(m->map, map.data(), map.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    SBP_TRY(launch_relabel(m, m->map));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    m->B = B_new;
+    return rebuild_blockmodel(m);
+}
+
+}  // namespace
+}  // namespace sbp
+
+using namespace sbp;
+
+extern "C" size_t sbp_last_error(char *buf, size_t len) {
+    const std::string &e = g_last_error;
+    if (buf && len) {
+        const size_t k = std::min(len - 1, e.size());
+        std::memcpy(buf, e.data(), k);
+        buf[k] = '\0';
+    }
+    return e.size();
+}
+
+extern "C" int sbp_default_params(sbp_params *p) {
+    if (!p) return fail(SBP_EINVAL, "sbp_default_params: NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->seed = 0;
+    p->beta = 3.0;
+    p->merge_proposals = 10;
+    p->max_sweeps = 100;
+    p->reduction = 0.5;
+    p->t_pre = 5e-4;
+    p->t_post = 1e-4;
+    p->dense_max_B = 4096;
+    return SBP_OK;
+}
+
+extern "C" void sbp_free_model(sbp_model_t *m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    cudaFree(m->b);
+    cudaFree(m->bnew);
+    cudaFree(m->M);
+    cudaFree(m->P);
+    cudaFree(m->dout);
+    cudaFree(m->din);
+    cudaFree(m->rcp);
+    cudaFree(m->dl);
+    cudaFree(m->partials);
+    cudaFree(m->counters);
+    cudaFree(m->status);
+    cudaFree(m->best_s);
+    cudaFree(m->best_d);
+    cudaFree(m->map);
+    cudaFree(m->vcount);
+    cudaFreeHost(m->pinned);
+    delete m;
+}
+
+extern "C" int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32_t *b, const sbp_params *p,
+                                    void *stream, sbp_model_t **out) {
+    if (!out) return fail(SBP_EINVAL, "sbp_build_blockmodel: out is NULL");
+    *out = nullptr;
+    if (!g) return fail(SBP_EINVAL, "sbp_build_blockmodel: graph is NULL");
+    sbp_params prm;
+    if (p) prm = *p;
+    else sbp_default_params(&prm);
+    SBP_TRY(validate_params(prm));
+    if (B < 1 || B > g->n) return fail(SBP_EINVAL, "sbp_build_blockmodel: B must be in [1, n]");
+    auto *m = new sbp_model();
+    m->g = g;
+    m->p = prm;
+    m->stream = static_cast<cudaStream_t>(stream);
+    m->npartials = 1024;
+    const size_t n = (size_t)g->n;
+    if (cudaMalloc(&m->b, n * 4) != cudaSuccess || cudaMalloc(&m->bnew, n * 4) != cudaSuccess ||
+        cudaMalloc(&m->dl, 16) != cudaSuccess || cudaMalloc(&m->partials, (size_t)m->npartials * 8) != cudaSuccess ||
+        cudaMalloc(&m->counters, sizeof(DevCounters)) != cudaSuccess || cudaMalloc(&m->status, 4) != cudaSuccess ||
+        cudaMallocHost(&m->pinned, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        sbp_free_model(m);
+        return fail(SBP_ENOMEM, "sbp_build_blockmodel: allocation failed");
+    }
+    cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream);
+    cudaMemsetAsync(m->status, 0, 4, m->stream);
+    cudaMemsetAsync(m->dl, 0, 16, m->stream);
+    const int rc = upload_assignment(m, B, b);
+    if (rc != SBP_OK) {
+        sbp_free_model(m);
+        return rc;
+    }
+    *out = m;
+    return SBP_OK;
+}
+
+extern "C" int sbp_set_assignment(sbp_model_t *m, int32_t B, const int32_t *b) {
+    if (!m) return fail(SBP_EINVAL, "sbp_set_assignment: NULL model");
+    return upload_assignment(m, B, b);
+}
+
+extern "C" int sbp_nodal_decide(sbp_model_t *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end,
+                                const sbp_vertex_trace *trace) {
+    if (!m) return fail(SBP_EINVAL, "sbp_nodal_decide: NULL model");
+    if (v_begin < 0 || v_end > m->g->n || v_begin > v_end) return fail(SBP_EINVAL, "sbp_nodal_decide: bad vertex range");
+    if (trace) {
+        const void *ps[4] = {trace->s, trace->flags, trace->dH, trace->logA};
+        for (const void *q : ps)
+            if (q && !is_device_ptr(q)) return fail(SBP_EINVAL, "sbp_nodal_decide: trace buffers must be device memory");
+    }
+    if (v_begin == v_end) return SBP_OK;
+    return launch_decide(m, sweep_id, v_begin, v_end, trace);
+}
+
+extern "C" int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats) {
+    if (!m) return fail(SBP_EINVAL, "sbp_commit: NULL model");
+    std::swap(m->b, m->bnew);
+    SBP_CUDA(cudaMemcpyAsync(m->dl + 1, m->dl, 8, cudaMemcpyDeviceToDevice, m->stream));
+    SBP_TRY(rebuild_blockmodel(m));
+    if (stats) SBP_TRY(read_stats(m, stats));
+    SBP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream));
+    return SBP_OK;
+}
+
+extern "C" int sbp_nodal_sweep(sbp_model_t *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end,
+                               sbp_sweep_stats *stats) {
+    SBP_TRY(sbp_nodal_decide(m, sweep_id, v_begin, v_end, nullptr));
+    return sbp_commit(m, stats);
+}
+
+extern "C" int sbp_merge_proposals(sbp_model_t *m, uint64_t round_id, int32_t *best_s, double *best_dDL) {
+    if (!m) return fail(SBP_EINVAL, "sbp_merge_proposals: NULL model");
+    if (m->B < 2) return fail(SBP_ESTATE, "sbp_merge_proposals: needs B >= 2");
+    SBP_TRY(launch_merge_proposals(m, round_id));
+    if (best_s) SBP_CUDA(cudaMemcpyAsync(best_s, m->best_s, (size_t)m->B * 4, kind_from_dev(best_s), m->stream));
+    if (best_dDL) SBP_CUDA(cudaMemcpyAsync(best_dDL, m->best_d, (size_t)m->B * 8, kind_from_dev(best_dDL), m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    return check_status(m);
+}
+
+extern "C" int sbp_merge_blocks(sbp_model_t *m, uint64_t round_id, int32_t n_merges, int32_t *B_out,
+                                int32_t *rounds_used) {
+    if (!m) return fail(SBP_EINVAL, "sbp_merge_blocks: NULL model");
+    if (n_merges < 1 || n_merges >= m->B) return fail(SBP_EINVAL, "sbp_merge_blocks: need 1 <= n_merges < B");
+    int32_t rounds = 0;
+    int64_t left = n_merges;
+    std::vector<int32_t> bs, map;
+    std::vector<double> bd;
+    while (left > 0 && m->B >= 2) {
+        const int32_t B = m->B;
+        SBP_TRY(launch_merge_proposals(m, round_id + (uint64_t)rounds));
+        ++rounds;
+        bs.resize((size_t)B);
+        bd.resize((size_t)B);
+        SBP_CUDA(cudaMemcpyAsync(bs.data(), m->best_s, (size_t)B * 4, cudaMemcpyDeviceToHost, m->stream));
+        SBP_CUDA(cudaMemcpyAsync(bd.data(), m->best_d, (size_t)B * 8, cudaMemcpyDeviceToHost, m->stream));
+        SBP_CUDA(cudaStreamSynchronize(m->stream));
+        int32_t Bn = B;
+        const int64_t done = apply_merges(B, bs, bd, left, map, Bn);
+        SBP_TRY(relabel_and_rebuild(m, map, Bn));
+        left -= done;
+        if (done == 0) break;
+    }
+    if (B_out) *B_out = m->B;
+    if (rounds_used) *rounds_used = rounds;
+    return check_status(m);
+}
+
+extern "C" int sbp_compact(sbp_model_t *m, int32_t *B_out) {
+    if (!m) return fail(SBP_EINVAL, "sbp_compact: NULL model");
+    const int32_t B = m->B;
+    SBP_TRY(launch_vertex_count(m));
+    std::vector<int32_t> cnt((size_t)B), map((size_t)B, -1);
+    SBP_CUDA(cudaMemcpyAsync(cnt.data(), m->vcount, (size_t)B * 4, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    int32_t next = 0;
+    for (int32_t c = 0; c < B; ++c)
+        if (cnt[(size_t)c] > 0) map[(size_t)c] = next++;
+    if (next != B) SBP_TRY(relabel_and_rebuild(m, map, next));
+    if (B_out) *B_out = m->B;
+    return SBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// golden-ratio search over the number of blocks (Section II-B)
+namespace sbp {
+namespace {
+
+struct State {
+    int32_t B = 0;
+    double dl = 0;
+    std::vector<int32_t> b;
+};
+
+struct Bracket {
+    State s[3];  // 0 hi, 1 mid, 2 lo (B == 0: empty)
+    void insert(State &&x) {
+        if (s[1].B == 0) {
+            s[1] = std::move(x);
+            return;
+        }
+        if (x.dl < s[1].dl) {
+            if (s[1].B > x.B) s[0] = std::move(s[1]);
+            else s[2] = std::move(s[1]);
+            s[1] = std::move(x);
+        } else {
+            if (x.B > s[1].B) s[0] = std::move(x);
+            else s[2] = std::move(x);
+        }
+    }
+    bool next(double reduction, int &start, int32_t &target) const {
+        if (s[2].B == 0) {
+            int64_t nm = (int64_t)std::floor((double)s[1].B * reduction);
+            if (nm > s[1].B - 1) nm = s[1].B - 1;
+            if (nm < 1) return false;
+            start = 1;
+            target = (int32_t)(s[1].B - nm);
+            return true;
+        }
+        if (s[0].B - s[2].B <= 2) return false;
+        const int32_t up = s[0].B - s[1].B, low = s[1].B - s[2].B;
+        int32_t upper, lower;
+        if (up >= low) { start = 0; upper = s[0].B; lower = s[1].B; }
+        else { start = 1; upper = s[1].B; lower = s[2].B; }
+        int32_t t = upper - (int32_t)std::llround(0.618 * (double)(upper - lower));
+        if (t >= upper) t = upper - 1;
+        if (t <= lower) t = lower + 1;
+        target = t;
+        return true;
+    }
+};
+
+int read_assignment(sbp_model *m, std::vector<int32_t> &b) {
+    b.resize((size_t)m->g->n);
+    SBP_CUDA(cudaMemcpyAsync(b.data(), m->b, b.size() * 4, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    return SBP_OK;
+}
+
+int read_dl(sbp_model *m, double &dl) {
+    SBP_CUDA(cudaMemcpyAsync(m->pinned, m->dl, 8, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    dl = *static_cast<double *>(m->pinned);
+    return SBP_OK;
+}
+
+int run_partition(sbp_model *m, int32_t *b_out, int32_t *B_out, double *dl_out, int64_t *n_sweeps) {
+    const sbp_params &p = m->p;
+    const int64_t n = m->g->n;
+    uint64_t sweep_id = 0, round_id = 0;
+    int64_t total = 0;
+    Bracket br;
+    State init;
+    init.B = m->B;
+    SBP_TRY(read_dl(m, init.dl));
+    SBP_TRY(read_assignment(m, init.b));
+    br.insert(std::move(init));
+    int start;
+    int32_t target;
+    std::vector<double> hist((size_t)p.max_sweeps + 1);
+    while (br.next(p.reduction, start, target)) {
+        const State &from = br.s[start];
+        SBP_TRY(upload_assignment(m, from.B, from.b.data()));
+        int32_t Bm = m->B, rounds = 0;
+        SBP_TRY(sbp_merge_blocks(m, round_id, from.B - target, &Bm, &rounds));
+        round_id += (uint64_t)rounds;
+        const double t = br.s[2].B == 0 ? p.t_pre : p.t_post;
+        SBP_TRY(read_dl(m, hist[0]));
+        int k;
+        for (k = 1; k <= p.max_sweeps; ++k) {
+            sbp_sweep_stats st;
+            SBP_TRY(sbp_nodal_sweep(m, sweep_id++, 0, n, &st));
+            hist[(size_t)k] = st.dl_after;
+            if (k >= 3 && std::fabs(hist[(size_t)k - 3] - hist[(size_t)k]) < t * hist[(size_t)k]) break;
+        }
+        total += k > p.max_sweeps ? p.max_sweeps : k;
+        int32_t Bc = m->B;
+        SBP_TRY(sbp_compact(m, &Bc));
+        State x;
+        x.B = m->B;
+        SBP_TRY(read_dl(m, x.dl));
+        SBP_TRY(read_assignment(m, x.b));
+        br.insert(std::move(x));
+    }
+    const State &best = br.s[1];
+    SBP_CUDA(cudaMemcpy(b_out, best.b.data(), (size_t)n * 4, is_device_ptr(b_out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    if (B_out) *B_out = best.B;
+    if (dl_out) *dl_out = best.dl;
+    if (n_sweeps) *n_sweeps = total;
+    return SBP_OK;
+}
+
+}  // namespace
+}  // namespace sbp
+
+extern "C" int sbp_partition(const sbp_graph_t *g, const sbp_params *p, void *stream, int32_t *b_out, int32_t *B_out,
+                             double *dl_out, int64_t *n_sweeps) {
+    if (!g || !b_out) return fail(SBP_EINVAL, "sbp_partition: NULL argument");
+    sbp_params prm;
+    if (p) prm = *p;
+    else sbp_default_params(&prm);
+    SBP_TRY(validate_params(prm));
+    std::vector<int32_t> ident((size_t)g->n);
+    std::iota(ident.begin(), ident.end(), 0);
+    sbp_model_t *m = nullptr;
+    SBP_TRY(sbp_build_blockmodel(g, (int32_t)g->n, ident.data(), &prm, stream, &m));
+    const int rc = run_partition(m, b_out, B_out, dl_out, n_sweeps);
+    sbp_free_model(m);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// read-back
+
+extern "C" int sbp_sync(const sbp_model_t *m) {
+    if (!m) return fail(SBP_EINVAL, "sbp_sync: NULL model");
+    return check_status(m);
+}
+
+extern "C" int sbp_get_assignment(const sbp_model_t *m, int32_t *b_out) {
+    if (!m || !b_out) return fail(SBP_EINVAL, "sbp_get_assignment: NULL argument");
+    SBP_CUDA(cudaMemcpyAsync(b_out, m->b, (size_t)m->g->n * 4, kind_from_dev(b_out), m->stream));
+    return check_status(m);
+}
+
+extern "C" int sbp_get_B(const sbp_model_t *m, int32_t *B_out) {
+    if (!m || !B_out) return fail(SBP_EINVAL, "sbp_get_B: NULL argument");
+    *B_out = m->B;
+    return SBP_OK;
+}
+
+extern "C" int sbp_get_dl(const sbp_model_t *m, double *dl_out) {
+    if (!m || !dl_out) return fail(SBP_EINVAL, "sbp_get_dl: NULL argument");
+    SBP_CUDA(cudaMemcpyAsync(dl_out, m->dl, 8, kind_from_dev(dl_out), m->stream));
+    return check_status(m);
+}
+
+extern "C" int sbp_get_blockmodel_dense(const sbp_model_t *m, int32_t *M_out) {
+    if (!m || !M_out) return fail(SBP_EINVAL, "sbp_get_blockmodel_dense: NULL argument");
+    if (!m->dense) return fail(SBP_ESTATE, "sbp_get_blockmodel_dense: model is not dense");
+    SBP_CUDA(cudaMemcpyAsync(M_out, m->M, (size_t)m->B * m->B * 4, kind_from_dev(M_out), m->stream));
+    return check_status(m);
+}
+
+extern "C" int sbp_get_degrees(const sbp_model_t *m, int32_t *dout, int32_t *din) {
+    if (!m) return fail(SBP_EINVAL, "sbp_get_degrees: NULL model");
+    if (dout) SBP_CUDA(cudaMemcpyAsync(dout, m->dout, (size_t)m->B * 4, kind_from_dev(dout), m->stream));
+    if (din) SBP_CUDA(cudaMemcpyAsync(din, m->din, (size_t)m->B * 4, kind_from_dev(din), m->stream));
+    return check_status(m);
+}
+
+// ---------------------------------------------------------------------------
+// Philox known-answer check
+namespace sbp {
+namespace {
+__global__ void k_philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1, int count,
+                         uint64_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const U64x4 w = philox4x64_10(c0 + (uint64_t)i, c1, c2, c3, k0, k1);
+    out[4 * i + 0] = w.x;
+    out[4 * i + 1] = w.y;
+    out[4 * i + 2] = w.z;
+    out[4 * i + 3] = w.w;
+}
+}  // namespace
+}  // namespace sbp
+
+extern "C" int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1,
+                                int32_t count, uint64_t *out) {
+    if (count < 1 || count > (1 << 20) || !out) return fail(SBP_EINVAL, "sbp_philox_check: bad count or NULL out");
+    uint64_t *d = nullptr;
+    SBP_CUDA(cudaMalloc(&d, (size_t)count * 32));
+    k_philox<<<(count + 255) / 256, 256>>>(c0, c1, c2, c3, k0, k1, count, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)count * 32, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "sbp_philox_check");
+    return SBP_OK;
+}

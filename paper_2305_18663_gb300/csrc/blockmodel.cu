@@ -1,0 +1,223 @@
+// blockmodel.cu -- rebuild of the blockmodel from the assignment.
+//
+// Section II-A: M[r][s] counts the edges from block r to block s; the block
+// degrees are its row and column sums.  Alg. 5: after every pass the moves
+// are applied and the blockmodel is made consistent again -- here by a full
+// recount from the new assignment, so the result is exact by construction.
+//
+// Dense form (B <= dense_max_B): M is B x B int32, counted by a
+// warp-aggregated atomic histogram over the out-edges.  P holds, per block
+// u, the inclusive prefix of row u followed by dout_u plus the inclusive
+// prefix of column u; the nodal and merge proposals search it.  DL (Eq. 2)
+// is reduced in a fixed order so it is reproducible bit for bit.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace sbp {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) k_hist_dense(GraphDev g, const int32_t *__restrict__ b,
+                                                         int32_t *__restrict__ M, int B) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.m; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        const bool valid = e < g.m;
+        int key = -1;
+        if (valid) key = b[g.esrc[e]] * B + b[g.oc[e]];
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&M[key], __popc(peers));
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += x;
+    }
+    return v;
+}
+
+// one warp per block u
+__global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__restrict__ M, int B,
+                                                           uint32_t *__restrict__ P, int32_t *__restrict__ dout,
+                                                           int32_t *__restrict__ din, double *__restrict__ rcp) {
+    const int u = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= B) return;
+    uint32_t *row = P + (size_t)u * 2 * B;
+    uint32_t carry = 0;
+    for (int c0 = 0; c0 < B; c0 += 32) {
+        const int c = c0 + lane;
+        uint32_t v = c < B ? (uint32_t)M[(size_t)u * B + c] : 0u;
+        v = warp_incl_scan(v) + carry;
+        if (c < B) row[c] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+    const uint32_t du_out = carry;
+    for (int c0 = 0; c0 < B; c0 += 32) {
+        const int c = c0 + lane;
+        uint32_t v = c < B ? (uint32_t)M[(size_t)c * B + u] : 0u;
+        v = warp_incl_scan(v) + carry;
+        if (c < B) row[B + c] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) {
+        const uint32_t du_in = carry - du_out;
+        dout[u] = (int32_t)du_out;
+        din[u] = (int32_t)du_in;
+        rcp[u] = 1.0 / ((double)du_out + (double)du_in + (double)B);
+    }
+}
+
+__device__ __forceinline__ double xlogx(int64_t x) { return x > 0 ? (double)x * log((double)x) : 0.0; }
+
+__device__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// sum over nonzero M of M ln M, minus the degree terms; one partial per block
+__global__ void __launch_bounds__(kThreads) k_dl_partial(const int32_t *__restrict__ M, int64_t BB,
+                                                         const int32_t *__restrict__ dout,
+                                                         const int32_t *__restrict__ din, int B,
+                                                         double *__restrict__ partials) {
+    __shared__ double sh[kThreads];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < BB; i += stride) acc += xlogx(M[i]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += stride)
+        acc -= xlogx(dout[i]) + xlogx(din[i]);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Eq. 2: DL = E h(B^2/E) + N ln B - L, h(x) = (1+x) ln(1+x) - x ln x
+__global__ void __launch_bounds__(kThreads) k_dl_final(const double *__restrict__ partials, int np, int64_t E,
+                                                       int64_t N, int B, double *__restrict__ dl) {
+    __shared__ double sh[kThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
+    const double L = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        double model = 0.0;
+        if (E > 0) {
+            const double x = (double)B * (double)B / (double)E;
+            model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
+        }
+        dl[0] = model + (double)N * log((double)B) - L;
+    }
+}
+
+__global__ void k_relabel(int32_t *__restrict__ b, int32_t *__restrict__ bnew, int n, const int32_t *__restrict__ map) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int x = map[b[v]];
+        b[v] = x;
+        bnew[v] = x;
+    }
+}
+
+__global__ void k_vertex_count(const int32_t *__restrict__ b, int n, int32_t *__restrict__ cnt) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) atomicAdd(&cnt[b[v]], 1);
+}
+
+int grid_for(int64_t work, int per_block, int cap) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace
+
+int ensure_capacity(sbp_model *m, int32_t B) {
+    if (B > m->p.dense_max_B)
+        return fail(SBP_ESTATE, "B = " + std::to_string(B) + " exceeds dense_max_B; only dense blockmodels are built");
+    m->dense = true;
+    if (B <= m->Bcap) return SBP_OK;
+    cudaFree(m->M);
+    cudaFree(m->P);
+    cudaFree(m->dout);
+    cudaFree(m->din);
+    cudaFree(m->rcp);
+    cudaFree(m->best_s);
+    cudaFree(m->best_d);
+    cudaFree(m->map);
+    cudaFree(m->vcount);
+    m->M = nullptr; m->P = nullptr; m->dout = m->din = nullptr; m->rcp = nullptr;
+    m->best_s = m->map = m->vcount = nullptr; m->best_d = nullptr;
+    m->Bcap = 0;
+    const size_t BB = (size_t)B * B;
+    if (cudaMalloc(&m->M, BB * 4) != cudaSuccess || cudaMalloc(&m->P, BB * 8) != cudaSuccess ||
+        cudaMalloc(&m->dout, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->din, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&m->best_d, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->map, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&m->vcount, (size_t)B * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SBP_ENOMEM, "cudaMalloc failed for a blockmodel of B = " + std::to_string(B));
+    }
+    m->Bcap = B;
+    return SBP_OK;
+}
+
+int rebuild_blockmodel(sbp_model *m) {
+    const sbp_graph *g = m->g;
+    const int B = m->B;
+    const int64_t BB = (int64_t)B * B;
+    const int sms = num_sms();
+    SBP_CUDA(cudaMemsetAsync(m->M, 0, (size_t)BB * 4, m->stream));
+    if (g->m > 0) {
+        k_hist_dense<<<grid_for(g->m, kThreads, sms * 8), kThreads, 0, m->stream>>>(g->dev(), m->b, m->M, B);
+        SBP_CUDA(cudaGetLastError());
+    }
+    k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(m->M, B, m->P, m->dout,
+                                                                                          m->din, m->rcp);
+    SBP_CUDA(cudaGetLastError());
+    const int np = grid_for(BB, kThreads * 4, m->npartials);
+    k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->partials);
+    SBP_CUDA(cudaGetLastError());
+    k_dl_final<<<1, kThreads, 0, m->stream>>>(m->partials, np, g->m, g->n, B, m->dl);
+    SBP_CUDA(cudaGetLastError());
+    SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
+    return SBP_OK;
+}
+
+int launch_relabel(sbp_model *m, const int32_t *map_dev) {
+    const int n = (int)m->g->n;
+    k_relabel<<<grid_for(n, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(m->b, m->bnew, n, map_dev);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+int launch_vertex_count(sbp_model *m) {
+    const int n = (int)m->g->n;
+    SBP_CUDA(cudaMemsetAsync(m->vcount, 0, (size_t)m->B * 4, m->stream));
+    k_vertex_count<<<grid_for(n, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(m->b, n, m->vcount);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+}  // namespace sbp

@@ -1,0 +1,207 @@
+// common.cuh -- internal types and device helpers of libsbp (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sbp.h"
+
+namespace sbp {
+
+// ---------------------------------------------------------------------------
+// error plumbing (host)
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SBP_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t _e = (call);                        \
+        if (_e != cudaSuccess) return sbp::cuda_fail(_e, #call); \
+    } while (0)
+
+#define SBP_TRY(call)                \
+    do {                             \
+        int _rc = (call);            \
+        if (_rc != SBP_OK) return _rc; \
+    } while (0)
+
+// device status word: first error code recorded by a kernel wins
+__device__ __forceinline__ void record_status(int32_t *status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// tuning constants
+constexpr int kWarp = 32;
+constexpr int kSmallDeg = 32;     // k <= 32: one neighbour per lane, no table
+constexpr int kWarpDeg = 128;     // k <= 128: one warp per vertex, per-warp table
+constexpr int kWarpCap = 256;     // per-warp table slots (>= 2 * kWarpDeg)
+constexpr int kWarpsPerCta = 8;
+constexpr int kBigThreads = 256;  // threads of the CTA-per-vertex kernel
+
+// ---------------------------------------------------------------------------
+// graph and model state
+struct GraphDev {
+    int32_t n;
+    int64_t m;
+    const int32_t *op, *ip;  // [n+1] out / in row offsets
+    const int32_t *oc, *ic;  // [m] neighbours, ascending per row
+    const int32_t *esrc;     // [m] source vertex of each out-edge (CSR order)
+};
+
+}  // namespace sbp
+
+struct sbp_graph {
+    int64_t n = 0, m = 0;
+    int device = 0;
+    int32_t *op = nullptr, *ip = nullptr, *oc = nullptr, *ic = nullptr, *esrc = nullptr;
+    int32_t *order = nullptr;  // vertices grouped: k=0 | 1..32 | 33..128 | >128
+    int64_t bin[5] = {0, 0, 0, 0, 0};
+    int32_t max_deg = 0;
+    sbp::GraphDev dev() const {
+        sbp::GraphDev d;
+        d.n = (int32_t)n; d.m = m; d.op = op; d.ip = ip; d.oc = oc; d.ic = ic; d.esrc = esrc;
+        return d;
+    }
+};
+
+namespace sbp {
+
+// device-side counters of a decision pass: proposed, moves, accepted, margin
+struct DevCounters {
+    unsigned long long proposed, moves, accepted, margin;
+};
+
+struct ModelDev {
+    int32_t B;
+    int32_t n;
+    int64_t m;
+    const int32_t *b;       // frozen assignment
+    int32_t *bnew;          // pending assignment
+    const int32_t *M;       // dense [B*B]
+    const uint32_t *P;      // [B*2B]: row prefix of M[u][.], then dout_u + column prefix of M[.][u]
+    const int32_t *dout, *din;
+    const double *rcp;      // 1 / (dout_t + din_t + B)
+    int32_t *status;
+    DevCounters *counters;
+};
+
+}  // namespace sbp
+
+struct sbp_model {
+    const sbp_graph *g = nullptr;
+    sbp_params p{};
+    cudaStream_t stream = nullptr;
+    int32_t B = 0, Bcap = 0;
+    int32_t *b = nullptr, *bnew = nullptr;
+    int32_t *M = nullptr;
+    uint32_t *P = nullptr;
+    int32_t *dout = nullptr, *din = nullptr;
+    double *rcp = nullptr;
+    double *dl = nullptr;        // [2]: current DL, DL before the last commit
+    double *partials = nullptr;  // reduction scratch
+    int32_t npartials = 0;
+    sbp::DevCounters *counters = nullptr;
+    int32_t *status = nullptr;
+    // merge scratch
+    int32_t *best_s = nullptr;
+    double *best_d = nullptr;
+    int32_t *map = nullptr;
+    int32_t *vcount = nullptr;
+    // pinned host mirror for small read-backs
+    void *pinned = nullptr;
+    bool dense = true;
+};
+
+namespace sbp {
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): two 64x64->128 products per round
+// with the published multipliers; key bumped by the published Weyl
+// constants between rounds.
+struct U64x4 {
+    uint64_t x, y, z, w;
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                                uint64_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        const uint64_t a = 0xD2E7470EE14C6C93ULL * c0, ah = __umul64hi(0xD2E7470EE14C6C93ULL, c0);
+        const uint64_t b = 0xCA5A826395121157ULL * c2, bh = __umul64hi(0xCA5A826395121157ULL, c2);
+        const uint64_t n0 = bh ^ c1 ^ k0, n2 = ah ^ c3 ^ k1;
+        c0 = n0; c1 = b; c2 = n2; c3 = a;
+    }
+    return U64x4{c0, c1, c2, c3};
+}
+
+// integer in [0, n): high word of w * n
+__device__ __forceinline__ int64_t draw_below(uint64_t w, uint64_t n) { return (int64_t)__umul64hi(w, n); }
+
+// f(x+k) - f(x) for f(x) = x ln x, as k ln(x+k) + x log1p(k/x)
+__device__ __forceinline__ double dxlogx(int64_t x, int64_t k) {
+    if (k == 0) return 0.0;
+    if (x == 0) return (double)k * log((double)k);
+    if (x + k == 0) return -(double)x * log((double)x);
+    return (double)k * log((double)(x + k)) + (double)x * log1p((double)k / (double)x);
+}
+
+// f(a+b) - f(a) - f(b) = a log1p(b/a) + b log1p(a/b)
+__device__ __forceinline__ double gmerge(int64_t a, int64_t b) {
+    if (a == 0 || b == 0) return 0.0;
+    return (double)a * log1p((double)b / (double)a) + (double)b * log1p((double)a / (double)b);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// first index i in a[0, len) with a[i] > t (a non-decreasing, a[len-1] > t),
+// warp-cooperative 32-ary search; every lane returns the answer
+__device__ __forceinline__ int warp_upper_bound(const uint32_t *__restrict__ a, int len, uint32_t t) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0;
+    while (len > 32) {
+        const int step = (len + 31) >> 5;
+        int idx = lo + (lane + 1) * step - 1;
+        const int last = lo + len - 1;
+        if (idx > last) idx = last;
+        const uint32_t val = a[idx];
+        const unsigned mask = __ballot_sync(0xffffffffu, val > t);
+        const int first = __ffs(mask) - 1;  // a[last] > t, so mask != 0
+        const int nlo = lo + first * step;
+        const int nhi = (lo + (first + 1) * step - 1 < last) ? lo + (first + 1) * step - 1 : last;
+        lo = nlo;
+        len = nhi - nlo + 1;
+    }
+    const uint32_t val = lane < len ? a[lo + lane] : 0xffffffffu;
+    const unsigned mask = __ballot_sync(0xffffffffu, val > t);
+    return lo + __ffs(mask) - 1;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers implemented in the .cu files
+int rebuild_blockmodel(sbp_model *m);  // M, P, degrees, rcp, DL from m->b
+int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
+int launch_merge_proposals(sbp_model *m, uint64_t round_id);
+int launch_relabel(sbp_model *m, const int32_t *map_dev);
+int launch_vertex_count(sbp_model *m);
+int ensure_capacity(sbp_model *m, int32_t B);
+int check_status(const sbp_model *m);
+
+}  // namespace sbp

@@ -1,0 +1,120 @@
+// merge.cu -- block-merge proposals and merge Delta DL (Alg. 1, Alg. 4).
+//
+// One warp per block r runs the x proposals of r in order.  Proposal i
+// (Philox counter (round_id, r, i), key (seed, 1)): u is the block at the
+// far end of a uniformly chosen edge of block r (row r then column r of M);
+// s != r is drawn with probability proportional to 1 + M[u][s] + M[s][u]
+// (a uniform part over the other B-1 blocks, then row u and column u with
+// block r left out).  A block with no edges draws s uniformly.
+//
+// Delta DL of merging r into s over rows and columns r, s only: row r moves
+// into row s, column r into column s, the 2x2 corner collapses into M[s][s],
+// and the block degrees of s absorb those of r.  Terms are written as
+// f(a+b) - f(a) - f(b) = a log1p(b/a) + b log1p(a/b), f(x) = x ln x.  The
+// model term of Eq. 2 is the same for every candidate and is left out.
+// The best proposal is the smallest score on a 2^-20-nat grid, earliest i
+// on a tie.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace sbp {
+ModelDev model_dev(sbp_model *m);
+
+namespace {
+
+__device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) { return md.M[(size_t)r * md.B + c]; }
+
+__device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1) {
+    const int B = md.B;
+    const uint32_t *Pr = md.P + (size_t)r * 2 * B;
+    const int64_t dr = (int64_t)md.dout[r] + md.din[r];
+    if (dr == 0) {
+        const int64_t y = draw_below(w1, (uint64_t)(B - 1));
+        return (int)(y + (y >= r));
+    }
+    const int64_t t0 = draw_below(w0, (uint64_t)dr);
+    int u = warp_upper_bound(Pr, 2 * B, (uint32_t)t0);
+    if (u >= B) u -= B;
+    const int64_t Mur = Mat(md, u, r), Mru = Mat(md, r, u);
+    const int64_t du_out = md.dout[u], du = du_out + md.din[u];
+    const int64_t W = (B - 1) + du - Mur - Mru;
+    const int64_t y = draw_below(w1, (uint64_t)W);
+    if (y < B - 1) return (int)(y + (y >= r));
+    const uint32_t *Pu = md.P + (size_t)u * 2 * B;
+    const int64_t t = y - (B - 1);
+    const int64_t row_w = du_out - Mur;
+    if (t < row_w) {
+        // row u with column r left out
+        const int64_t pre = r > 0 ? (int64_t)Pu[r - 1] : 0;
+        const int64_t tt = t >= pre ? t + Mur : t;
+        return warp_upper_bound(Pu, B, (uint32_t)tt);
+    }
+    // column u with row r left out; Pu[B + c] = dout_u + column prefix
+    const int64_t pre = r > 0 ? (int64_t)Pu[B + r - 1] : du_out;
+    int64_t target = du_out + (t - row_w);
+    if (target >= pre) target += Mru;
+    return warp_upper_bound(Pu + B, B, (uint32_t)target);
+}
+
+__device__ double merge_delta(const ModelDev &md, int r, int s) {
+    const int B = md.B, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int t = lane; t < B; t += 32) {
+        if (t == r || t == s) continue;
+        const int Mrt = Mat(md, r, t);
+        if (Mrt) acc += gmerge(Mat(md, s, t), Mrt);
+        const int Mtr = Mat(md, t, r);
+        if (Mtr) acc += gmerge(Mat(md, t, s), Mtr);
+    }
+    acc = warp_sum(acc);
+    const int64_t a = Mat(md, r, r), b = Mat(md, r, s), c = Mat(md, s, r), d = Mat(md, s, s);
+    acc += gmerge(a, b) + gmerge(a + b, c) + gmerge(a + b + c, d);
+    acc -= gmerge(md.dout[s], md.dout[r]) + gmerge(md.din[s], md.din[r]);
+    return -acc;
+}
+
+__device__ __forceinline__ long long score_key(double d) { return (long long)floor(d * 1048576.0 + 0.5); }
+
+__global__ void __launch_bounds__(256) k_merge_proposals(ModelDev md, uint64_t seed, uint64_t round_id, int x,
+                                                         int32_t *__restrict__ best_s, double *__restrict__ best_d) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < md.B; r += nw) {
+        int bs = -1;
+        double bd = 0.0;
+        long long bk = 0;
+        for (int i = 0; i < x; ++i) {
+            const U64x4 w = philox4x64_10(round_id, (uint64_t)r, (uint64_t)i, 0, seed, 1);
+            const int s = merge_propose(md, r, w.x, w.y);
+            const double d = merge_delta(md, r, s);
+            const long long key = score_key(d);
+            if (bs < 0 || key < bk) {
+                bs = s;
+                bd = d;
+                bk = key;
+            }
+        }
+        if (lane == 0) {
+            best_s[r] = bs;
+            best_d[r] = bd;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_merge_proposals(sbp_model *m, uint64_t round_id) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = ((int64_t)m->B * 32 + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_merge_proposals<<<(int)blocks, 256, 0, m->stream>>>(model_dev(m), m->p.seed, round_id, m->p.merge_proposals,
+                                                          m->best_s, m->best_d);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+}  // namespace sbp

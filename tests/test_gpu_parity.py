@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: assignments, proposals and M bit-exact; Delta DL within
+1e-9 * max(|Delta DL|, 1) (FP64 on both sides, different summation order);
+DL within 1e-12 relative.  A proposal whose log acceptance ratio lies
+within 1e-9 * max(|logA|, 1) of ln(u) is a margin case: it is not counted as
+a mismatch, and the oracle adopts the GPU's decision for it.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+import paper_2305_18663_gb300 as P  # noqa: E402
+from synth.dcsbm import dcsbm, make_config, perturb, random_labels  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+NT = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load()
+
+
+def close(a, b, tol=TOL):
+    return np.abs(a - b) <= tol * np.maximum(np.abs(b), 1.0)
+
+
+def gpu_decide(model, n, sweep_id, lo=0, hi=None):
+    dev = torch.device("cuda")
+    s = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    flags = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    dH = torch.zeros(n, dtype=torch.float64, device=dev)
+    logA = torch.zeros(n, dtype=torch.float64, device=dev)
+    P.sbp_nodal_decide(model.h, sweep_id, lo, n if hi is None else hi, s=s, flags=flags, dH=dH, logA=logA)
+    torch.cuda.synchronize()
+    return s.cpu().numpy(), flags.cpu().numpy(), dH.cpu().numpy(), logA.cpu().numpy()
+
+
+def compare_decisions(od, gd, b, idx):
+    """Compare oracle decisions od with GPU trace gd on vertices idx.
+    Returns the boolean margin mask over idx."""
+    s, flags, dH, logA = (x[idx] for x in gd)
+    assert np.array_equal(s, od.s[idx]), "proposals differ"
+    assert np.array_equal(flags & 1, od.flags[idx] & 1), "proposed flags differ"
+    moved = (s != b[idx]) & ((flags & 1) != 0)
+    assert np.all(close(dH[moved], od.dH[idx][moved])), np.max(np.abs(dH[moved] - od.dH[idx][moved]))
+    assert np.all(close(logA[moved], od.logA[idx][moved]))
+    o_margin = np.abs(od.lnu[idx] - od.logA[idx]) <= TOL * np.maximum(np.abs(od.logA[idx]), 1.0)
+    margin = moved & (o_margin | ((flags & 4) != 0))
+    agree = (flags & 2) == (od.flags[idx] & 2)
+    assert np.all(agree | margin), "accept decisions differ outside the margin band"
+    return margin
+
+
+def check_blockmodel(pm, om):
+    assert pm.B == om.B
+    assert np.array_equal(pm.dense().astype(np.int64), om.dense())
+    dout, din = pm.degrees()
+    odout, odin = om.degrees()
+    assert np.array_equal(dout, odout) and np.array_equal(din, odin)
+    assert pm.dl() == pytest.approx(om.dl(), rel=1e-12)
+
+
+def run_sweeps(g, B, b, sweeps, seed=7, first_sweep=0):
+    G = O.Graph(g.n, g.src, g.dst)
+    om = O.Model(G, B, b)
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, B, b, P.Params.default(seed=seed))
+    check_blockmodel(pm, om)
+    total_margin = 0
+    for sw in range(first_sweep, first_sweep + sweeps):
+        bcur = om.assignment()
+        gd = gpu_decide(pm, g.n, sw)
+        od = om.nodal_decide(seed, sw, 3.0, nthreads=NT)
+        margin = compare_decisions(od, gd, bcur, np.arange(g.n))
+        total_margin += int(margin.sum())
+        st = P.sbp_commit(pm.h)
+        bg = pm.assignment()
+        want = od.b_new.copy()
+        want[margin] = bg[margin]
+        assert np.array_equal(bg, want)
+        assert st.n_accepted == int(((gd[1] & 2) != 0).sum())
+        assert st.n_proposed == int(((gd[1] & 1) != 0).sum())
+        om.set_b(B, bg)
+        check_blockmodel(pm, om)
+    return pm, om, total_margin
+
+
+# ---------------------------------------------------------------------------
+
+def test_philox_device_matches_oracle():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        ctr = rng.integers(0, 2**62, 4, dtype=np.uint64)
+        key = rng.integers(0, 2**62, 2, dtype=np.uint64)
+        got = P.sbp_philox_check(ctr, key, 64)
+        for i in range(64):
+            c = ctr.copy()
+            c[0] = np.uint64(int(c[0]) + i)
+            assert np.array_equal(got[i], O.philox4x64(c, key))
+
+
+@pytest.mark.parametrize("B", [1, 8, 64, 1000])
+def test_blockmodel_rebuild_matches_oracle(B):
+    g = make_config("plain_1k")
+    b = random_labels(g.n, B, seed=B) if B < g.n else np.arange(g.n, dtype=np.int32)
+    G = O.Graph(g.n, g.src, g.dst)
+    om = O.Model(G, B, b)
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, B, b)
+    check_blockmodel(pm, om)
+    assert pm.dense().sum() == g.m
+
+
+@pytest.mark.parametrize("B", [8, 64])
+def test_nodal_sweeps_plain_1k(B):
+    g = make_config("plain_1k")
+    run_sweeps(g, B, random_labels(g.n, B, seed=B), sweeps=10)
+
+
+def test_nodal_sweeps_self_loops_duplicates_isolated():
+    rng = np.random.default_rng(11)
+    n = 300
+    src = rng.integers(0, n - 20, 3000).astype(np.int32)  # last 20 vertices isolated
+    dst = rng.integers(0, n - 20, 3000).astype(np.int32)
+    src[:200] = dst[:200]  # self-loops
+    src[200:400] = src[400:600]  # duplicates
+    dst[200:400] = dst[400:600]
+    hub = 5  # one high-degree vertex (CTA path) with self-loops
+    src = np.concatenate([src, np.full(400, hub, np.int32), np.full(3, hub, np.int32)])
+    dst = np.concatenate([dst, rng.integers(0, n - 20, 400).astype(np.int32), np.full(3, hub, np.int32)])
+
+    class Gr:
+        pass
+
+    g = Gr()
+    g.n, g.src, g.dst, g.m = n, src, dst, src.size
+    run_sweeps(g, 12, random_labels(n, 12, seed=1), sweeps=8)
+
+
+def test_nodal_sweeps_scaled_dcsbm():
+    # 50k vertices, 1M edges, 316 planted blocks, 30% reassigned: spans
+    # every degree group (one lane per edge, warp, CTA) and ragged tails
+    g = make_config("dcsbm_1m", scale=0.05)
+    b = perturb(g.planted, 316, 0.3, seed=0)
+    _, _, margin = run_sweeps(g, 316, b, sweeps=2)
+    assert margin <= 5
+
+
+def test_shards_then_commit_equal_one_sweep():
+    g = make_config("plain_1k")
+    b = random_labels(g.n, 16, seed=4)
+    pg = P.Graph(g.n, g.src, g.dst)
+    full = P.Model(pg, 16, b)
+    full.sweep(3)
+    shard = P.Model(pg, 16, b)
+    for lo, hi in [(0, 100), (100, 777), (777, g.n)]:
+        P.sbp_nodal_decide(shard.h, 3, lo, hi)
+    P.sbp_commit(shard.h)
+    assert np.array_equal(full.assignment(), shard.assignment())
+    assert np.array_equal(full.dense(), shard.dense())
+
+
+def test_single_block_and_no_edges():
+    g = make_config("plain_1k")
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, 1, np.zeros(g.n, np.int32))
+    st = pm.sweep(0)
+    assert st.n_accepted == 0 and st.n_moves == 0 and st.n_proposed == g.n
+    G = O.Graph(g.n, g.src, g.dst)
+    assert pm.dl() == pytest.approx(O.Model(G, 1, np.zeros(g.n, np.int32)).dl(), rel=1e-13)
+    e = np.zeros(0, np.int32)
+    pg0 = P.Graph(5, e, e)
+    pm0 = P.Model(pg0, 3, np.array([0, 1, 2, 0, 1], np.int32))
+    st = pm0.sweep(0)
+    assert st.n_proposed == 0 and st.n_accepted == 0
+    assert pm0.dl() == pytest.approx(O.Model(O.Graph(5, e, e), 3, np.array([0, 1, 2, 0, 1], np.int32)).dl(), rel=1e-14)
+
+
+def test_bad_arguments_raise():
+    g = make_config("plain_1k")
+    pg = P.Graph(g.n, g.src, g.dst)
+    with pytest.raises(P.SbpError) as e:
+        P.Model(pg, 4, np.full(g.n, 4, np.int32))
+    assert e.value.code == -1
+    pm = P.Model(pg, 4, np.zeros(g.n, np.int32))
+    with pytest.raises(P.SbpError):
+        P.sbp_nodal_sweep(pm.h, 0, 10, 5)
+    with pytest.raises(P.SbpError):
+        P.sbp_merge_blocks(pm.h, 0, 4)
+    with pytest.raises(P.SbpError):
+        P.Graph(3, np.array([0, 3], np.int32), np.array([1, 2], np.int32))
+
+
+def test_device_pointers_accepted():
+    g = make_config("plain_1k")
+    src = torch.from_numpy(g.src).cuda()
+    dst = torch.from_numpy(g.dst).cuda()
+    pg = P.Graph(g.n, src, dst)
+    b = random_labels(g.n, 8, seed=2)
+    pm = P.Model(pg, 8, torch.from_numpy(b).cuda())
+    out = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    P.sbp_get_assignment(pm.h, out)
+    assert np.array_equal(out.cpu().numpy(), b)
+    G = O.Graph(g.n, g.src, g.dst)
+    check_blockmodel(pm, O.Model(G, 8, b))
+
+
+# ---------------------------------------------------------------------------
+# merge phase
+
+@pytest.mark.parametrize("B", [40, 1000])
+def test_merge_proposals_match_oracle(B):
+    g = make_config("plain_1k")
+    b = random_labels(g.n, B, seed=5) if B < g.n else np.arange(g.n, dtype=np.int32)
+    G = O.Graph(g.n, g.src, g.dst)
+    om = O.Model(G, B, b)
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, B, b, P.Params.default(seed=9))
+    bs = np.zeros(B, np.int32)
+    bd = np.zeros(B, np.float64)
+    P.sbp_merge_proposals(pm.h, 4, bs, bd)
+    obs, obd = om.merge_proposals(9, 4, 10, nthreads=NT)
+    assert np.all(close(bd, obd))
+    diff = np.flatnonzero(bs != obs)
+    for r in diff:  # only ties on the score grid may differ, and both must be proposals
+        props = [om.merge_propose(9, 4, int(r), i) for i in range(10)]
+        assert bs[r] in props
+        assert O.merge_key(om.merge_delta(int(r), int(bs[r]))) == O.merge_key(obd[r])
+    assert diff.size <= max(2, B // 200)
+
+
+def test_merge_blocks_matches_oracle_application():
+    g = make_config("plain_1k")
+    B = 200
+    b = random_labels(g.n, B, seed=6)
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, B, b, P.Params.default(seed=2))
+    bs = np.zeros(B, np.int32)
+    bd = np.zeros(B, np.float64)
+    P.sbp_merge_proposals(pm.h, 8, bs, bd)
+    n_merges = 60
+    done, mp, Bn = O.merge_apply(B, bs, bd, n_merges)
+    assert done == n_merges
+    Bg, rounds = P.sbp_merge_blocks(pm.h, 8, n_merges)
+    assert rounds == 1 and Bg == Bn == B - n_merges
+    assert np.array_equal(pm.assignment(), mp[b])
+    G = O.Graph(g.n, g.src, g.dst)
+    check_blockmodel(pm, O.Model(G, Bn, mp[b]))
+
+
+def test_compact_drops_empty_blocks():
+    g = make_config("plain_1k")
+    b = (random_labels(g.n, 10, seed=1) * 3).astype(np.int32)  # labels 0,3,...,27 of 30
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, 30, b)
+    assert P.sbp_compact(pm.h) == 10
+    Bo, bo = O.compact(30, b)
+    assert Bo == 10 and np.array_equal(pm.assignment(), bo)
+
+
+def test_partition_plain_1k_matches_oracle():
+    g = make_config("plain_1k")
+    G = O.Graph(g.n, g.src, g.dst)
+    ob, oB, odl, ons = O.partition(G, O.Params(), nthreads=NT)
+    pg = P.Graph(g.n, g.src, g.dst)
+    b, B, dl, ns = pg.partition(P.Params.default())
+    assert B == oB == 8
+    assert dl == pytest.approx(odl, rel=1e-12)
+    assert np.array_equal(b, ob)
+    assert ns == ons

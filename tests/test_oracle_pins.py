@@ -488,3 +488,18 @@ def test_partition_recovers_planted_blocks():
     assert len(pairs) == 8
     b2, B2, dl2, _ = O.partition(G, O.Params())
     assert np.array_equal(b, b2) and dl == dl2
+
+
+def test_dl_without_edges_is_the_limit():
+    # E h(C^2/E) -> 0 as E -> 0 (h(x) ~ ln x + 1 for large x), so Eq. 2
+    # reduces to V ln C when the graph has no edges.
+    g = O.Graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    m = O.Model(g, 3, np.array([0, 1, 2, 0, 1], np.int32))
+    assert m.dl() == pytest.approx(5 * math.log(3), rel=1e-15)
+    prev = None
+    for E in (1e-2, 1e-4, 1e-6, 1e-8):
+        x = 9 / E
+        term = E * ((1 + x) * math.log1p(x) - x * math.log(x))
+        assert prev is None or term < prev
+        prev = term
+    assert prev < 1e-6
