@@ -223,7 +223,7 @@ extern "C" int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32
     m->npartials = 1024;
     const size_t n = (size_t)g->n;
     if (cudaMalloc(&m->b, n * 4) != cudaSuccess || cudaMalloc(&m->bnew, n * 4) != cudaSuccess ||
-        cudaMalloc(&m->dl, 16) != cudaSuccess || cudaMalloc(&m->partials, (size_t)m->npartials * 8) != cudaSuccess ||
+        cudaMalloc(&m->dl, 16) != cudaSuccess || cudaMalloc(&m->partials, (size_t)m->npartials * 32) != cudaSuccess ||
         cudaMalloc(&m->counters, sizeof(DevCounters)) != cudaSuccess || cudaMalloc(&m->status, 4) != cudaSuccess ||
         cudaMallocHost(&m->pinned, 4096) != cudaSuccess) {
         cudaGetLastError();

@@ -46,7 +46,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 // one warp per block u
 __global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__restrict__ M, int B,
                                                            uint32_t *__restrict__ P, int32_t *__restrict__ dout,
-                                                           int32_t *__restrict__ din, double *__restrict__ rcp) {
+                                                           int32_t *__restrict__ din, double *__restrict__ rcp,
+                                                           float *__restrict__ rcp32, int32_t *__restrict__ dsum) {
     const int u = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (u >= B) return;
@@ -72,53 +73,78 @@ __global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__rest
         dout[u] = (int32_t)du_out;
         din[u] = (int32_t)du_in;
         rcp[u] = 1.0 / ((double)du_out + (double)du_in + (double)B);
+        rcp32[u] = 1.0f / ((float)du_out + (float)du_in + (float)B);
+        dsum[u] = (int32_t)(du_out + du_in);
     }
 }
 
-__device__ __forceinline__ double xlogx(int64_t x) { return x > 0 ? (double)x * log((double)x) : 0.0; }
+struct DlPartial {
+    __int128 fix;  // sum of x ln x * 2^64 over counts inside the table
+    double fb;     // FP64 sum over counts beyond it
+    double pad;
+};
 
-__device__ double block_sum(double v, double *sh) {
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    const double r = sh[0];
-    __syncthreads();
-    return r;
+__device__ __forceinline__ void add_xlogx(const __int128 *__restrict__ T, int64_t XT, int64_t x, int sign, __int128 &fix,
+                                          double &fb) {
+    if (x < 2) return;
+    if (x < XT) fix += sign > 0 ? T[x] : -T[x];
+    else fb += sign * ((double)x * log((double)x));
 }
 
-// sum over nonzero M of M ln M, minus the degree terms; one partial per block
+// Eq. 1 split form: sum over M of x ln x minus the degree terms, one
+// partial per block, exact in fixed point inside the table
 __global__ void __launch_bounds__(kThreads) k_dl_partial(const int32_t *__restrict__ M, int64_t BB,
                                                          const int32_t *__restrict__ dout,
                                                          const int32_t *__restrict__ din, int B,
-                                                         double *__restrict__ partials) {
-    __shared__ double sh[kThreads];
-    double acc = 0.0;
+                                                         const __int128 *__restrict__ T, int64_t XT,
+                                                         DlPartial *__restrict__ partials) {
+    __shared__ __int128 sfix[kThreads / 32];
+    __shared__ double sfb[kThreads / 32];
+    __int128 fix = 0;
+    double fb = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < BB; i += stride) acc += xlogx(M[i]);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += stride)
-        acc -= xlogx(dout[i]) + xlogx(din[i]);
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < BB; i += stride) add_xlogx(T, XT, M[i], 1, fix, fb);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += stride) {
+        add_xlogx(T, XT, dout[i], -1, fix, fb);
+        add_xlogx(T, XT, din[i], -1, fix, fb);
+    }
+    fix = warp_sum_128(fix);
+    fb = warp_sum(fb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sfix[wid] = fix;
+        sfb[wid] = fb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __int128 f = 0;
+        double d = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) {
+            f += sfix[q];
+            d += sfb[q];
+        }
+        partials[blockIdx.x].fix = f;
+        partials[blockIdx.x].fb = d;
+    }
 }
 
 // Eq. 2: DL = E h(B^2/E) + N ln B - L, h(x) = (1+x) ln(1+x) - x ln x
-__global__ void __launch_bounds__(kThreads) k_dl_final(const double *__restrict__ partials, int np, int64_t E,
-                                                       int64_t N, int B, double *__restrict__ dl) {
-    __shared__ double sh[kThreads];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
-    const double L = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-        double model = 0.0;
-        if (E > 0) {
-            const double x = (double)B * (double)B / (double)E;
-            model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
-        }
-        dl[0] = model + (double)N * log((double)B) - L;
+__global__ void k_dl_final(const DlPartial *__restrict__ partials, int np, int64_t E, int64_t N, int B,
+                           double *__restrict__ dl) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __int128 f = 0;
+    double d = 0.0;
+    for (int i = 0; i < np; ++i) {
+        f += partials[i].fix;
+        d += partials[i].fb;
     }
+    const double L = fix_to_double(f) + d;
+    double model = 0.0;
+    if (E > 0) {
+        const double x = (double)B * (double)B / (double)E;
+        model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
+    }
+    dl[0] = model + (double)N * log((double)B) - L;
 }
 
 __global__ void k_relabel(int32_t *__restrict__ b, int32_t *__restrict__ bnew, int n, const int32_t *__restrict__ map) {
@@ -163,17 +189,20 @@ int ensure_capacity(sbp_model *m, int32_t B) {
     cudaFree(m->dout);
     cudaFree(m->din);
     cudaFree(m->rcp);
+    cudaFree(m->rcp32);
+    cudaFree(m->dsum);
     cudaFree(m->best_s);
     cudaFree(m->best_d);
     cudaFree(m->map);
     cudaFree(m->vcount);
-    m->M = nullptr; m->P = nullptr; m->dout = m->din = nullptr; m->rcp = nullptr;
+    m->M = nullptr; m->P = nullptr; m->dout = m->din = nullptr; m->rcp = nullptr; m->rcp32 = nullptr; m->dsum = nullptr;
     m->best_s = m->map = m->vcount = nullptr; m->best_d = nullptr;
     m->Bcap = 0;
     const size_t BB = (size_t)B * B;
     if (cudaMalloc(&m->M, BB * 4) != cudaSuccess || cudaMalloc(&m->P, BB * 8) != cudaSuccess ||
         cudaMalloc(&m->dout, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->din, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->rcp32, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&m->dsum, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
         cudaMalloc(&m->best_d, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->map, (size_t)B * 4) != cudaSuccess ||
         cudaMalloc(&m->vcount, (size_t)B * 4) != cudaSuccess) {
         cudaGetLastError();
@@ -188,18 +217,20 @@ int rebuild_blockmodel(sbp_model *m) {
     const int B = m->B;
     const int64_t BB = (int64_t)B * B;
     const int sms = num_sms();
+    SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
     SBP_CUDA(cudaMemsetAsync(m->M, 0, (size_t)BB * 4, m->stream));
     if (g->m > 0) {
         k_hist_dense<<<grid_for(g->m, kThreads, sms * 8), kThreads, 0, m->stream>>>(g->dev(), m->b, m->M, B);
         SBP_CUDA(cudaGetLastError());
     }
     k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(m->M, B, m->P, m->dout,
-                                                                                          m->din, m->rcp);
+                                                                                          m->din, m->rcp, m->rcp32, m->dsum);
     SBP_CUDA(cudaGetLastError());
     const int np = grid_for(BB, kThreads * 4, m->npartials);
-    k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->partials);
+    DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
+    k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->T, m->XT, parts);
     SBP_CUDA(cudaGetLastError());
-    k_dl_final<<<1, kThreads, 0, m->stream>>>(m->partials, np, g->m, g->n, B, m->dl);
+    k_dl_final<<<1, 32, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
     SBP_CUDA(cudaGetLastError());
     SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
     return SBP_OK;

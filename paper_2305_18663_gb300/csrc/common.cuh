@@ -41,6 +41,7 @@ constexpr int kWarpDeg = 128;     // k <= 128: one warp per vertex, per-warp tab
 constexpr int kWarpCap = 256;     // per-warp table slots (>= 2 * kWarpDeg)
 constexpr int kWarpsPerCta = 8;
 constexpr int kBigThreads = 256;  // threads of the CTA-per-vertex kernel
+constexpr int64_t kMaxTable = int64_t(1) << 22;  // largest x ln x table (entries)
 
 // ---------------------------------------------------------------------------
 // graph and model state
@@ -85,6 +86,10 @@ struct ModelDev {
     const uint32_t *P;      // [B*2B]: row prefix of M[u][.], then dout_u + column prefix of M[.][u]
     const int32_t *dout, *din;
     const double *rcp;      // 1 / (dout_t + din_t + B)
+    const float *rcp32;     // the same in FP32
+    const int32_t *dsum;    // dout_t + din_t
+    const __int128 *T;      // round(x ln x * 2^64), x < XT
+    int64_t XT;
     int32_t *status;
     DevCounters *counters;
 };
@@ -101,6 +106,10 @@ struct sbp_model {
     uint32_t *P = nullptr;
     int32_t *dout = nullptr, *din = nullptr;
     double *rcp = nullptr;
+    float *rcp32 = nullptr;
+    int32_t *dsum = nullptr;
+    const __int128 *T = nullptr;
+    int64_t XT = 0;
     double *dl = nullptr;        // [2]: current DL, DL before the last commit
     double *partials = nullptr;  // reduction scratch
     int32_t npartials = 0;
@@ -153,6 +162,44 @@ __device__ __forceinline__ double dxlogx(int64_t x, int64_t k) {
     return (double)k * log((double)(x + k)) + (double)x * log1p((double)k / (double)x);
 }
 
+// f(x+k) - f(x) from the fixed-point table when both counts are inside it;
+// otherwise the FP64 formula above is added to fb and 0 returned
+__device__ __forceinline__ __int128 dT(const __int128 *__restrict__ T, int64_t XT, int64_t x, int64_t k, double &fb) {
+    if (k == 0) return 0;
+    const int64_t y = x + k;
+    if (x < XT && y < XT) return T[y] - T[x];
+    fb += dxlogx(x, k);
+    return 0;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_128(__int128 v, int o) {
+    const unsigned long long lo = (unsigned long long)v;
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi2 << 64) | lo2);
+}
+
+__device__ __forceinline__ __int128 warp_sum_128(__int128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor_128(v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// fixed point (scale 2^64) to float / double
+__device__ __forceinline__ float fix_to_float(__int128 v) { return (float)(long long)(v >> 40) * 0x1p-24f; }
+__device__ __forceinline__ double fix_to_double(__int128 v) {
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return (double)hi + (double)lo * 0x1p-64;
+}
+
 // f(a+b) - f(a) - f(b) = a log1p(b/a) + b log1p(a/b)
 __device__ __forceinline__ double gmerge(int64_t a, int64_t b) {
     if (a == 0 || b == 0) return 0.0;
@@ -203,5 +250,6 @@ int launch_relabel(sbp_model *m, const int32_t *map_dev);
 int launch_vertex_count(sbp_model *m);
 int ensure_capacity(sbp_model *m, int32_t B);
 int check_status(const sbp_model *m);
+int xlogx_table(int64_t need, const __int128 **table, int64_t *size);
 
 }  // namespace sbp

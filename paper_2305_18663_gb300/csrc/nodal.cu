@@ -9,11 +9,19 @@
 //      vector of changes) aggregated with warp match/ballot and, for longer
 //      rows, a shared-memory hash table;
 //   3. Delta DL over the changed entries of rows r,s and columns r,s only
-//      (Section II-C), block degrees included; Eq. 1-2;
+//      (Section II-C), block degrees included (Eq. 1-2).  Every term is
+//      f(x+k) - f(x) with f(x) = x ln x at integer counts, summed exactly in
+//      128-bit fixed point from a table (FP64 for counts beyond the table);
 //   4. Hastings-corrected Metropolis test (Alg. 2): logA = -beta dDL +
-//      ln(p_bwd / p_fwd), accept iff logA >= 0 or ln(u) < logA.
+//      ln(p_bwd / p_fwd), accept iff ln(u) < logA.  The Hastings sums and
+//      the logarithms are first evaluated in FP32 with a rigorous error
+//      bound; when ln(u) falls inside that band (or a trace is requested)
+//      the sums and the test are redone in FP64, so every decision equals
+//      the FP64 one.
 // The decision goes to the pending assignment; M is untouched until commit.
 //
+// GB300 executes one FP64 warp instruction per ~20 SM cycles, so the FP64
+// work is kept off the common path and spread across lanes when it runs.
 // Work units: one lane per neighbour for k <= 32; one warp per vertex with
 // a per-warp table for k <= 128; one CTA per vertex above that.
 #include <cmath>
@@ -31,6 +39,7 @@ struct DecideArgs {
     int64_t v_begin, v_end;
     uint64_t seed, sweep_id;
     double beta;
+    int trace_on;
     sbp_vertex_trace tr;
 };
 
@@ -47,56 +56,127 @@ __device__ __forceinline__ void write_trace(const DecideArgs &a, int v, int s, i
 
 __device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) { return md.M[(size_t)r * md.B + c]; }
 
-// contribution of one neighbour block t not in {r, s}
-__device__ __forceinline__ void eval_entry(const ModelDev &md, int t, int ko, int ki, int r, int s, double &dL,
-                                           double &fwd, double &bwd) {
-    const int B = md.B;
-    const int64_t Mrt = Mat(md, r, t), Mst = Mat(md, s, t), Mtr = Mat(md, t, r), Mts = Mat(md, t, s);
-    if (ko) dL += dxlogx(Mrt, -ko) + dxlogx(Mst, ko);
-    if (ki) dL += dxlogx(Mtr, -ki) + dxlogx(Mts, ki);
-    const double den = (double)((int64_t)md.dout[t] + md.din[t] + B);
-    const double c = (double)(ko + ki);
-    fwd += c * (double)(Mts + Mst + 1) / den;
-    bwd += c * (double)((Mtr - ki) + (Mrt - ko) + 1) / den;
+// Per-vertex scalars shared by the evaluation steps.
+struct VertexCtx {
+    int v, r, s;
+    int64_t Kout, Kin, self;  // out / in degree of v (self-loops included), self-loops
+    int64_t ko_r, ki_r, ko_s, ki_s;
+    int64_t k;  // total degree, an upper bound on the number of entries
+};
+
+// one neighbour block t not in {r, s}: exact Delta L terms, FP32 Hastings terms
+__device__ __forceinline__ void entry_fast(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, __int128 &dl,
+                                           double &fb, float &pf, float &pb) {
+    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    if (ko) dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
+    if (ki) dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
+    const float rc = md.rcp32[t];
+    const float c = (float)(ko + ki);
+    pf += c * (float)(Mts + Mst + 1) * rc;
+    pb += c * (float)((Mtr - ki) + (Mrt - ko) + 1) * rc;
 }
 
-// cross entries, degree terms, Hastings terms of r and s, and the test
-__device__ void finalize(const DecideArgs &a, int v, int r, int s, int64_t Kout, int64_t Kin, int64_t self,
-                         int64_t ko_r, int64_t ki_r, int64_t ko_s, int64_t ki_s, double dL, double fwd, double bwd,
-                         uint64_t w2, Counts &c) {
-    const ModelDev &md = a.md;
-    const int B = md.B;
-    const int64_t Mrr = Mat(md, r, r), Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r);
-    const int64_t dor = md.dout[r], dos = md.dout[s], dir = md.din[r], dis = md.din[s];
-    dL += dxlogx(Mrr, -(ko_r + ki_r + self));
-    dL += dxlogx(Mss, ko_s + ki_s + self);
-    dL += dxlogx(Mrs, ki_r - ko_s);
-    dL += dxlogx(Msr, ko_r - ki_s);
-    dL -= dxlogx(dor, -Kout) + dxlogx(dos, Kout) + dxlogx(dir, -Kin) + dxlogx(dis, Kin);
-    const double dH = -dL;
-    const int64_t dr = dor + dir, ds = dos + dis, K = Kout + Kin;
-    fwd += (double)(ko_r + ki_r + 2 * self) * (double)(Mrs + Msr + 1) / (double)(dr + B);
-    fwd += (double)(ko_s + ki_s) * (double)(2 * Mss + 1) / (double)(ds + B);
-    const int64_t Mrr2 = Mrr - (ko_r + ki_r + self), Mrs2 = Mrs + ki_r - ko_s, Msr2 = Msr + ko_r - ki_s;
-    bwd += (double)(ko_r + ki_r) * (double)(2 * Mrr2 + 1) / (double)(dr - K + B);
-    bwd += (double)(ko_s + ki_s + 2 * self) * (double)(Msr2 + Mrs2 + 1) / (double)(ds + K + B);
-    const double logA = -a.beta * dH + log(bwd) - log(fwd);
-    const double uacc = (double)(w2 >> 11) * 0x1.0p-53;
-    const double lnu = log(uacc);
-    const bool accept = logA >= 0.0 || lnu < logA;
-    const bool margin = fabs(lnu - logA) <= 1e-9 * fmax(fabs(logA), 1.0);
-    if (accept) md.bnew[v] = s;
-    c.proposed++;
-    c.moves++;
-    c.accepted += accept;
-    c.margin += margin;
-    write_trace(a, v, s, 1 | (accept ? 2 : 0) | (margin ? 4 : 0), dH, logA);
+// the same Hastings terms in FP64 (the expression the FP64 test uses)
+__device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, double &pf,
+                                            double &pb) {
+    const int64_t Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    const double den = (double)((int64_t)md.dsum[t] + md.B);
+    const double c = (double)(ko + ki);
+    pf += c * (double)(Mts + Mst + 1) / den;
+    pb += c * (double)((Mtr - ki) + (Mrt - ko) + 1) / den;
+}
+
+// job j in 0..9: 0-3 cross entries (r,r) (s,s) (r,s) (s,r); 4-7 block degree
+// terms (subtracted); 8-9 Hastings terms of the neighbours in r and in s
+__device__ __forceinline__ void special_fast(const ModelDev &md, const VertexCtx &x, int j, __int128 &dl, double &fb,
+                                             float &pf, float &pb) {
+    const int r = x.r, s = x.s, B = md.B;
+    const int64_t cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
+    switch (j) {
+        case 0: dl += dT(md.T, md.XT, Mat(md, r, r), -(cr + x.self), fb); break;
+        case 1: dl += dT(md.T, md.XT, Mat(md, s, s), cs + x.self, fb); break;
+        case 2: dl += dT(md.T, md.XT, Mat(md, r, s), x.ki_r - x.ko_s, fb); break;
+        case 3: dl += dT(md.T, md.XT, Mat(md, s, r), x.ko_r - x.ki_s, fb); break;
+        case 4: case 5: case 6: case 7: {
+            const int blk = (j == 4 || j == 6) ? r : s;
+            const int64_t deg = j < 6 ? md.dout[blk] : md.din[blk];
+            const int64_t kk = j < 6 ? x.Kout : x.Kin;
+            double f2 = 0.0;
+            dl -= dT(md.T, md.XT, deg, (j == 4 || j == 6) ? -kk : kk, f2);
+            fb -= f2;
+            break;
+        }
+        case 8: {
+            const int64_t Mrr = Mat(md, r, r), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), dr = md.dsum[r];
+            pf += (float)(cr + 2 * x.self) * (float)(Mrs + Msr + 1) / (float)(dr + B);
+            pb += (float)cr * (float)(2 * (Mrr - cr - x.self) + 1) / (float)(dr - K + B);
+            break;
+        }
+        case 9: {
+            const int64_t Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), ds = md.dsum[s];
+            pf += (float)cs * (float)(2 * Mss + 1) / (float)(ds + B);
+            pb += (float)(cs + 2 * x.self) * (float)((Msr + x.ko_r - x.ki_s) + (Mrs + x.ki_r - x.ko_s) + 1) /
+                  (float)(ds + K + B);
+            break;
+        }
+        default: break;
+    }
+}
+
+__device__ __forceinline__ void special_exact(const ModelDev &md, const VertexCtx &x, int j, double &pf, double &pb) {
+    const int r = x.r, s = x.s, B = md.B;
+    const int64_t cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
+    if (j == 8) {
+        const int64_t Mrr = Mat(md, r, r), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), dr = md.dsum[r];
+        pf += (double)(cr + 2 * x.self) * (double)(Mrs + Msr + 1) / (double)(dr + B);
+        pb += (double)cr * (double)(2 * (Mrr - cr - x.self) + 1) / (double)(dr - K + B);
+    } else if (j == 9) {
+        const int64_t Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), ds = md.dsum[s];
+        pf += (double)cs * (double)(2 * Mss + 1) / (double)(ds + B);
+        pb += (double)(cs + 2 * x.self) * (double)((Msr + x.ko_r - x.ki_s) + (Mrs + x.ki_r - x.ko_s) + 1) /
+              (double)(ds + K + B);
+    }
+}
+
+// FP32 decision with its error band.  Returns 1 accept, 0 reject, -1 when
+// the band does not settle it (FP64 needed).
+__device__ __forceinline__ int fast_decision(double beta, __int128 dl, double fb, float pf, float pb, uint64_t w2,
+                                             int64_t k) {
+    const uint64_t um = w2 >> 11;
+    if (um == 0) return 1;  // u = 0: ln u = -inf
+    const float b32 = (float)beta;
+    const float dl32 = fix_to_float(dl), fb32 = (float)fb;
+    const float lnpf = logf(pf), lnpb = logf(pb);
+    const float logA = b32 * (dl32 + fb32) + (lnpb - lnpf);
+    const float lnu = logf((float)um * 0x1p-53f);
+    const float diff = logA - lnu;
+    const float e = b32 * 3.0f * 0x1p-24f * (fabsf(dl32) + fabsf(fb32) + 1.0f) + 2.0f * (float)(k + 9) * 0x1p-24f +
+                    0x1p-23f * (fabsf(lnpf) + fabsf(lnpb) + 2.0f * fabsf(lnu) + fabsf(logA) + 1.0f);
+    const float band = 4.0f * e + 1e-6f;
+    if (!(fabsf(diff) > band)) return -1;  // also catches NaN / inf
+    return diff > 0.0f ? 1 : 0;
+}
+
+struct Exact {
+    double dH, logA;
+    bool accept, margin;
+};
+
+__device__ __forceinline__ Exact exact_decision(double beta, __int128 dl, double fb, double pf, double pb, uint64_t w2) {
+    Exact e;
+    const double dL = fix_to_double(dl) + fb;
+    e.dH = -dL;
+    e.logA = -beta * e.dH + log(pb) - log(pf);
+    const double lnu = log((double)(w2 >> 11) * 0x1p-53);
+    e.accept = lnu < e.logA;
+    e.margin = fabs(lnu - e.logA) <= 1e-9 * fmax(fabs(e.logA), 1.0);
+    return e;
 }
 
 // s from u: y < B picks s = y, else the inverse CDF over row u then column u
 __device__ __forceinline__ int propose_block(const ModelDev &md, int u, uint64_t w1) {
     const int B = md.B;
-    const int64_t du = (int64_t)md.dout[u] + md.din[u];
+    const int64_t du = md.dsum[u];
     const int64_t y = draw_below(w1, (uint64_t)(du + B));
     if (y < B) return (int)y;
     const int idx = warp_upper_bound(md.P + (size_t)u * 2 * B, 2 * B, (uint32_t)(y - B));
@@ -127,10 +207,80 @@ __device__ __forceinline__ bool table_add(int *keys, unsigned long long *cnt, in
     return false;
 }
 
+__device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin) {
+    c.proposed++;
+    c.moves++;
+    c.accepted += accept;
+    c.margin += margin;
+}
+
 // ---------------------------------------------------------------------------
 // warp per vertex (k <= kWarpDeg)
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_decide_warp(DecideArgs a) {
+// Evaluates the move v: r -> s once the entries are aggregated.
+// each_entry(f) calls f(t, ko, ki) for each entry the calling lane holds.
+// All 32 lanes call this; the result is written by lane 0.
+template <class EachEntry>
+__device__ __forceinline__ void evaluate_warp(const DecideArgs &a, VertexCtx &x, uint64_t w2, EachEntry each_entry,
+                                              Counts &c) {
+    const ModelDev &md = a.md;
+    const int lane = threadIdx.x & 31;
+    // neighbours in r and in s, packed one byte each (k <= kWarpDeg < 256)
+    int packed = 0;
+    each_entry([&](int t, int ko, int ki) {
+        if (t == x.r) packed += ko | (ki << 8);
+        else if (t == x.s) packed += (ko << 16) | (ki << 24);
+    });
+    packed = warp_sum_i(packed);
+    x.ko_r = packed & 0xff;
+    x.ki_r = (packed >> 8) & 0xff;
+    x.ko_s = (packed >> 16) & 0xff;
+    x.ki_s = (packed >> 24) & 0xff;
+
+    __int128 dl = 0;
+    double fb = 0.0;
+    float pf = 0.0f, pb = 0.0f;
+    each_entry([&](int t, int ko, int ki) {
+        if (t != x.r && t != x.s) entry_fast(md, x, t, ko, ki, dl, fb, pf, pb);
+    });
+    if (lane < 10) special_fast(md, x, lane, dl, fb, pf, pb);
+    dl = warp_sum_128(dl);
+    pf = warp_sum_f(pf);
+    pb = warp_sum_f(pb);
+    if (__any_sync(0xffffffffu, fb != 0.0)) fb = warp_sum(fb);
+    const int dec = a.trace_on ? -1 : fast_decision(a.beta, dl, fb, pf, pb, w2, x.k);
+    if (dec >= 0) {
+        if (lane == 0) {
+            if (dec) md.bnew[x.v] = x.s;
+            count_result(c, dec != 0, false);
+        }
+        return;
+    }
+    double pf64 = 0.0, pb64 = 0.0;
+    each_entry([&](int t, int ko, int ki) {
+        if (t != x.r && t != x.s) entry_exact(md, x, t, ko, ki, pf64, pb64);
+    });
+    special_exact(md, x, lane, pf64, pb64);
+    pf64 = warp_sum(pf64);
+    pb64 = warp_sum(pb64);
+    if (lane == 0) {
+        const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
+        if (e.accept) md.bnew[x.v] = x.s;
+        count_result(c, e.accept, e.margin);
+        write_trace(a, x.v, x.s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
+    }
+}
+
+__device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c) {
+    if (c.proposed | c.moves) {
+        atomicAdd(&md.counters->proposed, c.proposed);
+        atomicAdd(&md.counters->moves, c.moves);
+        atomicAdd(&md.counters->accepted, c.accepted);
+        atomicAdd(&md.counters->margin, c.margin);
+    }
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs a) {
     __shared__ int s_keys[kWarpsPerCta][kWarpCap];
     __shared__ unsigned long long s_cnt[kWarpsPerCta][kWarpCap];
     __shared__ int s_list[kWarpsPerCta][kWarpCap];
@@ -215,33 +365,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_decide_warp(DecideArgs a)
                 write_trace(a, v, r, 1, 0.0, 0.0);
             }
         } else {
-            double dL = 0.0, fwd = 0.0, bwd = 0.0;
-            int ko_r = 0, ki_r = 0, ko_s = 0, ki_s = 0;
+            VertexCtx x;
+            x.v = v; x.r = r; x.s = s;
+            x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
             if (k <= kSmallDeg) {
-                if (my_t >= 0) {
-                    if (my_t == r) { ko_r = my_ko; ki_r = my_ki; }
-                    else if (my_t == s) { ko_s = my_ko; ki_s = my_ki; }
-                    else eval_entry(md, my_t, my_ko, my_ki, r, s, dL, fwd, bwd);
-                }
+                evaluate_warp(a, x, w.z, [&](auto &&f) {
+                    if (my_t >= 0) f(my_t, my_ko, my_ki);
+                }, c);
             } else {
-                for (int e = lane; e < D; e += 32) {
-                    const int slot = list[e];
-                    const int t = keys[slot];
-                    const unsigned long long cc = cnt[slot];
-                    const int ko = (int)(cc & 0xffffffffu), ki = (int)(cc >> 32);
-                    if (t == r) { ko_r = ko; ki_r = ki; }
-                    else if (t == s) { ko_s = ko; ki_s = ki; }
-                    else eval_entry(md, t, ko, ki, r, s, dL, fwd, bwd);
-                }
+                evaluate_warp(a, x, w.z, [&](auto &&f) {
+                    for (int e = lane; e < D; e += 32) {
+                        const int slot = list[e];
+                        const unsigned long long cc = cnt[slot];
+                        f(keys[slot], (int)(cc & 0xffffffffu), (int)(cc >> 32));
+                    }
+                }, c);
             }
-            dL = warp_sum(dL);
-            fwd = warp_sum(fwd);
-            bwd = warp_sum(bwd);
-            ko_r = warp_sum_i(ko_r);
-            ki_r = warp_sum_i(ki_r);
-            ko_s = warp_sum_i(ko_s);
-            ki_s = warp_sum_i(ki_s);
-            if (lane == 0) finalize(a, v, r, s, kout, kin, self, ko_r, ki_r, ko_s, ki_s, dL, fwd, bwd, w.z, c);
         }
         if (k > kSmallDeg) {
             __syncwarp();
@@ -255,56 +394,38 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) k_decide_warp(DecideArgs a)
             __syncwarp();
         }
     }
-    if (lane == 0 && (c.proposed | c.moves)) {
-        atomicAdd(&md.counters->proposed, c.proposed);
-        atomicAdd(&md.counters->moves, c.moves);
-        atomicAdd(&md.counters->accepted, c.accepted);
-        atomicAdd(&md.counters->margin, c.margin);
-    }
+    if (lane == 0) flush_counts(md, c);
 }
 
 // ---------------------------------------------------------------------------
 // CTA per vertex (k > kWarpDeg); the table lives in dynamic shared memory
 
-__device__ double block_sum_d(double v, double *sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
-    __syncthreads();
-    return r;  // valid in thread 0
-}
-
-__device__ int block_sum_i(int v, int *sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum_i(v);
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    int r = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
-    __syncthreads();
-    return r;  // valid in thread 0
-}
+struct CtaScratch {
+    __int128 dl[kBigThreads / 32];
+    double fb[kBigThreads / 32], pf64[kBigThreads / 32], pb64[kBigThreads / 32];
+    float pf[kBigThreads / 32], pb[kBigThreads / 32];
+    __int128 dl_tot;
+    double fb_tot;
+    int rs[4];
+    int nlist, self, u, s, ok, dec;
+};
 
 __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int cap, int cap_log2) {
     extern __shared__ unsigned long long smem_u64[];
     unsigned long long *cnt = smem_u64;
     int *keys = reinterpret_cast<int *>(cnt + cap);
     int *list = keys + cap;
-    __shared__ int s_nlist, s_self, s_u, s_s;
-    __shared__ int s_ok;
-    __shared__ double sh_d[kBigThreads / 32];
-    __shared__ int sh_i[kBigThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ CtaScratch sh;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = kBigThreads / 32;
     for (int i = tid; i < cap; i += blockDim.x) {
         keys[i] = -1;
         cnt[i] = 0;
     }
-    if (tid == 0) { s_nlist = 0; s_self = 0; s_ok = 1; }
+    if (tid == 0) {
+        sh.nlist = 0;
+        sh.self = 0;
+        sh.ok = 1;
+    }
     __syncthreads();
 
     const GraphDev &g = a.g;
@@ -319,59 +440,121 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
         const int k = kout + kin;
         const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
         const int j = (int)draw_below(w.x, (uint64_t)k);
+        if (tid < 4) sh.rs[tid] = 0;
         for (int base = 0; base < k; base += blockDim.x) {
             const int idx = base + tid;
             const bool valid = idx < k, is_out = idx < kout;
             const int nb = valid ? (is_out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
             const int tb = valid ? md.b[nb] : -1;
-            if (idx == j) s_u = tb;
+            if (idx == j) sh.u = tb;
             const bool is_self = valid && nb == v;
             const int nself = __popc(__ballot_sync(0xffffffffu, is_self && is_out));
-            if (lane == 0 && nself) atomicAdd(&s_self, nself);
+            if (lane == 0 && nself) atomicAdd(&sh.self, nself);
             const int key = (valid && !is_self) ? tb : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, key);
             const unsigned outm = __ballot_sync(0xffffffffu, valid && !is_self && is_out);
             if (key >= 0 && lane == __ffs(peers) - 1) {
                 const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                if (!table_add(keys, cnt, list, &s_nlist, cap, cap_log2, key,
+                if (!table_add(keys, cnt, list, &sh.nlist, cap, cap_log2, key,
                                (unsigned long long)ko | ((unsigned long long)ki << 32)))
-                    s_ok = 0;
+                    sh.ok = 0;
             }
         }
         __syncthreads();
-        if (tid < 32) {
-            const int s = propose_block(md, s_u, w.y);
-            if (tid == 0) s_s = s;
+        if (wid == 0) {
+            const int s = propose_block(md, sh.u, w.y);
+            if (tid == 0) sh.s = s;
         }
         __syncthreads();
-        const int s = s_s, D = s_nlist, self = s_self, u_unused = s_u;
-        (void)u_unused;
-        if (tid == 0 && !s_ok) record_status(md.status, SBP_EHASHFULL);
+        const int s = sh.s, D = sh.nlist;
+        if (tid == 0 && !sh.ok) record_status(md.status, SBP_EHASHFULL);
         if (s == r) {
             if (tid == 0) {
                 c.proposed++;
                 write_trace(a, v, r, 1, 0.0, 0.0);
             }
         } else {
-            double dL = 0.0, fwd = 0.0, bwd = 0.0;
-            int ko_r = 0, ki_r = 0, ko_s = 0, ki_s = 0;
+            VertexCtx x;
+            x.v = v; x.r = r; x.s = s;
+            x.Kout = kout; x.Kin = kin; x.self = sh.self; x.k = k;
             for (int e = tid; e < D; e += blockDim.x) {
                 const int slot = list[e];
                 const int t = keys[slot];
                 const unsigned long long cc = cnt[slot];
-                const int ko = (int)(cc & 0xffffffffu), ki = (int)(cc >> 32);
-                if (t == r) { ko_r = ko; ki_r = ki; }
-                else if (t == s) { ko_s = ko; ki_s = ki; }
-                else eval_entry(md, t, ko, ki, r, s, dL, fwd, bwd);
+                if (t == r) { sh.rs[0] = (int)(cc & 0xffffffffu); sh.rs[1] = (int)(cc >> 32); }
+                if (t == s) { sh.rs[2] = (int)(cc & 0xffffffffu); sh.rs[3] = (int)(cc >> 32); }
             }
-            dL = block_sum_d(dL, sh_d);
-            fwd = block_sum_d(fwd, sh_d);
-            bwd = block_sum_d(bwd, sh_d);
-            ko_r = block_sum_i(ko_r, sh_i);
-            ki_r = block_sum_i(ki_r, sh_i);
-            ko_s = block_sum_i(ko_s, sh_i);
-            ki_s = block_sum_i(ki_s, sh_i);
-            if (tid == 0) finalize(a, v, r, s, kout, kin, self, ko_r, ki_r, ko_s, ki_s, dL, fwd, bwd, w.z, c);
+            __syncthreads();
+            x.ko_r = sh.rs[0]; x.ki_r = sh.rs[1]; x.ko_s = sh.rs[2]; x.ki_s = sh.rs[3];
+            __int128 dl = 0;
+            double fb = 0.0;
+            float pf = 0.0f, pb = 0.0f;
+            for (int e = tid; e < D; e += blockDim.x) {
+                const int slot = list[e];
+                const int t = keys[slot];
+                const unsigned long long cc = cnt[slot];
+                if (t != r && t != s) entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
+            }
+            if (tid < 10) special_fast(md, x, tid, dl, fb, pf, pb);
+            dl = warp_sum_128(dl);
+            pf = warp_sum_f(pf);
+            pb = warp_sum_f(pb);
+            fb = warp_sum(fb);
+            if (lane == 0) {
+                sh.dl[wid] = dl;
+                sh.fb[wid] = fb;
+                sh.pf[wid] = pf;
+                sh.pb[wid] = pb;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                __int128 dlt = 0;
+                double fbt = 0.0;
+                float pft = 0.0f, pbt = 0.0f;
+                for (int q = 0; q < nwarps; ++q) {
+                    dlt += sh.dl[q];
+                    fbt += sh.fb[q];
+                    pft += sh.pf[q];
+                    pbt += sh.pb[q];
+                }
+                sh.dl_tot = dlt;
+                sh.fb_tot = fbt;
+                const int dec = a.trace_on ? -1 : fast_decision(a.beta, dlt, fbt, pft, pbt, w.z, k);
+                sh.dec = dec;
+                if (dec >= 0) {
+                    if (dec) md.bnew[v] = s;
+                    count_result(c, dec != 0, false);
+                }
+            }
+            __syncthreads();
+            if (sh.dec < 0) {
+                double pf64 = 0.0, pb64 = 0.0;
+                for (int e = tid; e < D; e += blockDim.x) {
+                    const int slot = list[e];
+                    const int t = keys[slot];
+                    const unsigned long long cc = cnt[slot];
+                    if (t != r && t != s) entry_exact(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), pf64, pb64);
+                }
+                special_exact(md, x, tid, pf64, pb64);
+                pf64 = warp_sum(pf64);
+                pb64 = warp_sum(pb64);
+                if (lane == 0) {
+                    sh.pf64[wid] = pf64;
+                    sh.pb64[wid] = pb64;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double pft = 0.0, pbt = 0.0;
+                    for (int q = 0; q < nwarps; ++q) {
+                        pft += sh.pf64[q];
+                        pbt += sh.pb64[q];
+                    }
+                    const Exact e = exact_decision(a.beta, sh.dl_tot, sh.fb_tot, pft, pbt, w.z);
+                    if (e.accept) md.bnew[v] = s;
+                    count_result(c, e.accept, e.margin);
+                    write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
+                }
+            }
         }
         __syncthreads();
         for (int e = tid; e < D; e += blockDim.x) {
@@ -379,15 +562,13 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
             keys[slot] = -1;
             cnt[slot] = 0;
         }
-        if (tid == 0) { s_nlist = 0; s_self = 0; }
+        if (tid == 0) {
+            sh.nlist = 0;
+            sh.self = 0;
+        }
         __syncthreads();
     }
-    if (tid == 0 && (c.proposed | c.moves)) {
-        atomicAdd(&md.counters->proposed, c.proposed);
-        atomicAdd(&md.counters->moves, c.moves);
-        atomicAdd(&md.counters->accepted, c.accepted);
-        atomicAdd(&md.counters->margin, c.margin);
-    }
+    if (tid == 0) flush_counts(md, c);
 }
 
 int sm_count() {
@@ -415,6 +596,10 @@ ModelDev model_dev(sbp_model *m) {
     d.dout = m->dout;
     d.din = m->din;
     d.rcp = m->rcp;
+    d.rcp32 = m->rcp32;
+    d.dsum = m->dsum;
+    d.T = m->T;
+    d.XT = m->XT;
     d.status = m->status;
     d.counters = m->counters;
     return d;
@@ -432,16 +617,16 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.sweep_id = sweep_id;
     a.beta = m->p.beta;
     a.tr = trace ? *trace : sbp_vertex_trace{nullptr, nullptr, nullptr, nullptr};
-    const bool want_trace = a.tr.s || a.tr.flags || a.tr.dH || a.tr.logA;
+    a.trace_on = (a.tr.s || a.tr.flags || a.tr.dH || a.tr.logA) ? 1 : 0;
     const int sms = sm_count();
 
     // k <= kWarpDeg (and k = 0 when a trace is requested)
-    a.lo = want_trace ? g->bin[0] : g->bin[1];
+    a.lo = a.trace_on ? g->bin[0] : g->bin[1];
     a.hi = g->bin[3];
     if (a.hi > a.lo) {
         const int64_t warps = a.hi - a.lo;
         int64_t blocks = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
-        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
         k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, 0, m->stream>>>(a);
         SBP_CUDA(cudaGetLastError());
     }
@@ -454,7 +639,7 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
         while ((int64_t(1) << cap_log2) < need) ++cap_log2;
         const int cap = 1 << cap_log2;
         const size_t smem = (size_t)cap * (8 + 4 + 4);
-        if (smem > 200 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
+        if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
         SBP_CUDA(cudaFuncSetAttribute(k_decide_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int64_t blocks = a.hi - a.lo;
         if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
