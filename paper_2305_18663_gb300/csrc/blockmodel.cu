@@ -19,18 +19,34 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Warp-aggregated atomic histogram of (b[src], b[dst]) over the out-edges.
+// Diagonal counts (intra-block edges, the large majority) go to a per-CTA
+// shared-memory copy of the diagonal first, flushed once per CTA.
 __global__ void __launch_bounds__(kThreads) k_hist_dense(GraphDev g, const int32_t *__restrict__ b,
                                                          int32_t *__restrict__ M, int B) {
+    extern __shared__ int diag[];
+    for (int i = threadIdx.x; i < B; i += blockDim.x) diag[i] = 0;
+    __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.m; base += stride) {
         const int64_t e = base + threadIdx.x;
         const bool valid = e < g.m;
-        int key = -1;
-        if (valid) key = b[g.esrc[e]] * B + b[g.oc[e]];
+        int key = -1, r = 0, t = 0;
+        if (valid) {
+            r = b[g.esrc[e]];
+            t = b[g.oc[e]];
+            key = r * B + t;
+        }
         const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&M[key], __popc(peers));
+        if (valid && lane == __ffs(peers) - 1) {
+            if (r == t) atomicAdd(&diag[r], __popc(peers));
+            else atomicAdd(&M[key], __popc(peers));
+        }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+        if (diag[i]) atomicAdd(&M[(size_t)i * B + i], diag[i]);
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
@@ -220,7 +236,9 @@ int rebuild_blockmodel(sbp_model *m) {
     SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
     SBP_CUDA(cudaMemsetAsync(m->M, 0, (size_t)BB * 4, m->stream));
     if (g->m > 0) {
-        k_hist_dense<<<grid_for(g->m, kThreads, sms * 8), kThreads, 0, m->stream>>>(g->dev(), m->b, m->M, B);
+        const size_t smem = (size_t)B * 4;
+        if (smem > 48 * 1024) SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_hist_dense<<<grid_for(g->m, kThreads, sms * 2), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B);
         SBP_CUDA(cudaGetLastError());
     }
     k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(m->M, B, m->P, m->dout,

@@ -162,13 +162,15 @@ __device__ __forceinline__ double dxlogx(int64_t x, int64_t k) {
     return (double)k * log((double)(x + k)) + (double)x * log1p((double)k / (double)x);
 }
 
+static __device__ __noinline__ double dxlogx_slow(int64_t x, int64_t k) { return dxlogx(x, k); }
+
 // f(x+k) - f(x) from the fixed-point table when both counts are inside it;
 // otherwise the FP64 formula above is added to fb and 0 returned
 __device__ __forceinline__ __int128 dT(const __int128 *__restrict__ T, int64_t XT, int64_t x, int64_t k, double &fb) {
     if (k == 0) return 0;
     const int64_t y = x + k;
     if (x < XT && y < XT) return T[y] - T[x];
-    fb += dxlogx(x, k);
+    fb += dxlogx_slow(x, k);
     return 0;
 }
 
@@ -193,7 +195,12 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 }
 
 // fixed point (scale 2^64) to float / double
-__device__ __forceinline__ float fix_to_float(__int128 v) { return (float)(long long)(v >> 40) * 0x1p-24f; }
+// (two 32-bit conversions: 64-bit integer conversions would use the FP64 pipe)
+__device__ __forceinline__ float fix_to_float(__int128 v) {
+    const int hi = (int)(v >> 72);                           // units of 2^8
+    const unsigned lo = (unsigned)((v >> 40) & 0xffffffffu);  // units of 2^-24
+    return fmaf((float)hi, 256.0f, (float)lo * 0x1p-24f);
+}
 __device__ __forceinline__ double fix_to_double(__int128 v) {
     const long long hi = (long long)(v >> 64);
     const unsigned long long lo = (unsigned long long)v;

@@ -99,6 +99,9 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     for (int i = 0; i < 4; ++i) g->bin[i + 1] = g->bin[i] + cnt[i];
     int64_t pos[4] = {g->bin[0], g->bin[1], g->bin[2], g->bin[3]};
     for (int64_t v = 0; v < n; ++v) order[(size_t)pos[group(v)]++] = (int32_t)v;
+    // the largest rows first inside the top group, for load balance
+    auto deg = [&](int32_t v) { return (op[(size_t)v + 1] - op[(size_t)v]) + (ip[(size_t)v + 1] - ip[(size_t)v]); };
+    std::stable_sort(order.begin() + g->bin[3], order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
 
     g->n = n;
     g->m = m;

@@ -39,6 +39,7 @@ struct DecideArgs {
     int64_t v_begin, v_end;
     uint64_t seed, sweep_id;
     double beta;
+    float beta32;
     int trace_on;
     sbp_vertex_trace tr;
 };
@@ -59,9 +60,9 @@ __device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) { return md
 // Per-vertex scalars shared by the evaluation steps.
 struct VertexCtx {
     int v, r, s;
-    int64_t Kout, Kin, self;  // out / in degree of v (self-loops included), self-loops
-    int64_t ko_r, ki_r, ko_s, ki_s;
-    int64_t k;  // total degree, an upper bound on the number of entries
+    int Kout, Kin, self;  // out / in degree of v (self-loops included), self-loops
+    int ko_r, ki_r, ko_s, ki_s;
+    int k;  // total degree, an upper bound on the number of entries
 };
 
 // one neighbour block t not in {r, s}: exact Delta L terms, FP32 Hastings terms
@@ -91,7 +92,7 @@ __device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx 
 __device__ __forceinline__ void special_fast(const ModelDev &md, const VertexCtx &x, int j, __int128 &dl, double &fb,
                                              float &pf, float &pb) {
     const int r = x.r, s = x.s, B = md.B;
-    const int64_t cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
+    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
     switch (j) {
         case 0: dl += dT(md.T, md.XT, Mat(md, r, r), -(cr + x.self), fb); break;
         case 1: dl += dT(md.T, md.XT, Mat(md, s, s), cs + x.self, fb); break;
@@ -99,21 +100,21 @@ __device__ __forceinline__ void special_fast(const ModelDev &md, const VertexCtx
         case 3: dl += dT(md.T, md.XT, Mat(md, s, r), x.ko_r - x.ki_s, fb); break;
         case 4: case 5: case 6: case 7: {
             const int blk = (j == 4 || j == 6) ? r : s;
-            const int64_t deg = j < 6 ? md.dout[blk] : md.din[blk];
-            const int64_t kk = j < 6 ? x.Kout : x.Kin;
+            const int deg = j < 6 ? md.dout[blk] : md.din[blk];
+            const int kk = j < 6 ? x.Kout : x.Kin;
             double f2 = 0.0;
             dl -= dT(md.T, md.XT, deg, (j == 4 || j == 6) ? -kk : kk, f2);
             fb -= f2;
             break;
         }
         case 8: {
-            const int64_t Mrr = Mat(md, r, r), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), dr = md.dsum[r];
+            const int Mrr = Mat(md, r, r), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), dr = md.dsum[r];
             pf += (float)(cr + 2 * x.self) * (float)(Mrs + Msr + 1) / (float)(dr + B);
             pb += (float)cr * (float)(2 * (Mrr - cr - x.self) + 1) / (float)(dr - K + B);
             break;
         }
         case 9: {
-            const int64_t Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), ds = md.dsum[s];
+            const int Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), ds = md.dsum[s];
             pf += (float)cs * (float)(2 * Mss + 1) / (float)(ds + B);
             pb += (float)(cs + 2 * x.self) * (float)((Msr + x.ko_r - x.ki_s) + (Mrs + x.ki_r - x.ko_s) + 1) /
                   (float)(ds + K + B);
@@ -140,15 +141,15 @@ __device__ __forceinline__ void special_exact(const ModelDev &md, const VertexCt
 
 // FP32 decision with its error band.  Returns 1 accept, 0 reject, -1 when
 // the band does not settle it (FP64 needed).
-__device__ __forceinline__ int fast_decision(double beta, __int128 dl, double fb, float pf, float pb, uint64_t w2,
-                                             int64_t k) {
+__device__ __forceinline__ int fast_decision(float b32, __int128 dl, bool has_fb, double fb, float pf, float pb,
+                                             uint64_t w2, int k) {
     const uint64_t um = w2 >> 11;
     if (um == 0) return 1;  // u = 0: ln u = -inf
-    const float b32 = (float)beta;
-    const float dl32 = fix_to_float(dl), fb32 = (float)fb;
+    const float dl32 = fix_to_float(dl), fb32 = has_fb ? (float)fb : 0.0f;
     const float lnpf = logf(pf), lnpb = logf(pb);
     const float logA = b32 * (dl32 + fb32) + (lnpb - lnpf);
-    const float lnu = logf((float)um * 0x1p-53f);
+    const float u32 = fmaf((float)(unsigned)(um >> 21), 0x1p-32f, (float)(unsigned)(um & 0x1fffffu) * 0x1p-53f);
+    const float lnu = logf(u32);
     const float diff = logA - lnu;
     const float e = b32 * 3.0f * 0x1p-24f * (fabsf(dl32) + fabsf(fb32) + 1.0f) + 2.0f * (float)(k + 9) * 0x1p-24f +
                     0x1p-23f * (fabsf(lnpf) + fabsf(lnpb) + 2.0f * fabsf(lnu) + fabsf(logA) + 1.0f);
@@ -162,7 +163,7 @@ struct Exact {
     bool accept, margin;
 };
 
-__device__ __forceinline__ Exact exact_decision(double beta, __int128 dl, double fb, double pf, double pb, uint64_t w2) {
+__device__ __noinline__ Exact exact_decision(double beta, __int128 dl, double fb, double pf, double pb, uint64_t w2) {
     Exact e;
     const double dL = fix_to_double(dl) + fb;
     e.dH = -dL;
@@ -207,6 +208,26 @@ __device__ __forceinline__ bool table_add(int *keys, unsigned long long *cnt, in
     return false;
 }
 
+// the same with 32-bit counts (ko | ki << 16) and 16-bit list entries
+__device__ __forceinline__ bool table_add32(int *keys, unsigned *cnt, unsigned short *list, int *nlist, int cap,
+                                            int cap_log2, int key, unsigned inc) {
+    unsigned h = hash_slot(key, cap_log2);
+    for (int p = 0; p < cap; ++p) {
+        const int prev = atomicCAS(&keys[h], -1, key);
+        if (prev == -1) {
+            list[atomicAdd(nlist, 1)] = (unsigned short)h;
+            atomicAdd(&cnt[h], inc);
+            return true;
+        }
+        if (prev == key) {
+            atomicAdd(&cnt[h], inc);
+            return true;
+        }
+        h = (h + 1) & (unsigned)(cap - 1);
+    }
+    return false;
+}
+
 __device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin) {
     c.proposed++;
     c.moves++;
@@ -225,17 +246,31 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, VertexCtx &x,
                                               Counts &c) {
     const ModelDev &md = a.md;
     const int lane = threadIdx.x & 31;
-    // neighbours in r and in s, packed one byte each (k <= kWarpDeg < 256)
-    int packed = 0;
-    each_entry([&](int t, int ko, int ki) {
-        if (t == x.r) packed += ko | (ki << 8);
-        else if (t == x.s) packed += (ko << 16) | (ki << 24);
-    });
-    packed = warp_sum_i(packed);
-    x.ko_r = packed & 0xff;
-    x.ki_r = (packed >> 8) & 0xff;
-    x.ko_s = (packed >> 16) & 0xff;
-    x.ki_s = (packed >> 24) & 0xff;
+    // neighbours in r and in s (one lane holds each); 16-bit fields when
+    // the degree allows it
+    int pr = 0, ps = 0;
+    if (x.k < 65536) {
+        each_entry([&](int t, int ko, int ki) {
+            if (t == x.r) pr += ko | (ki << 16);
+            else if (t == x.s) ps += ko | (ki << 16);
+        });
+        pr = warp_sum_i(pr);
+        ps = warp_sum_i(ps);
+        x.ko_r = pr & 0xffff;
+        x.ki_r = pr >> 16;
+        x.ko_s = ps & 0xffff;
+        x.ki_s = ps >> 16;
+    } else {
+        int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        each_entry([&](int t, int ko, int ki) {
+            if (t == x.r) { a0 += ko; a1 += ki; }
+            else if (t == x.s) { a2 += ko; a3 += ki; }
+        });
+        x.ko_r = warp_sum_i(a0);
+        x.ki_r = warp_sum_i(a1);
+        x.ko_s = warp_sum_i(a2);
+        x.ki_s = warp_sum_i(a3);
+    }
 
     __int128 dl = 0;
     double fb = 0.0;
@@ -247,8 +282,9 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, VertexCtx &x,
     dl = warp_sum_128(dl);
     pf = warp_sum_f(pf);
     pb = warp_sum_f(pb);
-    if (__any_sync(0xffffffffu, fb != 0.0)) fb = warp_sum(fb);
-    const int dec = a.trace_on ? -1 : fast_decision(a.beta, dl, fb, pf, pb, w2, x.k);
+    const bool has_fb = __any_sync(0xffffffffu, __double_as_longlong(fb) != 0);
+    if (has_fb) fb = warp_sum(fb);
+    const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
     if (dec >= 0) {
         if (lane == 0) {
             if (dec) md.bnew[x.v] = x.s;
@@ -280,30 +316,28 @@ __device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c
     }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs a) {
-    __shared__ int s_keys[kWarpsPerCta][kWarpCap];
-    __shared__ unsigned long long s_cnt[kWarpsPerCta][kWarpCap];
-    __shared__ int s_list[kWarpsPerCta][kWarpCap];
-    __shared__ int s_nlist[kWarpsPerCta];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *keys = s_keys[wid];
-    unsigned long long *cnt = s_cnt[wid];
-    int *list = s_list[wid];
-    int *nlist = &s_nlist[wid];
-    for (int i = lane; i < kWarpCap; i += 32) {
+// Per warp, in dynamic shared memory: cap int keys, cap 32-bit counts
+// (ko | ki << 16, so degrees stay below 65536), cap 16-bit list entries, one
+// list length.  Warps per CTA = blockDim.x / 32.
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs a, int cap, int cap_log2) {
+    extern __shared__ int dsm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    int *keys = dsm + (size_t)wid * cap;
+    unsigned *cnt = reinterpret_cast<unsigned *>(dsm + (size_t)nwarps * cap) + (size_t)wid * cap;
+    int *nlist = dsm + (size_t)2 * nwarps * cap + wid;
+    unsigned short *list = reinterpret_cast<unsigned short *>(dsm + (size_t)2 * nwarps * cap + nwarps) + (size_t)wid * cap;
+    for (int i = lane; i < cap; i += 32) {
         keys[i] = -1;
         cnt[i] = 0;
     }
     if (lane == 0) *nlist = 0;
     __syncwarp();
-    constexpr int cap_log2 = 8;
-    static_assert((1 << cap_log2) == kWarpCap, "table size");
 
     const GraphDev &g = a.g;
     const ModelDev &md = a.md;
     Counts c;
-    const int64_t nw = (int64_t)gridDim.x * kWarpsPerCta;
-    for (int64_t i = a.lo + (int64_t)blockIdx.x * kWarpsPerCta + wid; i < a.hi; i += nw) {
+    const int64_t nw = (int64_t)gridDim.x * nwarps;
+    for (int64_t i = a.lo + (int64_t)blockIdx.x * nwarps + wid; i < a.hi; i += nw) {
         const int v = a.order[i];
         if (v < a.v_begin || v >= a.v_end) continue;
         const int r = md.b[v];
@@ -349,8 +383,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs
                 const unsigned outm = __ballot_sync(0xffffffffu, valid && !is_self && is_out);
                 if (key >= 0 && lane == __ffs(peers) - 1) {
                     const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                    ok &= table_add(keys, cnt, list, nlist, kWarpCap, cap_log2, key,
-                                    (unsigned long long)ko | ((unsigned long long)ki << 32));
+                    ok &= table_add32(keys, cnt, list, nlist, cap, cap_log2, key, ko | (ki << 16));
                 }
                 __syncwarp();
             }
@@ -376,8 +409,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs
                 evaluate_warp(a, x, w.z, [&](auto &&f) {
                     for (int e = lane; e < D; e += 32) {
                         const int slot = list[e];
-                        const unsigned long long cc = cnt[slot];
-                        f(keys[slot], (int)(cc & 0xffffffffu), (int)(cc >> 32));
+                        const unsigned cc = cnt[slot];
+                        f(keys[slot], (int)(cc & 0xffffu), (int)(cc >> 16));
                     }
                 }, c);
             }
@@ -499,7 +532,7 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
             dl = warp_sum_128(dl);
             pf = warp_sum_f(pf);
             pb = warp_sum_f(pb);
-            fb = warp_sum(fb);
+            if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
             if (lane == 0) {
                 sh.dl[wid] = dl;
                 sh.fb[wid] = fb;
@@ -519,7 +552,8 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
                 }
                 sh.dl_tot = dlt;
                 sh.fb_tot = fbt;
-                const int dec = a.trace_on ? -1 : fast_decision(a.beta, dlt, fbt, pft, pbt, w.z, k);
+                const bool has_fb = __double_as_longlong(fbt) != 0;
+                const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dlt, has_fb, fbt, pft, pbt, w.z, k);
                 sh.dec = dec;
                 if (dec >= 0) {
                     if (dec) md.bnew[v] = s;
@@ -616,35 +650,51 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.seed = m->p.seed;
     a.sweep_id = sweep_id;
     a.beta = m->p.beta;
+    a.beta32 = (float)m->p.beta;
     a.tr = trace ? *trace : sbp_vertex_trace{nullptr, nullptr, nullptr, nullptr};
     a.trace_on = (a.tr.s || a.tr.flags || a.tr.dH || a.tr.logA) ? 1 : 0;
     const int sms = sm_count();
 
-    // k <= kWarpDeg (and k = 0 when a trace is requested)
+    auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
+    // k <= kWarpDeg (and k = 0 when a trace is requested): 256-slot tables
     a.lo = a.trace_on ? g->bin[0] : g->bin[1];
     a.hi = g->bin[3];
     if (a.hi > a.lo) {
         const int64_t warps = a.hi - a.lo;
         int64_t blocks = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
         if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
-        k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, 0, m->stream>>>(a);
+        // the attribute is per function: set it for this launch's size
+        const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
+        SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a, kWarpCap, 8);
         SBP_CUDA(cudaGetLastError());
     }
-    // k > kWarpDeg
+    // k > kWarpDeg: per-warp tables sized for min(max degree, B) distinct
+    // blocks while they fit, one CTA per vertex beyond that
     a.lo = g->bin[3];
     a.hi = g->bin[4];
     if (a.hi > a.lo) {
-        int64_t need = 2 * (int64_t)(g->max_deg < m->B ? g->max_deg : m->B) + 2;
+        const int64_t need = 2 * (int64_t)(g->max_deg < m->B ? g->max_deg : m->B) + 2;
         int cap_log2 = 6;
         while ((int64_t(1) << cap_log2) < need) ++cap_log2;
         const int cap = 1 << cap_log2;
-        const size_t smem = (size_t)cap * (8 + 4 + 4);
-        if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
-        SBP_CUDA(cudaFuncSetAttribute(k_decide_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int64_t blocks = a.hi - a.lo;
-        if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
-        k_decide_cta<<<(int)blocks, kBigThreads, smem, m->stream>>>(a, cap, cap_log2);
-        SBP_CUDA(cudaGetLastError());
+        if (cap <= 4096 && g->max_deg < 65536) {
+            const int nwarps = cap <= 1024 ? 8 : 4;
+            const size_t smem = warp_smem(cap, nwarps);
+            SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int64_t blocks = (a.hi - a.lo + nwarps - 1) / nwarps;
+            if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+            k_decide_warp<<<(int)blocks, nwarps * 32, smem, m->stream>>>(a, cap, cap_log2);
+            SBP_CUDA(cudaGetLastError());
+        } else {
+            const size_t smem = (size_t)cap * (8 + 4 + 4);
+            if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
+            SBP_CUDA(cudaFuncSetAttribute(k_decide_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int64_t blocks = a.hi - a.lo;
+            if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+            k_decide_cta<<<(int)blocks, kBigThreads, smem, m->stream>>>(a, cap, cap_log2);
+            SBP_CUDA(cudaGetLastError());
+        }
     }
     return SBP_OK;
 }

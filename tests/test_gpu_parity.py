@@ -146,6 +146,35 @@ def test_nodal_sweeps_self_loops_duplicates_isolated():
     run_sweeps(g, 12, random_labels(n, 12, seed=1), sweeps=8)
 
 
+class _G:
+    def __init__(self, n, src, dst):
+        self.n, self.src, self.dst, self.m = n, src.astype(np.int32), dst.astype(np.int32), src.size
+
+
+def test_nodal_sweeps_large_B_hubs_cta_path():
+    # B = 3000 and hubs above 2048 edges: per-vertex tables beyond 4096
+    # slots take the CTA-per-vertex kernel
+    rng = np.random.default_rng(21)
+    n = 6000
+    src = rng.integers(0, n, 40000)
+    dst = rng.integers(0, n, 40000)
+    for hub, deg in [(7, 2600), (8, 3100), (9, 5000)]:
+        src = np.concatenate([src, np.full(deg, hub), rng.integers(0, n, deg // 2), [hub, hub]])
+        dst = np.concatenate([dst, rng.integers(0, n, deg), np.full(deg // 2, hub), [hub, hub]])
+    g = _G(n, src, dst)
+    run_sweeps(g, 3000, random_labels(n, 3000, seed=2), sweeps=3)
+
+
+def test_nodal_sweeps_degree_above_65535():
+    # a hub with 70,000 edges: 16-bit packed counts no longer fit
+    rng = np.random.default_rng(22)
+    n = 80000
+    src = np.concatenate([np.zeros(70000, np.int64), rng.integers(1, n, 100000)])
+    dst = np.concatenate([rng.integers(1, n, 70000), rng.integers(1, n, 100000)])
+    g = _G(n, src, dst)
+    run_sweeps(g, 16, random_labels(n, 16, seed=3), sweeps=2)
+
+
 def test_nodal_sweeps_scaled_dcsbm():
     # 50k vertices, 1M edges, 316 planted blocks, 30% reassigned: spans
     # every degree group (one lane per edge, warp, CTA) and ragged tails
