@@ -48,7 +48,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    flags = FLAGS + (extra or [])
+    # SBP_NVCC_FLAGS: extra nvcc flags for tuning builds (e.g. -DSBP_DECIDE_MIN_BLOCKS=2)
+    flags = FLAGS + (extra or []) + os.environ.get("SBP_NVCC_FLAGS", "").split()
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))

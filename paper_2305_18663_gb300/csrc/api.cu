@@ -191,6 +191,7 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     cudaFree(m->bnew);
     cudaFree(m->M);
     cudaFree(m->P);
+    cudaFree(m->Pc);
     cudaFree(m->dout);
     cudaFree(m->din);
     cudaFree(m->rcp);

@@ -19,30 +19,52 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Warp-aggregated atomic histogram of (b[src], b[dst]) over the out-edges.
-// Diagonal counts (intra-block edges, the large majority) go to a per-CTA
-// shared-memory copy of the diagonal first, flushed once per CTA.
+// Warp-aggregated atomic histogram of (b[src], b[dst]) over the out-edges,
+// four consecutive edges per thread (16-byte loads, eight independent
+// gathers in flight).  Diagonal counts (intra-block edges, the large
+// majority) go to a per-CTA shared-memory copy of the diagonal first.
+__device__ __forceinline__ void hist_add(int32_t *__restrict__ M, int *diag, int B, bool valid, int r, int t) {
+    const int key = valid ? r * B + t : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+        if (r == t) atomicAdd(&diag[r], __popc(peers));
+        else atomicAdd(&M[key], __popc(peers));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_hist_dense(GraphDev g, const int32_t *__restrict__ b,
                                                          int32_t *__restrict__ M, int B) {
     extern __shared__ int diag[];
     for (int i = threadIdx.x; i < B; i += blockDim.x) diag[i] = 0;
     __syncthreads();
+    const int64_t m4 = g.m >> 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.m; base += stride) {
-        const int64_t e = base + threadIdx.x;
-        const bool valid = e < g.m;
-        int key = -1, r = 0, t = 0;
+    const int4 *es4 = reinterpret_cast<const int4 *>(g.esrc);
+    const int4 *oc4 = reinterpret_cast<const int4 *>(g.oc);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m4; base += stride) {
+        const int64_t q = base + threadIdx.x;
+        const bool valid = q < m4;
+        int4 s4 = make_int4(0, 0, 0, 0), d4 = make_int4(0, 0, 0, 0);
         if (valid) {
-            r = b[g.esrc[e]];
-            t = b[g.oc[e]];
-            key = r * B + t;
+            s4 = es4[q];
+            d4 = oc4[q];
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (valid && lane == __ffs(peers) - 1) {
-            if (r == t) atomicAdd(&diag[r], __popc(peers));
-            else atomicAdd(&M[key], __popc(peers));
+        int r0 = 0, r1 = 0, r2 = 0, r3 = 0, t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        if (valid) {
+            r0 = b[s4.x]; r1 = b[s4.y]; r2 = b[s4.z]; r3 = b[s4.w];
+            t0 = b[d4.x]; t1 = b[d4.y]; t2 = b[d4.z]; t3 = b[d4.w];
         }
+        hist_add(M, diag, B, valid, r0, t0);
+        hist_add(M, diag, B, valid, r1, t1);
+        hist_add(M, diag, B, valid, r2, t2);
+        hist_add(M, diag, B, valid, r3, t3);
+    }
+    // the last m % 4 edges
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const int64_t e = (m4 << 2) + threadIdx.x;
+        const bool valid = e < g.m;
+        const int r = valid ? b[g.esrc[e]] : 0, t = valid ? b[g.oc[e]] : 0;
+        hist_add(M, diag, B, valid, r, t);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < B; i += blockDim.x)
@@ -63,7 +85,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
 __global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__restrict__ M, int B,
                                                            uint32_t *__restrict__ P, int32_t *__restrict__ dout,
                                                            int32_t *__restrict__ din, double *__restrict__ rcp,
-                                                           float *__restrict__ rcp32, int32_t *__restrict__ dsum) {
+                                                           float *__restrict__ rcp32, int32_t *__restrict__ dsum,
+                                                           uint32_t *__restrict__ Pc, int pstep) {
     const int u = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (u >= B) return;
@@ -84,6 +107,9 @@ __global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__rest
         if (c < B) row[B + c] = v;
         carry = __shfl_sync(0xffffffffu, v, 31);
     }
+    __syncwarp();
+    const int pi = (lane + 1) * pstep - 1 < 2 * B - 1 ? (lane + 1) * pstep - 1 : 2 * B - 1;
+    Pc[(size_t)u * 32 + lane] = row[pi];
     if (lane == 0) {
         const uint32_t du_in = carry - du_out;
         dout[u] = (int32_t)du_out;
@@ -202,6 +228,7 @@ int ensure_capacity(sbp_model *m, int32_t B) {
     if (B <= m->Bcap) return SBP_OK;
     cudaFree(m->M);
     cudaFree(m->P);
+    cudaFree(m->Pc);
     cudaFree(m->dout);
     cudaFree(m->din);
     cudaFree(m->rcp);
@@ -211,11 +238,12 @@ int ensure_capacity(sbp_model *m, int32_t B) {
     cudaFree(m->best_d);
     cudaFree(m->map);
     cudaFree(m->vcount);
-    m->M = nullptr; m->P = nullptr; m->dout = m->din = nullptr; m->rcp = nullptr; m->rcp32 = nullptr; m->dsum = nullptr;
+    m->M = nullptr; m->P = nullptr; m->Pc = nullptr; m->dout = m->din = nullptr; m->rcp = nullptr; m->rcp32 = nullptr; m->dsum = nullptr;
     m->best_s = m->map = m->vcount = nullptr; m->best_d = nullptr;
     m->Bcap = 0;
     const size_t BB = (size_t)B * B;
     if (cudaMalloc(&m->M, BB * 4) != cudaSuccess || cudaMalloc(&m->P, BB * 8) != cudaSuccess ||
+        cudaMalloc(&m->Pc, (size_t)B * 32 * 4) != cudaSuccess ||
         cudaMalloc(&m->dout, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->din, (size_t)B * 4) != cudaSuccess ||
         cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->rcp32, (size_t)B * 4) != cudaSuccess ||
         cudaMalloc(&m->dsum, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
@@ -238,11 +266,12 @@ int rebuild_blockmodel(sbp_model *m) {
     if (g->m > 0) {
         const size_t smem = (size_t)B * 4;
         if (smem > 48 * 1024) SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_hist_dense<<<grid_for(g->m, kThreads, sms * 2), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B);
+        k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B);
         SBP_CUDA(cudaGetLastError());
     }
     k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(m->M, B, m->P, m->dout,
-                                                                                          m->din, m->rcp, m->rcp32, m->dsum);
+                                                                                          m->din, m->rcp, m->rcp32, m->dsum, m->Pc,
+                                                                                          (2 * B + 31) / 32);
     SBP_CUDA(cudaGetLastError());
     const int np = grid_for(BB, kThreads * 4, m->npartials);
     DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);

@@ -84,6 +84,8 @@ struct ModelDev {
     int32_t *bnew;          // pending assignment
     const int32_t *M;       // dense [B*B]
     const uint32_t *P;      // [B*2B]: row prefix of M[u][.], then dout_u + column prefix of M[.][u]
+    const uint32_t *Pc;     // [B*32]: every pstep-th entry of P[u] (coarse CDF)
+    int32_t pstep;          // ceil(2B / 32)
     const int32_t *dout, *din;
     const double *rcp;      // 1 / (dout_t + din_t + B)
     const float *rcp32;     // the same in FP32
@@ -104,6 +106,7 @@ struct sbp_model {
     int32_t *b = nullptr, *bnew = nullptr;
     int32_t *M = nullptr;
     uint32_t *P = nullptr;
+    uint32_t *Pc = nullptr;
     int32_t *dout = nullptr, *din = nullptr;
     double *rcp = nullptr;
     float *rcp32 = nullptr;
@@ -246,6 +249,27 @@ __device__ __forceinline__ int warp_upper_bound(const uint32_t *__restrict__ a, 
     const uint32_t val = lane < len ? a[lo + lane] : 0xffffffffu;
     const unsigned mask = __ballot_sync(0xffffffffu, val > t);
     return lo + __ffs(mask) - 1;
+}
+
+// first index i in Pu[0, len) with Pu[i] > t, given the 32 pivots
+// Pcu[q] = Pu[min((q+1) step - 1, len - 1)]: the pivots pick a segment of at
+// most `step` entries, searched with one more read while step <= 32
+__device__ __forceinline__ int warp_cdf_search(const uint32_t *__restrict__ Pu, const uint32_t *Pcu, int len, int step,
+                                               uint32_t t) {
+    const int lane = threadIdx.x & 31;
+    if (len <= 32) {
+        const uint32_t val = lane < len ? Pu[lane] : 0xffffffffu;
+        return __ffs(__ballot_sync(0xffffffffu, val > t)) - 1;
+    }
+    const uint32_t pv = Pcu[lane];
+    const int first = __ffs(__ballot_sync(0xffffffffu, pv > t)) - 1;
+    const int lo = first * step;
+    const int seg = step < len - lo ? step : len - lo;
+    if (seg <= 32) {
+        const uint32_t val = lane < seg ? Pu[lo + lane] : 0xffffffffu;
+        return lo + __ffs(__ballot_sync(0xffffffffu, val > t)) - 1;
+    }
+    return lo + warp_upper_bound(Pu + lo, seg, t);
 }
 
 // ---------------------------------------------------------------------------

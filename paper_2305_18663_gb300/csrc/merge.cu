@@ -34,7 +34,7 @@ __device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1
         return (int)(y + (y >= r));
     }
     const int64_t t0 = draw_below(w0, (uint64_t)dr);
-    int u = warp_upper_bound(Pr, 2 * B, (uint32_t)t0);
+    int u = warp_cdf_search(Pr, md.Pc + (size_t)r * 32, 2 * B, md.pstep, (uint32_t)t0);
     if (u >= B) u -= B;
     const int64_t Mur = Mat(md, u, r), Mru = Mat(md, r, u);
     const int64_t du_out = md.dout[u], du = du_out + md.din[u];

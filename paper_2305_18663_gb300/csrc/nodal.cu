@@ -28,6 +28,11 @@
 
 #include "common.cuh"
 
+// CTAs per SM the warp kernel is compiled for (register budget)
+#ifndef SBP_DECIDE_MIN_BLOCKS
+#define SBP_DECIDE_MIN_BLOCKS 3
+#endif
+
 namespace sbp {
 namespace {
 
@@ -69,8 +74,9 @@ struct VertexCtx {
 __device__ __forceinline__ void entry_fast(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, __int128 &dl,
                                            double &fb, float &pf, float &pb) {
     const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
-    if (ko) dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
-    if (ki) dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
+    // a zero count gives T[x] - T[x] = 0, so no branch is needed
+    dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
+    dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
     const float rc = md.rcp32[t];
     const float c = (float)(ko + ki);
     pf += c * (float)(Mts + Mst + 1) * rc;
@@ -87,56 +93,59 @@ __device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx 
     pb += c * (double)((Mtr - ki) + (Mrt - ko) + 1) / den;
 }
 
-// job j in 0..9: 0-3 cross entries (r,r) (s,s) (r,s) (s,r); 4-7 block degree
-// terms (subtracted); 8-9 Hastings terms of the neighbours in r and in s
-__device__ __forceinline__ void special_fast(const ModelDev &md, const VertexCtx &x, int j, __int128 &dl, double &fb,
-                                             float &pf, float &pb) {
+// Delta L terms of the 2x2 corner (j = 0..3: (r,r) (s,s) (r,s) (s,r)) and of
+// the block degrees (j = 4..7: dout_r dout_s din_r din_s, subtracted), one
+// per lane, selected without divergence.  Returns the count it read (lanes
+// 0..3 read the four corner entries of M).
+__device__ __forceinline__ int special_terms(const ModelDev &md, const VertexCtx &x, int j, __int128 &dl, double &fb) {
+    if (j >= 8) return 0;
     const int r = x.r, s = x.s, B = md.B;
-    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
-    switch (j) {
-        case 0: dl += dT(md.T, md.XT, Mat(md, r, r), -(cr + x.self), fb); break;
-        case 1: dl += dT(md.T, md.XT, Mat(md, s, s), cs + x.self, fb); break;
-        case 2: dl += dT(md.T, md.XT, Mat(md, r, s), x.ki_r - x.ko_s, fb); break;
-        case 3: dl += dT(md.T, md.XT, Mat(md, s, r), x.ko_r - x.ki_s, fb); break;
-        case 4: case 5: case 6: case 7: {
-            const int blk = (j == 4 || j == 6) ? r : s;
-            const int deg = j < 6 ? md.dout[blk] : md.din[blk];
-            const int kk = j < 6 ? x.Kout : x.Kin;
-            double f2 = 0.0;
-            dl -= dT(md.T, md.XT, deg, (j == 4 || j == 6) ? -kk : kk, f2);
-            fb -= f2;
-            break;
-        }
-        case 8: {
-            const int Mrr = Mat(md, r, r), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), dr = md.dsum[r];
-            pf += (float)(cr + 2 * x.self) * (float)(Mrs + Msr + 1) / (float)(dr + B);
-            pb += (float)cr * (float)(2 * (Mrr - cr - x.self) + 1) / (float)(dr - K + B);
-            break;
-        }
-        case 9: {
-            const int Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), ds = md.dsum[s];
-            pf += (float)cs * (float)(2 * Mss + 1) / (float)(ds + B);
-            pb += (float)(cs + 2 * x.self) * (float)((Msr + x.ko_r - x.ki_s) + (Mrs + x.ki_r - x.ko_s) + 1) /
-                  (float)(ds + K + B);
-            break;
-        }
-        default: break;
-    }
+    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s;
+    const int rowi = (j == 0 || j == 2) ? r : s;
+    const int coli = (j == 0 || j == 3) ? r : s;
+    const int blk = (j == 4 || j == 6) ? r : s;
+    const int *ptr = j < 4 ? md.M + (size_t)rowi * B + coli : (j < 6 ? md.dout + blk : md.din + blk);
+    const int kk = j == 0   ? -(cr + x.self)
+                   : j == 1 ? cs + x.self
+                   : j == 2 ? x.ki_r - x.ko_s
+                   : j == 3 ? x.ko_r - x.ki_s
+                   : j == 4 ? -x.Kout
+                   : j == 5 ? x.Kout
+                   : j == 6 ? -x.Kin
+                            : x.Kin;
+    const int val = *ptr;
+    double f2 = 0.0;
+    const __int128 d = dT(md.T, md.XT, val, kk, f2);
+    dl += j < 4 ? d : -d;
+    fb += j < 4 ? f2 : -f2;
+    return val;
 }
 
-__device__ __forceinline__ void special_exact(const ModelDev &md, const VertexCtx &x, int j, double &pf, double &pb) {
-    const int r = x.r, s = x.s, B = md.B;
-    const int64_t cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
-    if (j == 8) {
-        const int64_t Mrr = Mat(md, r, r), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), dr = md.dsum[r];
-        pf += (double)(cr + 2 * x.self) * (double)(Mrs + Msr + 1) / (double)(dr + B);
-        pb += (double)cr * (double)(2 * (Mrr - cr - x.self) + 1) / (double)(dr - K + B);
-    } else if (j == 9) {
-        const int64_t Mss = Mat(md, s, s), Mrs = Mat(md, r, s), Msr = Mat(md, s, r), ds = md.dsum[s];
-        pf += (double)cs * (double)(2 * Mss + 1) / (double)(ds + B);
-        pb += (double)(cs + 2 * x.self) * (double)((Msr + x.ko_r - x.ki_s) + (Mrs + x.ki_r - x.ko_s) + 1) /
-              (double)(ds + K + B);
-    }
+// Hastings terms of v's neighbours in r and in s (forward and backward),
+// from the corner entries and the block degrees; FP32 and FP64 versions.
+struct CornerVals {
+    int Mrr, Mss, Mrs, Msr, dr, ds;
+};
+
+__device__ __forceinline__ void corner_hastings_fast(const VertexCtx &x, const CornerVals &c, int B, float &pf,
+                                                     float &pb) {
+    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
+    pf += (float)(cr + 2 * x.self) * (float)(c.Mrs + c.Msr + 1) / (float)(c.dr + B);
+    pf += (float)cs * (float)(2 * c.Mss + 1) / (float)(c.ds + B);
+    pb += (float)cr * (float)(2 * (c.Mrr - cr - x.self) + 1) / (float)(c.dr - K + B);
+    pb += (float)(cs + 2 * x.self) * (float)((c.Msr + x.ko_r - x.ki_s) + (c.Mrs + x.ki_r - x.ko_s) + 1) /
+          (float)(c.ds + K + B);
+}
+
+__device__ __forceinline__ void corner_hastings_exact(const VertexCtx &x, const CornerVals &c, int B, double &pf,
+                                                      double &pb) {
+    const int64_t cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin, self = x.self;
+    pf += (double)(cr + 2 * self) * (double)((int64_t)c.Mrs + c.Msr + 1) / (double)((int64_t)c.dr + B);
+    pf += (double)cs * (double)(2 * (int64_t)c.Mss + 1) / (double)((int64_t)c.ds + B);
+    pb += (double)cr * (double)(2 * ((int64_t)c.Mrr - cr - self) + 1) / (double)((int64_t)c.dr - K + B);
+    pb += (double)(cs + 2 * self) *
+          (double)(((int64_t)c.Msr + x.ko_r - x.ki_s) + ((int64_t)c.Mrs + x.ki_r - x.ko_s) + 1) /
+          (double)((int64_t)c.ds + K + B);
 }
 
 // FP32 decision with its error band.  Returns 1 accept, 0 reject, -1 when
@@ -180,7 +189,7 @@ __device__ __forceinline__ int propose_block(const ModelDev &md, int u, uint64_t
     const int64_t du = md.dsum[u];
     const int64_t y = draw_below(w1, (uint64_t)(du + B));
     if (y < B) return (int)y;
-    const int idx = warp_upper_bound(md.P + (size_t)u * 2 * B, 2 * B, (uint32_t)(y - B));
+    const int idx = warp_cdf_search(md.P + (size_t)u * 2 * B, md.Pc + (size_t)u * 32, 2 * B, md.pstep, (uint32_t)(y - B));
     return idx < B ? idx : idx - B;
 }
 
@@ -242,9 +251,8 @@ __device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin
 // each_entry(f) calls f(t, ko, ki) for each entry the calling lane holds.
 // All 32 lanes call this; the result is written by lane 0.
 template <class EachEntry>
-__device__ __forceinline__ void evaluate_warp(const DecideArgs &a, VertexCtx &x, uint64_t w2, EachEntry each_entry,
-                                              Counts &c) {
-    const ModelDev &md = a.md;
+__device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
+                                              EachEntry each_entry, Counts &c) {
     const int lane = threadIdx.x & 31;
     // neighbours in r and in s (one lane holds each); 16-bit fields when
     // the degree allows it
@@ -278,10 +286,18 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, VertexCtx &x,
     each_entry([&](int t, int ko, int ki) {
         if (t != x.r && t != x.s) entry_fast(md, x, t, ko, ki, dl, fb, pf, pb);
     });
-    if (lane < 10) special_fast(md, x, lane, dl, fb, pf, pb);
+    const int val = special_terms(md, x, lane, dl, fb);
+    CornerVals cv;
+    cv.Mrr = __shfl_sync(0xffffffffu, val, 0);
+    cv.Mss = __shfl_sync(0xffffffffu, val, 1);
+    cv.Mrs = __shfl_sync(0xffffffffu, val, 2);
+    cv.Msr = __shfl_sync(0xffffffffu, val, 3);
+    cv.dr = md.dsum[x.r];
+    cv.ds = md.dsum[x.s];
     dl = warp_sum_128(dl);
     pf = warp_sum_f(pf);
     pb = warp_sum_f(pb);
+    corner_hastings_fast(x, cv, md.B, pf, pb);
     const bool has_fb = __any_sync(0xffffffffu, __double_as_longlong(fb) != 0);
     if (has_fb) fb = warp_sum(fb);
     const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
@@ -296,9 +312,9 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, VertexCtx &x,
     each_entry([&](int t, int ko, int ki) {
         if (t != x.r && t != x.s) entry_exact(md, x, t, ko, ki, pf64, pb64);
     });
-    special_exact(md, x, lane, pf64, pb64);
     pf64 = warp_sum(pf64);
     pb64 = warp_sum(pb64);
+    corner_hastings_exact(x, cv, md.B, pf64, pb64);
     if (lane == 0) {
         const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
         if (e.accept) md.bnew[x.v] = x.s;
@@ -316,16 +332,43 @@ __device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c
     }
 }
 
-// Per warp, in dynamic shared memory: cap int keys, cap 32-bit counts
-// (ko | ki << 16, so degrees stay below 65536), cap 16-bit list entries, one
-// list length.  Warps per CTA = blockDim.x / 32.
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs a, int cap, int cap_log2) {
+// Dynamic shared memory: optionally a copy of the per-block arrays (32
+// pivots, dsum, dout, din, rcp32 per block) when cache_blocks is set, then
+// per warp: cap int keys, cap 32-bit counts (ko | ki << 16, so degrees stay
+// below 65536), cap 16-bit list entries and one list length.  Warps per
+// CTA = blockDim.x / 32.  Each warp takes chunks of `chunk` consecutive
+// entries of the order list and prefetches their offsets and labels with
+// one lane per vertex.
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_decide_warp(DecideArgs a, int cap, int cap_log2,
+                                                                      int cache_blocks, int chunk) {
     extern __shared__ int dsm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    int *keys = dsm + (size_t)wid * cap;
-    unsigned *cnt = reinterpret_cast<unsigned *>(dsm + (size_t)nwarps * cap) + (size_t)wid * cap;
-    int *nlist = dsm + (size_t)2 * nwarps * cap + wid;
-    unsigned short *list = reinterpret_cast<unsigned short *>(dsm + (size_t)2 * nwarps * cap + nwarps) + (size_t)wid * cap;
+    ModelDev md = a.md;
+    int *base = dsm;
+    if (cache_blocks) {
+        const int B = md.B;
+        uint32_t *s_pc = reinterpret_cast<uint32_t *>(base);
+        int *s_dsum = base + 32 * B, *s_dout = s_dsum + B, *s_din = s_dout + B;
+        float *s_rcp = reinterpret_cast<float *>(s_din + B);
+        for (int i = threadIdx.x; i < 32 * B; i += blockDim.x) s_pc[i] = a.md.Pc[i];
+        for (int i = threadIdx.x; i < B; i += blockDim.x) {
+            s_dsum[i] = a.md.dsum[i];
+            s_dout[i] = a.md.dout[i];
+            s_din[i] = a.md.din[i];
+            s_rcp[i] = a.md.rcp32[i];
+        }
+        __syncthreads();
+        md.Pc = s_pc;
+        md.dsum = s_dsum;
+        md.dout = s_dout;
+        md.din = s_din;
+        md.rcp32 = s_rcp;
+        base += 36 * B;
+    }
+    int *keys = base + (size_t)wid * cap;
+    unsigned *cnt = reinterpret_cast<unsigned *>(base + (size_t)nwarps * cap) + (size_t)wid * cap;
+    int *nlist = base + (size_t)2 * nwarps * cap + wid;
+    unsigned short *list = reinterpret_cast<unsigned short *>(base + (size_t)2 * nwarps * cap + nwarps) + (size_t)wid * cap;
     for (int i = lane; i < cap; i += 32) {
         keys[i] = -1;
         cnt[i] = 0;
@@ -334,22 +377,41 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs
     __syncwarp();
 
     const GraphDev &g = a.g;
-    const ModelDev &md = a.md;
     Counts c;
     const int64_t nw = (int64_t)gridDim.x * nwarps;
-    for (int64_t i = a.lo + (int64_t)blockIdx.x * nwarps + wid; i < a.hi; i += nw) {
-        const int v = a.order[i];
+    const int64_t nchunk = (a.hi - a.lo + chunk - 1) / chunk;
+    for (int64_t ch = (int64_t)blockIdx.x * nwarps + wid; ch < nchunk; ch += nw) {
+        const int64_t first = a.lo + ch * chunk;
+        const int cnt_v = (int)(a.hi - first < chunk ? a.hi - first : chunk);
+        int pv = 0, pr = 0, po = 0, pko = 0, pi = 0, pki = 0;
+        uint64_t pw0 = 0, pw1 = 0, pw2 = 0;
+        if (lane < cnt_v) {
+            pv = a.order[first + lane];
+            pr = md.b[pv];
+            po = g.op[pv];
+            pko = g.op[pv + 1] - po;
+            pi = g.ip[pv];
+            pki = g.ip[pv + 1] - pi;
+            // one lane per vertex draws that vertex's Philox block
+            const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)pv, 0, 0, a.seed, 0);
+            pw0 = w.x;
+            pw1 = w.y;
+            pw2 = w.z;
+        }
+        for (int q = 0; q < cnt_v; ++q) {
+        const int v = __shfl_sync(0xffffffffu, pv, q);
         if (v < a.v_begin || v >= a.v_end) continue;
-        const int r = md.b[v];
-        const int o0 = g.op[v], kout = g.op[v + 1] - o0;
-        const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
+        const int r = __shfl_sync(0xffffffffu, pr, q);
+        const int o0 = __shfl_sync(0xffffffffu, po, q), kout = __shfl_sync(0xffffffffu, pko, q);
+        const int i0 = __shfl_sync(0xffffffffu, pi, q), kin = __shfl_sync(0xffffffffu, pki, q);
         const int k = kout + kin;
         if (k == 0) {
             if (lane == 0) write_trace(a, v, r, 0, 0.0, 0.0);
             continue;
         }
-        const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
-        const int j = (int)draw_below(w.x, (uint64_t)k);
+        const uint64_t w0 = __shfl_sync(0xffffffffu, pw0, q), w1 = __shfl_sync(0xffffffffu, pw1, q);
+        const uint64_t w2 = __shfl_sync(0xffffffffu, pw2, q);
+        const int j = (int)draw_below(w0, (uint64_t)k);
 
         int self = 0, u = r, D = 0;
         int my_t = -1, my_ko = 0, my_ki = 0;
@@ -369,29 +431,41 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs
                 my_ki = __popc(peers) - my_ko;
             }
         } else {
+            // four 32-neighbour chunks per round: their loads are in flight together
             bool ok = true;
-            for (int base = 0; base < k; base += 32) {
-                const int idx = base + lane;
-                const bool valid = idx < k, is_out = idx < kout;
-                const int nb = valid ? (is_out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
-                const int tb = valid ? md.b[nb] : -1;
-                if (j >= base && j < base + 32) u = __shfl_sync(0xffffffffu, tb, j - base);
-                const bool is_self = valid && nb == v;
-                self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
-                const int key = (valid && !is_self) ? tb : -1;
-                const unsigned peers = __match_any_sync(0xffffffffu, key);
-                const unsigned outm = __ballot_sync(0xffffffffu, valid && !is_self && is_out);
-                if (key >= 0 && lane == __ffs(peers) - 1) {
-                    const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                    ok &= table_add32(keys, cnt, list, nlist, cap, cap_log2, key, ko | (ki << 16));
+            for (int base = 0; base < k; base += 128) {
+                int nb[4], tb[4];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int idx = base + c4 * 32 + lane;
+                    nb[c4] = idx < k ? (idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
                 }
-                __syncwarp();
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) tb[c4] = nb[c4] >= 0 ? md.b[nb[c4]] : -1;
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int cb = base + c4 * 32;
+                    if (cb >= k) break;
+                    const int idx = cb + lane;
+                    const bool valid = idx < k, is_out = idx < kout;
+                    if (j >= cb && j < cb + 32) u = __shfl_sync(0xffffffffu, tb[c4], j - cb);
+                    const bool is_self = valid && nb[c4] == v;
+                    self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
+                    const int key = (valid && !is_self) ? tb[c4] : -1;
+                    const unsigned peers = __match_any_sync(0xffffffffu, key);
+                    const unsigned outm = __ballot_sync(0xffffffffu, valid && !is_self && is_out);
+                    if (key >= 0 && lane == __ffs(peers) - 1) {
+                        const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
+                        ok &= table_add32(keys, cnt, list, nlist, cap, cap_log2, key, ko | (ki << 16));
+                    }
+                    __syncwarp();
+                }
             }
             if (!ok) record_status(md.status, SBP_EHASHFULL);
             D = *nlist;
         }
 
-        const int s = propose_block(md, u, w.y);
+        const int s = propose_block(md, u, w1);
         if (s == r) {
             if (lane == 0) {
                 c.proposed++;
@@ -402,11 +476,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs
             x.v = v; x.r = r; x.s = s;
             x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
             if (k <= kSmallDeg) {
-                evaluate_warp(a, x, w.z, [&](auto &&f) {
+                evaluate_warp(a, md, x, w2, [&](auto &&f) {
                     if (my_t >= 0) f(my_t, my_ko, my_ki);
                 }, c);
             } else {
-                evaluate_warp(a, x, w.z, [&](auto &&f) {
+                evaluate_warp(a, md, x, w2, [&](auto &&f) {
                     for (int e = lane; e < D; e += 32) {
                         const int slot = list[e];
                         const unsigned cc = cnt[slot];
@@ -425,6 +499,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3) k_decide_warp(DecideArgs
             __syncwarp();
             if (lane == 0) *nlist = 0;
             __syncwarp();
+        }
         }
     }
     if (lane == 0) flush_counts(md, c);
@@ -528,7 +603,7 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
                 const unsigned long long cc = cnt[slot];
                 if (t != r && t != s) entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
             }
-            if (tid < 10) special_fast(md, x, tid, dl, fb, pf, pb);
+            if (tid < 32) special_terms(md, x, tid, dl, fb);
             dl = warp_sum_128(dl);
             pf = warp_sum_f(pf);
             pb = warp_sum_f(pb);
@@ -552,6 +627,14 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
                 }
                 sh.dl_tot = dlt;
                 sh.fb_tot = fbt;
+                CornerVals cv;
+                cv.Mrr = Mat(md, r, r);
+                cv.Mss = Mat(md, s, s);
+                cv.Mrs = Mat(md, r, s);
+                cv.Msr = Mat(md, s, r);
+                cv.dr = md.dsum[r];
+                cv.ds = md.dsum[s];
+                corner_hastings_fast(x, cv, md.B, pft, pbt);
                 const bool has_fb = __double_as_longlong(fbt) != 0;
                 const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dlt, has_fb, fbt, pft, pbt, w.z, k);
                 sh.dec = dec;
@@ -569,7 +652,6 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
                     const unsigned long long cc = cnt[slot];
                     if (t != r && t != s) entry_exact(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), pf64, pb64);
                 }
-                special_exact(md, x, tid, pf64, pb64);
                 pf64 = warp_sum(pf64);
                 pb64 = warp_sum(pb64);
                 if (lane == 0) {
@@ -583,6 +665,14 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
                         pft += sh.pf64[q];
                         pbt += sh.pb64[q];
                     }
+                    CornerVals cv;
+                    cv.Mrr = Mat(md, r, r);
+                    cv.Mss = Mat(md, s, s);
+                    cv.Mrs = Mat(md, r, s);
+                    cv.Msr = Mat(md, s, r);
+                    cv.dr = md.dsum[r];
+                    cv.ds = md.dsum[s];
+                    corner_hastings_exact(x, cv, md.B, pft, pbt);
                     const Exact e = exact_decision(a.beta, sh.dl_tot, sh.fb_tot, pft, pbt, w.z);
                     if (e.accept) md.bnew[v] = s;
                     count_result(c, e.accept, e.margin);
@@ -627,6 +717,8 @@ ModelDev model_dev(sbp_model *m) {
     d.bnew = m->bnew;
     d.M = m->M;
     d.P = m->P;
+    d.Pc = m->Pc;
+    d.pstep = (2 * m->B + 31) / 32;
     d.dout = m->dout;
     d.din = m->din;
     d.rcp = m->rcp;
@@ -656,17 +748,20 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     const int sms = sm_count();
 
     auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
-    // k <= kWarpDeg (and k = 0 when a trace is requested): 256-slot tables
+    const int B = m->B;
+    // k <= kWarpDeg (and k = 0 when a trace is requested): 256-slot tables;
+    // the per-block arrays are copied to shared memory while they are small
     a.lo = a.trace_on ? g->bin[0] : g->bin[1];
     a.hi = g->bin[3];
     if (a.hi > a.lo) {
-        const int64_t warps = a.hi - a.lo;
-        int64_t blocks = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
+        const int cache = B <= 448 ? 1 : 0;
+        const size_t smem = warp_smem(kWarpCap, kWarpsPerCta) + (cache ? (size_t)36 * B * 4 : 0);
+        const int64_t chunks = (a.hi - a.lo + 31) / 32;
+        int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
         if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
         // the attribute is per function: set it for this launch's size
-        const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
         SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a, kWarpCap, 8);
+        k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a, kWarpCap, 8, cache, 32);
         SBP_CUDA(cudaGetLastError());
     }
     // k > kWarpDeg: per-warp tables sized for min(max degree, B) distinct
@@ -684,7 +779,7 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
             SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int64_t blocks = (a.hi - a.lo + nwarps - 1) / nwarps;
             if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
-            k_decide_warp<<<(int)blocks, nwarps * 32, smem, m->stream>>>(a, cap, cap_log2);
+            k_decide_warp<<<(int)blocks, nwarps * 32, smem, m->stream>>>(a, cap, cap_log2, 0, 1);
             SBP_CUDA(cudaGetLastError());
         } else {
             const size_t smem = (size_t)cap * (8 + 4 + 4);
