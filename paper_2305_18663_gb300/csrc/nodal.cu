@@ -150,11 +150,10 @@ __device__ __forceinline__ void corner_hastings_exact(const VertexCtx &x, const 
 
 // FP32 decision with its error band.  Returns 1 accept, 0 reject, -1 when
 // the band does not settle it (FP64 needed).
-__device__ __forceinline__ int fast_decision(float b32, __int128 dl, bool has_fb, double fb, float pf, float pb,
-                                             uint64_t w2, int k) {
+__device__ __forceinline__ int fast_decision_f(float b32, float dl32, float fb32, float pf, float pb, uint64_t w2,
+                                               int k) {
     const uint64_t um = w2 >> 11;
     if (um == 0) return 1;  // u = 0: ln u = -inf
-    const float dl32 = fix_to_float(dl), fb32 = has_fb ? (float)fb : 0.0f;
     const float lnpf = logf(pf), lnpb = logf(pb);
     const float logA = b32 * (dl32 + fb32) + (lnpb - lnpf);
     const float u32 = fmaf((float)(unsigned)(um >> 21), 0x1p-32f, (float)(unsigned)(um & 0x1fffffu) * 0x1p-53f);
@@ -167,20 +166,29 @@ __device__ __forceinline__ int fast_decision(float b32, __int128 dl, bool has_fb
     return diff > 0.0f ? 1 : 0;
 }
 
+__device__ __forceinline__ int fast_decision(float b32, __int128 dl, bool has_fb, double fb, float pf, float pb,
+                                             uint64_t w2, int k) {
+    return fast_decision_f(b32, fix_to_float(dl), has_fb ? (float)fb : 0.0f, pf, pb, w2, k);
+}
+
 struct Exact {
     double dH, logA;
     bool accept, margin;
 };
 
-__device__ __noinline__ Exact exact_decision(double beta, __int128 dl, double fb, double pf, double pb, uint64_t w2) {
+// the FP64 test: logA = -beta dDL + ln p_bwd - ln p_fwd, accept iff ln u < logA
+__device__ __noinline__ Exact exact_decision_d(double beta, double dL, double pf, double pb, uint64_t w2) {
     Exact e;
-    const double dL = fix_to_double(dl) + fb;
     e.dH = -dL;
     e.logA = -beta * e.dH + log(pb) - log(pf);
     const double lnu = log((double)(w2 >> 11) * 0x1p-53);
     e.accept = lnu < e.logA;
     e.margin = fabs(lnu - e.logA) <= 1e-9 * fmax(fabs(e.logA), 1.0);
     return e;
+}
+
+__device__ __forceinline__ Exact exact_decision(double beta, __int128 dl, double fb, double pf, double pb, uint64_t w2) {
+    return exact_decision_d(beta, fix_to_double(dl) + fb, pf, pb, w2);
 }
 
 // s from u: y < B picks s = y, else the inverse CDF over row u then column u
@@ -695,6 +703,314 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
     if (tid == 0) flush_counts(md, c);
 }
 
+// ---------------------------------------------------------------------------
+// batches of 32 vertices with 1 <= k <= 32 per warp
+//
+// Phases per batch (lane q <-> vertex q of the batch):
+//   P1 lane per vertex: offsets, labels, Philox; exclusive prefix of k;
+//   P2 edge parallel over the batch's concatenated rows (four 32-wide
+//      chunks in flight): neighbour ids and their blocks into shared memory;
+//   P3 per vertex, warp wide: match/ballot aggregation of its row into
+//      (q, t, kout, kin) entries, compacted in place;
+//   P4 lane per vertex: proposal s from u by the CDF search;
+//   P5 entry parallel: Delta L (128-bit table sums, accumulated per vertex in
+//      64-bit fixed point at 2^-48, exact integer adds) and FP32 Hastings
+//      terms, shared-memory atomics per vertex;
+//   P6 lane per vertex: corner and degree terms, FP32 test with its band, the
+//      FP64 recheck (sequential over the vertex's entries) when needed.
+// Scalar work is spread over the lanes instead of repeated by all 32.
+
+constexpr int kBatchEdges = 32 * kSmallDeg;
+
+struct BatchWarp {
+    int key[kBatchEdges];  // edge ends: (t << 1) | in, -2 out self-loop, -1 in self-loop; then entries
+    int r[32], s[32], rsr[32], rss[32], hasfb[32];
+    unsigned long long dl[32];  // Delta L, fixed point 2^-48
+    float pf[32], pb[32];
+    double fb[32];
+};
+
+// entry: q (5 bits) | ko (6) | ki (6) | t (15)
+__device__ __forceinline__ unsigned pack_entry(int q, int t, int ko, int ki) {
+    return ((unsigned)q << 27) | ((unsigned)ko << 21) | ((unsigned)ki << 15) | (unsigned)t;
+}
+
+// first index i in Pu[0, len) with Pu[i] > t, searched by one lane: the 32
+// pivots with vector loads, then the segment (all loads issued together
+// while it is at most 32 long)
+__device__ __forceinline__ int lane_cdf_search(const uint32_t *__restrict__ Pu, const uint32_t *__restrict__ Pcu, int len,
+                                               int step, uint32_t t) {
+    int lo = 0, seg = len;
+    if (len > 32) {
+        uint4 pv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pv[i] = reinterpret_cast<const uint4 *>(Pcu)[i];
+        int fp = 31;
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
+            if (pv[i].w > t) fp = 4 * i + 3;
+            if (pv[i].z > t) fp = 4 * i + 2;
+            if (pv[i].y > t) fp = 4 * i + 1;
+            if (pv[i].x > t) fp = 4 * i;
+        }
+        lo = fp * step;
+        seg = step < len - lo ? step : len - lo;
+    }
+    if (seg <= 32) {
+        // eight loads in flight per group
+        for (int g0 = 0; g0 < seg; g0 += 8) {
+            uint32_t x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = g0 + i < seg ? Pu[lo + g0 + i] : 0xffffffffu;
+            int idx = -1;
+#pragma unroll
+            for (int i = 7; i >= 0; --i)
+                if (x[i] > t) idx = i;
+            if (idx >= 0) return lo + g0 + idx;
+        }
+        return lo + seg - 1;
+    }
+    int n = seg;
+    while (n > 0) {
+        const int half = n >> 1;
+        if (Pu[lo + half] <= t) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float fix48_to_float(long long v) {
+    return fmaf((float)(int)(v >> 32), 0x1p-16f, (float)(unsigned)(v & 0xffffffffu) * 0x1p-48f);
+}
+__device__ __forceinline__ double fix48_to_double(long long v) {
+    return (double)(int)(v >> 32) * 0x1p-16 + (double)(unsigned)(v & 0xffffffffu) * 0x1p-48;
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_decide_batch(DecideArgs a) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    BatchWarp &W = reinterpret_cast<BatchWarp *>(bsm)[wid];
+    const GraphDev &g = a.g;
+    const ModelDev &md = a.md;
+    const int B = md.B;
+    Counts c;
+    const int64_t nbatch = (a.hi - a.lo + 31) >> 5;
+    for (int64_t bt = (int64_t)blockIdx.x * nwarps + wid; bt < nbatch; bt += (int64_t)gridDim.x * nwarps) {
+        const int64_t first_i = a.lo + (bt << 5);
+        const int nv = (int)(a.hi - first_i < 32 ? a.hi - first_i : 32);
+        // ---- P1
+        int v = 0, r = 0, o0 = 0, kout = 0, i0 = 0, kin = 0, k = 0, j = 0;
+        uint64_t w1 = 0, w2 = 0;
+        if (lane < nv) {
+            v = a.order[first_i + lane];
+            if (v >= a.v_begin && v < a.v_end) {
+                r = md.b[v];
+                o0 = g.op[v];
+                kout = g.op[v + 1] - o0;
+                i0 = g.ip[v];
+                kin = g.ip[v + 1] - i0;
+                k = kout + kin;
+                const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
+                j = (int)draw_below(w.x, (uint64_t)k);
+                w1 = w.y;
+                w2 = w.z;
+            }
+        }
+        int incl = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int first = incl - k;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        // ---- P2
+        for (int base = 0; base < total; base += 128) {
+            int nb[4], vq[4], eo[4];
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const int p = base + c4 * 32 + lane;
+                int q = 0;
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const int f = __shfl_sync(0xffffffffu, first, q + st);
+                    if (f <= p) q += st;
+                }
+                const int fq = __shfl_sync(0xffffffffu, first, q);
+                const int kq = __shfl_sync(0xffffffffu, kout, q);
+                const int oq = __shfl_sync(0xffffffffu, o0, q);
+                const int iq = __shfl_sync(0xffffffffu, i0, q);
+                vq[c4] = __shfl_sync(0xffffffffu, v, q);
+                const int e = p - fq;
+                eo[c4] = e < kq ? 1 : 0;
+                nb[c4] = p < total ? (e < kq ? g.oc[oq + e] : g.ic[iq + e - kq]) : -1;
+            }
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const int p = base + c4 * 32 + lane;
+                if (nb[c4] >= 0) {
+                    const int t = md.b[nb[c4]];
+                    W.key[p] = nb[c4] == vq[c4] ? (eo[c4] ? -2 : -1) : ((t << 1) | (eo[c4] ? 0 : 1));
+                }
+            }
+        }
+        __syncwarp();
+        // ---- P3
+        int nent = 0, my_u = r, my_self = 0, my_est = 0, my_ecnt = 0;
+        for (int q = 0; q < nv; ++q) {
+            const int kq = __shfl_sync(0xffffffffu, k, q);
+            if (kq == 0) continue;
+            const int fq = __shfl_sync(0xffffffffu, first, q);
+            const int jq = __shfl_sync(0xffffffffu, j, q);
+            const int rq = __shfl_sync(0xffffffffu, r, q);
+            const int x = lane < kq ? W.key[fq + lane] : -3;
+            const int t = x >= 0 ? (x >> 1) : -1;
+            const bool in = x >= 0 && (x & 1);
+            const int uq = __shfl_sync(0xffffffffu, x >= 0 ? t : rq, jq);
+            const int selfq = __popc(__ballot_sync(0xffffffffu, x == -2));
+            const unsigned peers = __match_any_sync(0xffffffffu, t);
+            const unsigned outm = __ballot_sync(0xffffffffu, t >= 0 && !in);
+            const bool leader = t >= 0 && lane == __ffs(peers) - 1;
+            const unsigned lm = __ballot_sync(0xffffffffu, leader);
+            if (leader) {
+                const int ko = __popc(peers & outm), ki = __popc(peers) - ko;
+                W.key[nent + __popc(lm & ((1u << lane) - 1u))] = (int)pack_entry(q, t, ko, ki);
+            }
+            if (lane == q) {
+                my_u = uq;
+                my_self = selfq;
+                my_est = nent;
+                my_ecnt = __popc(lm);
+            }
+            nent += __popc(lm);
+        }
+        // ---- P4
+        int s = r;
+        if (k > 0) {
+            const int64_t du = md.dsum[my_u];
+            const int64_t y = draw_below(w1, (uint64_t)(du + B));
+            if (y < B) {
+                s = (int)y;
+            } else {
+                const int idx = lane_cdf_search(md.P + (size_t)my_u * 2 * B, md.Pc + (size_t)my_u * 32, 2 * B, md.pstep,
+                                                (uint32_t)(y - B));
+                s = idx < B ? idx : idx - B;
+            }
+        }
+        const bool move = k > 0 && s != r;
+        W.r[lane] = r;
+        W.s[lane] = move ? s : -1;
+        W.rsr[lane] = 0;
+        W.rss[lane] = 0;
+        W.hasfb[lane] = 0;
+        W.dl[lane] = 0ull;
+        W.pf[lane] = 0.0f;
+        W.pb[lane] = 0.0f;
+        W.fb[lane] = 0.0;
+        __syncwarp();
+        // ---- P5
+        for (int e = lane; e < nent; e += 32) {
+            const unsigned ent = (unsigned)W.key[e];
+            const int q = (int)(ent >> 27), t = (int)(ent & 0x7fffu);
+            const int ko = (int)((ent >> 21) & 63u), ki = (int)((ent >> 15) & 63u);
+            const int sq = W.s[q];
+            if (sq < 0) continue;
+            const int rq = W.r[q];
+            if (t == rq) {
+                W.rsr[q] = ko | (ki << 8);
+                continue;
+            }
+            if (t == sq) {
+                W.rss[q] = ko | (ki << 8);
+                continue;
+            }
+            VertexCtx x;
+            x.r = rq;
+            x.s = sq;
+            __int128 d = 0;
+            double f = 0.0;
+            float pfe = 0.0f, pbe = 0.0f;
+            entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
+            atomicAdd(&W.dl[q], (unsigned long long)(long long)(d >> 16));
+            atomicAdd(&W.pf[q], pfe);
+            atomicAdd(&W.pb[q], pbe);
+            if (__double_as_longlong(f) != 0) {
+                atomicAdd(&W.fb[q], f);
+                W.hasfb[q] = 1;
+            }
+        }
+        __syncwarp();
+        // ---- P6
+        if (k > 0 && !move) {
+            c.proposed++;
+            write_trace(a, v, r, 1, 0.0, 0.0);
+        }
+        if (move) {
+            VertexCtx x;
+            x.v = v; x.r = r; x.s = s;
+            x.Kout = kout; x.Kin = kin; x.self = my_self; x.k = k;
+            const int rsr = W.rsr[lane], rss = W.rss[lane];
+            x.ko_r = rsr & 0xff; x.ki_r = rsr >> 8;
+            x.ko_s = rss & 0xff; x.ki_s = rss >> 8;
+            __int128 d = 0;
+            double fb = W.hasfb[lane] ? W.fb[lane] : 0.0;
+            bool has_fb = W.hasfb[lane] != 0;
+            CornerVals cv;
+            cv.Mrr = special_terms(md, x, 0, d, fb);
+            cv.Mss = special_terms(md, x, 1, d, fb);
+            cv.Mrs = special_terms(md, x, 2, d, fb);
+            cv.Msr = special_terms(md, x, 3, d, fb);
+#pragma unroll
+            for (int jj = 4; jj < 8; ++jj) special_terms(md, x, jj, d, fb);
+            has_fb = has_fb || __double_as_longlong(fb) != 0;
+            cv.dr = md.dsum[r];
+            cv.ds = md.dsum[s];
+            const long long dl48 = (long long)W.dl[lane] + (long long)(d >> 16);
+            float pf = W.pf[lane], pb = W.pb[lane];
+            corner_hastings_fast(x, cv, B, pf, pb);
+            const int dec = a.trace_on ? -1
+                                       : fast_decision_f(a.beta32, fix48_to_float(dl48), has_fb ? (float)fb : 0.0f, pf, pb,
+                                                         w2, k);
+            if (dec >= 0) {
+                if (dec) md.bnew[v] = s;
+                count_result(c, dec != 0, false);
+            } else {
+                double pf64 = 0.0, pb64 = 0.0;
+                for (int e = my_est; e < my_est + my_ecnt; ++e) {
+                    const unsigned ent = (unsigned)W.key[e];
+                    const int t = (int)(ent & 0x7fffu);
+                    if (t == r || t == s) continue;
+                    entry_exact(md, x, t, (int)((ent >> 21) & 63u), (int)((ent >> 15) & 63u), pf64, pb64);
+                }
+                corner_hastings_exact(x, cv, B, pf64, pb64);
+                const Exact ex = exact_decision_d(a.beta, fix48_to_double(dl48) + (has_fb ? fb : 0.0), pf64, pb64, w2);
+                if (ex.accept) md.bnew[v] = s;
+                count_result(c, ex.accept, ex.margin);
+                write_trace(a, v, s, 1 | (ex.accept ? 2 : 0) | (ex.margin ? 4 : 0), ex.dH, ex.logA);
+            }
+        }
+        __syncwarp();
+    }
+    // warp-sum the counters, one atomic per warp
+    unsigned long long cp = c.proposed, cm = c.moves, ca = c.accepted, cg = c.margin;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cp += __shfl_xor_sync(0xffffffffu, cp, o);
+        cm += __shfl_xor_sync(0xffffffffu, cm, o);
+        ca += __shfl_xor_sync(0xffffffffu, ca, o);
+        cg += __shfl_xor_sync(0xffffffffu, cg, o);
+    }
+    if (lane == 0) {
+        Counts t;
+        t.proposed = cp; t.moves = cm; t.accepted = ca; t.margin = cg;
+        flush_counts(md, t);
+    }
+}
+
 int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -749,19 +1065,35 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
 
     auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
     const int B = m->B;
-    // k <= kWarpDeg (and k = 0 when a trace is requested): 256-slot tables;
-    // the per-block arrays are copied to shared memory while they are small
-    a.lo = a.trace_on ? g->bin[0] : g->bin[1];
-    a.hi = g->bin[3];
-    if (a.hi > a.lo) {
+    // k = 0 (trace only) and 33 <= k <= kWarpDeg: warp per vertex, 256-slot
+    // tables; the per-block arrays are copied to shared memory while small
+    {
         const int cache = B <= 448 ? 1 : 0;
         const size_t smem = warp_smem(kWarpCap, kWarpsPerCta) + (cache ? (size_t)36 * B * 4 : 0);
-        const int64_t chunks = (a.hi - a.lo + 31) / 32;
-        int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
-        if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
-        // the attribute is per function: set it for this launch's size
         SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a, kWarpCap, 8, cache, 32);
+        const int64_t ranges[2][2] = {{g->bin[0], a.trace_on ? g->bin[1] : g->bin[0]}, {g->bin[2], g->bin[3]}};
+        for (int rg = 0; rg < 2; ++rg) {
+            a.lo = ranges[rg][0];
+            a.hi = ranges[rg][1];
+            if (a.hi <= a.lo) continue;
+            const int64_t chunks = (a.hi - a.lo + 31) / 32;
+            int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+            if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
+            k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a, kWarpCap, 8, cache, 32);
+            SBP_CUDA(cudaGetLastError());
+        }
+    }
+    // 1 <= k <= 32: batches of 32 vertices per warp (the dense t < 2^15 fits
+    // the packed entries)
+    a.lo = g->bin[1];
+    a.hi = g->bin[2];
+    if (a.hi > a.lo) {
+        const size_t smem = sizeof(BatchWarp) * kWarpsPerCta;
+        SBP_CUDA(cudaFuncSetAttribute(k_decide_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t batches = (a.hi - a.lo + 31) / 32;
+        int64_t blocks = (batches + kWarpsPerCta - 1) / kWarpsPerCta;
+        if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
+        k_decide_batch<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a);
         SBP_CUDA(cudaGetLastError());
     }
     // k > kWarpDeg: per-warp tables sized for min(max degree, B) distinct
