@@ -107,13 +107,15 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-def algorithmic_bytes(n, m, B):
+def algorithmic_bytes(n, m, B, move_edges):
     """Per-sweep bytes the method has to move (each gather at its element
-    size): decide = offsets 8(N+1) + adjacency 8E + block gathers 8E + b read
-    and b_new write 8N; rebuild = adjacency 4E + gathers 8E (both ends) +
-    edge sources 4E + zeroing and prefix of M 12 B^2.  Blockmodel lookups
-    (L2-resident at this B) are not counted."""
-    decide = 8 * (n + 1) + 8 * m + 8 * m + 8 * n
+    size).  Decide: offsets 8(N+1), labels 4N, the proposal's edge and its
+    block 8N, and for the vertices whose proposal differs from their block
+    their rows and the blocks at the far ends, 8 per edge end.  Rebuild:
+    adjacency 4E + gathers 8E (both ends) + edge sources 4E + zeroing and
+    prefix of M 12 B^2.  Blockmodel lookups (L2-resident at this B) are not
+    counted."""
+    decide = 8 * (n + 1) + 12 * n + 8 * move_edges
     rebuild = 4 * m + 8 * m + 4 * m + 12 * B * B
     return decide, rebuild
 
@@ -200,7 +202,7 @@ def run_ours(args, rank, world, local_rank):
     res = None
     if rank == 0:
         hbm, hbm_kind = peaks()
-        dec_b, reb_b = algorithmic_bytes(g.n, g.m, B)
+        dec_b, reb_b = algorithmic_bytes(g.n, g.m, B, st.n_move_edges)
         dec_avg = statistics.mean(decide_ms)
         achieved = dec_b / (dec_avg * 1e-3) / 1e9
         ms_step = total_ms / args.steps
@@ -223,7 +225,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": g.n * e2e_steps * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * g.n, "d2h_bytes_per_step": 4 * g.n + 48},
             "gpu_launches": 6 * args.steps,
-            "roofline": {"kernel": "nodal decide pass (k_decide_warp + k_decide_cta)", "bound": "hbm",
+            "roofline": {"kernel": "nodal decide pass (k_propose, k_eval_batch, k_eval_warp, k_eval_cta)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_kind": hbm_kind, "algorithmic_bytes": dec_b, "traffic": None},
             "breakdown_ms": {"decide": dec_avg, "commit": statistics.mean(commit_ms),

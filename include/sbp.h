@@ -76,12 +76,15 @@ typedef struct sbp_params {
  * n_accepted: moves taken; n_margin: proposals whose log acceptance ratio
  * lies within 1e-9 * max(|logA|, 1) of log(u) (decided, and reported so a
  * comparison with another FP64 implementation can excuse them);
- * dl_before / dl_after: DL (Eq. 2) before and after the rebuild. */
+ * n_move_edges: sum of the degrees of the vertices with s != current block
+ * (the rows the pass had to aggregate); dl_before / dl_after: DL (Eq. 2)
+ * before and after the rebuild. */
 typedef struct sbp_sweep_stats {
     int64_t n_proposed;
     int64_t n_moves;
     int64_t n_accepted;
     int64_t n_margin;
+    int64_t n_move_edges;
     double dl_before;
     double dl_after;
 } sbp_sweep_stats;

@@ -66,6 +66,7 @@ class SweepStats(C.Structure):
         ("n_moves", C.c_int64),
         ("n_accepted", C.c_int64),
         ("n_margin", C.c_int64),
+        ("n_move_edges", C.c_int64),
         ("dl_before", C.c_double),
         ("dl_after", C.c_double),
     ]

@@ -85,6 +85,7 @@ int read_stats(sbp_model *m, sbp_sweep_stats *out) {
     out->n_moves = (int64_t)h->c.moves;
     out->n_accepted = (int64_t)h->c.accepted;
     out->n_margin = (int64_t)h->c.margin;
+    out->n_move_edges = (int64_t)h->c.move_edges;
     out->dl_after = h->dl[0];
     out->dl_before = h->dl[1];
     return SBP_OK;
@@ -203,6 +204,8 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     cudaFree(m->best_d);
     cudaFree(m->map);
     cudaFree(m->vcount);
+    cudaFree(m->movers);
+    cudaFree(m->mcount);
     cudaFreeHost(m->pinned);
     delete m;
 }

@@ -73,7 +73,7 @@ namespace sbp {
 
 // device-side counters of a decision pass: proposed, moves, accepted, margin
 struct DevCounters {
-    unsigned long long proposed, moves, accepted, margin;
+    unsigned long long proposed, moves, accepted, margin, move_edges;
 };
 
 struct ModelDev {
@@ -123,6 +123,9 @@ struct sbp_model {
     double *best_d = nullptr;
     int32_t *map = nullptr;
     int32_t *vcount = nullptr;
+    // nodal pass: proposals with s != r, in three lists by degree
+    void *movers = nullptr;
+    unsigned *mcount = nullptr;
     // pinned host mirror for small read-backs
     void *pinned = nullptr;
     bool dense = true;

@@ -22,8 +22,11 @@
 //
 // GB300 executes one FP64 warp instruction per ~20 SM cycles, so the FP64
 // work is kept off the common path and spread across lanes when it runs.
-// Work units: one lane per neighbour for k <= 32; one warp per vertex with
-// a per-warp table for k <= 128; one CTA per vertex above that.
+// Kernels: k_propose (one lane per vertex) draws every proposal and sends
+// those with s != r to three lists by degree; k_eval_batch (32 movers per
+// warp, k <= 32), k_eval_warp (one warp per mover with a shared-memory
+// table) and k_eval_cta (one CTA per mover, very large tables) aggregate
+// the rows of the movers only and run the test.
 #include <cmath>
 
 #include "common.cuh"
@@ -36,12 +39,19 @@
 namespace sbp {
 namespace {
 
+// A proposal with s != b[v] that still needs its Delta DL and test.
+struct Mover {
+    int v, s;
+    unsigned long long w2;  // the Philox word of the acceptance draw
+};
+
 struct DecideArgs {
     GraphDev g;
     ModelDev md;
-    const int32_t *order;
-    int64_t lo, hi;
     int64_t v_begin, v_end;
+    Mover *movers;           // three lists: k <= 32, 33..128, > 128
+    unsigned *mcount;        // their lengths (device counters)
+    int64_t mbase[3];        // their offsets in movers
     uint64_t seed, sweep_id;
     double beta;
     float beta32;
@@ -191,16 +201,6 @@ __device__ __forceinline__ Exact exact_decision(double beta, __int128 dl, double
     return exact_decision_d(beta, fix_to_double(dl) + fb, pf, pb, w2);
 }
 
-// s from u: y < B picks s = y, else the inverse CDF over row u then column u
-__device__ __forceinline__ int propose_block(const ModelDev &md, int u, uint64_t w1) {
-    const int B = md.B;
-    const int64_t du = md.dsum[u];
-    const int64_t y = draw_below(w1, (uint64_t)(du + B));
-    if (y < B) return (int)y;
-    const int idx = warp_cdf_search(md.P + (size_t)u * 2 * B, md.Pc + (size_t)u * 32, 2 * B, md.pstep, (uint32_t)(y - B));
-    return idx < B ? idx : idx - B;
-}
-
 __device__ __forceinline__ unsigned hash_slot(int key, int cap_log2) {
     return ((unsigned)key * 0x9E3779B1u) >> (32 - cap_log2);
 }
@@ -253,7 +253,146 @@ __device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin
 }
 
 // ---------------------------------------------------------------------------
-// warp per vertex (k <= kWarpDeg)
+// proposals: one lane per vertex, all vertices of the range
+
+__device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c) {
+    if (c.proposed | c.moves) {
+        atomicAdd(&md.counters->proposed, c.proposed);
+        atomicAdd(&md.counters->moves, c.moves);
+        atomicAdd(&md.counters->accepted, c.accepted);
+        atomicAdd(&md.counters->margin, c.margin);
+    }
+}
+
+__device__ __forceinline__ void flush_counts_warp(const ModelDev &md, Counts c, unsigned long long extra_edges) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c.proposed += __shfl_xor_sync(0xffffffffu, c.proposed, o);
+        c.moves += __shfl_xor_sync(0xffffffffu, c.moves, o);
+        c.accepted += __shfl_xor_sync(0xffffffffu, c.accepted, o);
+        c.margin += __shfl_xor_sync(0xffffffffu, c.margin, o);
+        extra_edges += __shfl_xor_sync(0xffffffffu, extra_edges, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        flush_counts(md, c);
+        if (extra_edges) atomicAdd(&md.counters->move_edges, extra_edges);
+    }
+}
+
+// first index i in Pu[0, len) with Pu[i] > t, searched by one lane: the 32
+// pivots with vector loads, then the segment eight entries at a time
+__device__ __forceinline__ int lane_cdf_search(const uint32_t *__restrict__ Pu, const uint32_t *__restrict__ Pcu, int len,
+                                               int step, uint32_t t) {
+    int lo = 0, seg = len;
+    if (len > 32) {
+        uint4 pv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pv[i] = reinterpret_cast<const uint4 *>(Pcu)[i];
+        int fp = 31;
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
+            if (pv[i].w > t) fp = 4 * i + 3;
+            if (pv[i].z > t) fp = 4 * i + 2;
+            if (pv[i].y > t) fp = 4 * i + 1;
+            if (pv[i].x > t) fp = 4 * i;
+        }
+        lo = fp * step;
+        seg = step < len - lo ? step : len - lo;
+    }
+    if (seg <= 32) {
+        for (int g0 = 0; g0 < seg; g0 += 8) {
+            uint32_t x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = g0 + i < seg ? Pu[lo + g0 + i] : 0xffffffffu;
+            int idx = -1;
+#pragma unroll
+            for (int i = 7; i >= 0; --i)
+                if (x[i] > t) idx = i;
+            if (idx >= 0) return lo + g0 + idx;
+        }
+        return lo + seg - 1;
+    }
+    int n = seg;
+    while (n > 0) {
+        const int half = n >> 1;
+        if (Pu[lo + half] <= t) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// Proposal of every vertex in [v_begin, v_end) (Alg. 2 "propose new
+// community"): the j-th incident edge gives u, then s by the inverse CDF of
+// (1 + M[u][s] + M[s][u]) / (d_u + B).  Proposals with s = r end here; the
+// others are appended to the list of their degree group.
+__global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
+    const ModelDev &md = a.md;
+    const GraphDev &g = a.g;
+    const int lane = threadIdx.x & 31, B = md.B;
+    Counts c;
+    unsigned long long medges = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = a.v_begin + (int64_t)blockIdx.x * blockDim.x; base < a.v_end; base += stride) {
+        const int64_t vv = base + threadIdx.x;
+        int bin = -1, s = 0, v = (int)vv;
+        uint64_t w2 = 0;
+        if (vv < a.v_end) {
+            const int r = md.b[v];
+            const int o0 = g.op[v], kout = g.op[v + 1] - o0;
+            const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
+            const int k = kout + kin;
+            if (k == 0) {
+                write_trace(a, v, r, 0, 0.0, 0.0);
+            } else {
+                const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
+                const int j = (int)draw_below(w.x, (uint64_t)k);
+                const int nb = j < kout ? g.oc[o0 + j] : g.ic[i0 + j - kout];
+                const int u = md.b[nb];
+                const int64_t du = md.dsum[u];
+                const int64_t y = draw_below(w.y, (uint64_t)(du + B));
+                if (y < B) {
+                    s = (int)y;
+                } else {
+                    const int idx = lane_cdf_search(md.P + (size_t)u * 2 * B, md.Pc + (size_t)u * 32, 2 * B, md.pstep,
+                                                    (uint32_t)(y - B));
+                    s = idx < B ? idx : idx - B;
+                }
+                if (s == r) {
+                    c.proposed++;
+                    write_trace(a, v, r, 1, 0.0, 0.0);
+                } else {
+                    bin = k <= kSmallDeg ? 0 : k <= kWarpDeg ? 1 : 2;
+                    w2 = w.z;
+                    medges += (unsigned long long)k;
+                }
+            }
+        }
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const unsigned msk = __ballot_sync(0xffffffffu, bin == bb);
+            if (msk == 0) continue;
+            const int leader = __ffs(msk) - 1;
+            unsigned pos0 = 0;
+            if (lane == leader) pos0 = atomicAdd(&a.mcount[bb], (unsigned)__popc(msk));
+            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+            if (bin == bb) {
+                Mover mv;
+                mv.v = v;
+                mv.s = s;
+                mv.w2 = w2;
+                a.movers[a.mbase[bb] + pos0 + __popc(msk & ((1u << lane) - 1u))] = mv;
+            }
+        }
+    }
+    flush_counts_warp(md, c, medges);
+}
+
+// ---------------------------------------------------------------------------
+// moves of vertices with 33 <= k (one warp per vertex)
 
 // Evaluates the move v: r -> s once the entries are aggregated.
 // each_entry(f) calls f(t, ko, ki) for each entry the calling lane holds.
@@ -264,8 +403,8 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     const int lane = threadIdx.x & 31;
     // neighbours in r and in s (one lane holds each); 16-bit fields when
     // the degree allows it
-    int pr = 0, ps = 0;
     if (x.k < 65536) {
+        int pr = 0, ps = 0;
         each_entry([&](int t, int ko, int ki) {
             if (t == x.r) pr += ko | (ki << 16);
             else if (t == x.s) ps += ko | (ki << 16);
@@ -331,52 +470,20 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     }
 }
 
-__device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c) {
-    if (c.proposed | c.moves) {
-        atomicAdd(&md.counters->proposed, c.proposed);
-        atomicAdd(&md.counters->moves, c.moves);
-        atomicAdd(&md.counters->accepted, c.accepted);
-        atomicAdd(&md.counters->margin, c.margin);
-    }
-}
-
-// Dynamic shared memory: optionally a copy of the per-block arrays (32
-// pivots, dsum, dout, din, rcp32 per block) when cache_blocks is set, then
-// per warp: cap int keys, cap 32-bit counts (ko | ki << 16, so degrees stay
-// below 65536), cap 16-bit list entries and one list length.  Warps per
-// CTA = blockDim.x / 32.  Each warp takes chunks of `chunk` consecutive
-// entries of the order list and prefetches their offsets and labels with
-// one lane per vertex.
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_decide_warp(DecideArgs a, int cap, int cap_log2,
-                                                                      int cache_blocks, int chunk) {
+// One warp per mover of list `bin` (k >= 33).  Dynamic shared memory per
+// warp: cap int keys, cap 32-bit counts (ko | ki << 16, degrees below
+// 65536), cap 16-bit list entries, one list length.  Warps take chunks of
+// `chunk` movers and prefetch their records with one lane per mover.
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_warp(DecideArgs a, int bin, int cap,
+                                                                                    int cap_log2, int chunk) {
     extern __shared__ int dsm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    ModelDev md = a.md;
-    int *base = dsm;
-    if (cache_blocks) {
-        const int B = md.B;
-        uint32_t *s_pc = reinterpret_cast<uint32_t *>(base);
-        int *s_dsum = base + 32 * B, *s_dout = s_dsum + B, *s_din = s_dout + B;
-        float *s_rcp = reinterpret_cast<float *>(s_din + B);
-        for (int i = threadIdx.x; i < 32 * B; i += blockDim.x) s_pc[i] = a.md.Pc[i];
-        for (int i = threadIdx.x; i < B; i += blockDim.x) {
-            s_dsum[i] = a.md.dsum[i];
-            s_dout[i] = a.md.dout[i];
-            s_din[i] = a.md.din[i];
-            s_rcp[i] = a.md.rcp32[i];
-        }
-        __syncthreads();
-        md.Pc = s_pc;
-        md.dsum = s_dsum;
-        md.dout = s_dout;
-        md.din = s_din;
-        md.rcp32 = s_rcp;
-        base += 36 * B;
-    }
-    int *keys = base + (size_t)wid * cap;
-    unsigned *cnt = reinterpret_cast<unsigned *>(base + (size_t)nwarps * cap) + (size_t)wid * cap;
-    int *nlist = base + (size_t)2 * nwarps * cap + wid;
-    unsigned short *list = reinterpret_cast<unsigned short *>(base + (size_t)2 * nwarps * cap + nwarps) + (size_t)wid * cap;
+    const ModelDev &md = a.md;
+    const GraphDev &g = a.g;
+    int *keys = dsm + (size_t)wid * cap;
+    unsigned *cnt = reinterpret_cast<unsigned *>(dsm + (size_t)nwarps * cap) + (size_t)wid * cap;
+    int *nlist = dsm + (size_t)2 * nwarps * cap + wid;
+    unsigned short *list = reinterpret_cast<unsigned short *>(dsm + (size_t)2 * nwarps * cap + nwarps) + (size_t)wid * cap;
     for (int i = lane; i < cap; i += 32) {
         keys[i] = -1;
         cnt[i] = 0;
@@ -384,62 +491,37 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
     if (lane == 0) *nlist = 0;
     __syncwarp();
 
-    const GraphDev &g = a.g;
+    const Mover *mlist = a.movers + a.mbase[bin];
+    const int64_t count = *(volatile unsigned *)&a.mcount[bin];
     Counts c;
     const int64_t nw = (int64_t)gridDim.x * nwarps;
-    const int64_t nchunk = (a.hi - a.lo + chunk - 1) / chunk;
+    const int64_t nchunk = (count + chunk - 1) / chunk;
     for (int64_t ch = (int64_t)blockIdx.x * nwarps + wid; ch < nchunk; ch += nw) {
-        const int64_t first = a.lo + ch * chunk;
-        const int cnt_v = (int)(a.hi - first < chunk ? a.hi - first : chunk);
-        int pv = 0, pr = 0, po = 0, pko = 0, pi = 0, pki = 0;
-        uint64_t pw0 = 0, pw1 = 0, pw2 = 0;
+        const int64_t first = ch * chunk;
+        const int cnt_v = (int)(count - first < chunk ? count - first : chunk);
+        int pv = 0, ps = 0, pr = 0, po = 0, pko = 0, pi = 0, pki = 0;
+        uint64_t pw2 = 0;
         if (lane < cnt_v) {
-            pv = a.order[first + lane];
+            const Mover mv = mlist[first + lane];
+            pv = mv.v;
+            ps = mv.s;
+            pw2 = mv.w2;
             pr = md.b[pv];
             po = g.op[pv];
             pko = g.op[pv + 1] - po;
             pi = g.ip[pv];
             pki = g.ip[pv + 1] - pi;
-            // one lane per vertex draws that vertex's Philox block
-            const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)pv, 0, 0, a.seed, 0);
-            pw0 = w.x;
-            pw1 = w.y;
-            pw2 = w.z;
         }
         for (int q = 0; q < cnt_v; ++q) {
-        const int v = __shfl_sync(0xffffffffu, pv, q);
-        if (v < a.v_begin || v >= a.v_end) continue;
-        const int r = __shfl_sync(0xffffffffu, pr, q);
-        const int o0 = __shfl_sync(0xffffffffu, po, q), kout = __shfl_sync(0xffffffffu, pko, q);
-        const int i0 = __shfl_sync(0xffffffffu, pi, q), kin = __shfl_sync(0xffffffffu, pki, q);
-        const int k = kout + kin;
-        if (k == 0) {
-            if (lane == 0) write_trace(a, v, r, 0, 0.0, 0.0);
-            continue;
-        }
-        const uint64_t w0 = __shfl_sync(0xffffffffu, pw0, q), w1 = __shfl_sync(0xffffffffu, pw1, q);
-        const uint64_t w2 = __shfl_sync(0xffffffffu, pw2, q);
-        const int j = (int)draw_below(w0, (uint64_t)k);
-
-        int self = 0, u = r, D = 0;
-        int my_t = -1, my_ko = 0, my_ki = 0;
-        if (k <= kSmallDeg) {
-            const bool valid = lane < k, is_out = lane < kout;
-            const int nb = valid ? (is_out ? g.oc[o0 + lane] : g.ic[i0 + lane - kout]) : -1;
-            const int tb = valid ? md.b[nb] : -1;
-            u = __shfl_sync(0xffffffffu, tb, j);
-            const bool is_self = valid && nb == v;
-            self = __popc(__ballot_sync(0xffffffffu, is_self && is_out));
-            const int key = (valid && !is_self) ? tb : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            const unsigned outm = __ballot_sync(0xffffffffu, valid && !is_self && is_out);
-            if (key >= 0 && lane == __ffs(peers) - 1) {
-                my_t = key;
-                my_ko = __popc(peers & outm);
-                my_ki = __popc(peers) - my_ko;
-            }
-        } else {
-            // four 32-neighbour chunks per round: their loads are in flight together
+            const int v = __shfl_sync(0xffffffffu, pv, q);
+            const int s = __shfl_sync(0xffffffffu, ps, q);
+            const int r = __shfl_sync(0xffffffffu, pr, q);
+            const int o0 = __shfl_sync(0xffffffffu, po, q), kout = __shfl_sync(0xffffffffu, pko, q);
+            const int i0 = __shfl_sync(0xffffffffu, pi, q), kin = __shfl_sync(0xffffffffu, pki, q);
+            const uint64_t w2 = __shfl_sync(0xffffffffu, pw2, q);
+            const int k = kout + kin;
+            // aggregate the row: four 32-neighbour chunks per round
+            int self = 0;
             bool ok = true;
             for (int base = 0; base < k; base += 128) {
                 int nb[4], tb[4];
@@ -456,7 +538,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
                     if (cb >= k) break;
                     const int idx = cb + lane;
                     const bool valid = idx < k, is_out = idx < kout;
-                    if (j >= cb && j < cb + 32) u = __shfl_sync(0xffffffffu, tb[c4], j - cb);
                     const bool is_self = valid && nb[c4] == v;
                     self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
                     const int key = (valid && !is_self) ? tb[c4] : -1;
@@ -470,34 +551,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
                 }
             }
             if (!ok) record_status(md.status, SBP_EHASHFULL);
-            D = *nlist;
-        }
-
-        const int s = propose_block(md, u, w1);
-        if (s == r) {
-            if (lane == 0) {
-                c.proposed++;
-                write_trace(a, v, r, 1, 0.0, 0.0);
-            }
-        } else {
+            const int D = *nlist;
             VertexCtx x;
             x.v = v; x.r = r; x.s = s;
             x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
-            if (k <= kSmallDeg) {
-                evaluate_warp(a, md, x, w2, [&](auto &&f) {
-                    if (my_t >= 0) f(my_t, my_ko, my_ki);
-                }, c);
-            } else {
-                evaluate_warp(a, md, x, w2, [&](auto &&f) {
-                    for (int e = lane; e < D; e += 32) {
-                        const int slot = list[e];
-                        const unsigned cc = cnt[slot];
-                        f(keys[slot], (int)(cc & 0xffffu), (int)(cc >> 16));
-                    }
-                }, c);
-            }
-        }
-        if (k > kSmallDeg) {
+            evaluate_warp(a, md, x, w2, [&](auto &&f) {
+                for (int e = lane; e < D; e += 32) {
+                    const int slot = list[e];
+                    const unsigned cc = cnt[slot];
+                    f(keys[slot], (int)(cc & 0xffffu), (int)(cc >> 16));
+                }
+            }, c);
             __syncwarp();
             for (int e = lane; e < D; e += 32) {
                 const int slot = list[e];
@@ -508,13 +572,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
             if (lane == 0) *nlist = 0;
             __syncwarp();
         }
-        }
     }
     if (lane == 0) flush_counts(md, c);
 }
 
 // ---------------------------------------------------------------------------
-// CTA per vertex (k > kWarpDeg); the table lives in dynamic shared memory
+// CTA per mover: tables beyond 4096 slots or degree >= 65536
 
 struct CtaScratch {
     __int128 dl[kBigThreads / 32];
@@ -523,10 +586,10 @@ struct CtaScratch {
     __int128 dl_tot;
     double fb_tot;
     int rs[4];
-    int nlist, self, u, s, ok, dec;
+    int nlist, self, ok, dec;
 };
 
-__global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int cap, int cap_log2) {
+__global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin, int cap, int cap_log2) {
     extern __shared__ unsigned long long smem_u64[];
     unsigned long long *cnt = smem_u64;
     int *keys = reinterpret_cast<int *>(cnt + cap);
@@ -546,23 +609,22 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
 
     const GraphDev &g = a.g;
     const ModelDev &md = a.md;
+    const Mover *mlist = a.movers + a.mbase[bin];
+    const int64_t count = *(volatile unsigned *)&a.mcount[bin];
     Counts c;
-    for (int64_t i = a.lo + blockIdx.x; i < a.hi; i += gridDim.x) {
-        const int v = a.order[i];
-        if (v < a.v_begin || v >= a.v_end) continue;
+    for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const Mover mv = mlist[i];
+        const int v = mv.v, s = mv.s;
         const int r = md.b[v];
         const int o0 = g.op[v], kout = g.op[v + 1] - o0;
         const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
         const int k = kout + kin;
-        const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
-        const int j = (int)draw_below(w.x, (uint64_t)k);
         if (tid < 4) sh.rs[tid] = 0;
         for (int base = 0; base < k; base += blockDim.x) {
             const int idx = base + tid;
             const bool valid = idx < k, is_out = idx < kout;
             const int nb = valid ? (is_out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
             const int tb = valid ? md.b[nb] : -1;
-            if (idx == j) sh.u = tb;
             const bool is_self = valid && nb == v;
             const int nself = __popc(__ballot_sync(0xffffffffu, is_self && is_out));
             if (lane == 0 && nself) atomicAdd(&sh.self, nself);
@@ -577,115 +639,96 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
             }
         }
         __syncthreads();
-        if (wid == 0) {
-            const int s = propose_block(md, sh.u, w.y);
-            if (tid == 0) sh.s = s;
+        const int D = sh.nlist;
+        if (tid == 0 && !sh.ok) record_status(md.status, SBP_EHASHFULL);
+        VertexCtx x;
+        x.v = v; x.r = r; x.s = s;
+        x.Kout = kout; x.Kin = kin; x.self = sh.self; x.k = k;
+        for (int e = tid; e < D; e += blockDim.x) {
+            const int slot = list[e];
+            const int t = keys[slot];
+            const unsigned long long cc = cnt[slot];
+            if (t == r) { sh.rs[0] = (int)(cc & 0xffffffffu); sh.rs[1] = (int)(cc >> 32); }
+            if (t == s) { sh.rs[2] = (int)(cc & 0xffffffffu); sh.rs[3] = (int)(cc >> 32); }
         }
         __syncthreads();
-        const int s = sh.s, D = sh.nlist;
-        if (tid == 0 && !sh.ok) record_status(md.status, SBP_EHASHFULL);
-        if (s == r) {
-            if (tid == 0) {
-                c.proposed++;
-                write_trace(a, v, r, 1, 0.0, 0.0);
+        x.ko_r = sh.rs[0]; x.ki_r = sh.rs[1]; x.ko_s = sh.rs[2]; x.ki_s = sh.rs[3];
+        __int128 dl = 0;
+        double fb = 0.0;
+        float pf = 0.0f, pb = 0.0f;
+        for (int e = tid; e < D; e += blockDim.x) {
+            const int slot = list[e];
+            const int t = keys[slot];
+            const unsigned long long cc = cnt[slot];
+            if (t != r && t != s) entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
+        }
+        if (tid < 32) special_terms(md, x, tid, dl, fb);
+        dl = warp_sum_128(dl);
+        pf = warp_sum_f(pf);
+        pb = warp_sum_f(pb);
+        if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
+        if (lane == 0) {
+            sh.dl[wid] = dl;
+            sh.fb[wid] = fb;
+            sh.pf[wid] = pf;
+            sh.pb[wid] = pb;
+        }
+        __syncthreads();
+        CornerVals cv;
+        cv.Mrr = Mat(md, r, r);
+        cv.Mss = Mat(md, s, s);
+        cv.Mrs = Mat(md, r, s);
+        cv.Msr = Mat(md, s, r);
+        cv.dr = md.dsum[r];
+        cv.ds = md.dsum[s];
+        if (tid == 0) {
+            __int128 dlt = 0;
+            double fbt = 0.0;
+            float pft = 0.0f, pbt = 0.0f;
+            for (int q = 0; q < nwarps; ++q) {
+                dlt += sh.dl[q];
+                fbt += sh.fb[q];
+                pft += sh.pf[q];
+                pbt += sh.pb[q];
             }
-        } else {
-            VertexCtx x;
-            x.v = v; x.r = r; x.s = s;
-            x.Kout = kout; x.Kin = kin; x.self = sh.self; x.k = k;
+            sh.dl_tot = dlt;
+            sh.fb_tot = fbt;
+            corner_hastings_fast(x, cv, md.B, pft, pbt);
+            const bool has_fb = __double_as_longlong(fbt) != 0;
+            const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dlt, has_fb, fbt, pft, pbt, mv.w2, k);
+            sh.dec = dec;
+            if (dec >= 0) {
+                if (dec) md.bnew[v] = s;
+                count_result(c, dec != 0, false);
+            }
+        }
+        __syncthreads();
+        if (sh.dec < 0) {
+            double pf64 = 0.0, pb64 = 0.0;
             for (int e = tid; e < D; e += blockDim.x) {
                 const int slot = list[e];
                 const int t = keys[slot];
                 const unsigned long long cc = cnt[slot];
-                if (t == r) { sh.rs[0] = (int)(cc & 0xffffffffu); sh.rs[1] = (int)(cc >> 32); }
-                if (t == s) { sh.rs[2] = (int)(cc & 0xffffffffu); sh.rs[3] = (int)(cc >> 32); }
+                if (t != r && t != s) entry_exact(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), pf64, pb64);
             }
-            __syncthreads();
-            x.ko_r = sh.rs[0]; x.ki_r = sh.rs[1]; x.ko_s = sh.rs[2]; x.ki_s = sh.rs[3];
-            __int128 dl = 0;
-            double fb = 0.0;
-            float pf = 0.0f, pb = 0.0f;
-            for (int e = tid; e < D; e += blockDim.x) {
-                const int slot = list[e];
-                const int t = keys[slot];
-                const unsigned long long cc = cnt[slot];
-                if (t != r && t != s) entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
-            }
-            if (tid < 32) special_terms(md, x, tid, dl, fb);
-            dl = warp_sum_128(dl);
-            pf = warp_sum_f(pf);
-            pb = warp_sum_f(pb);
-            if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
+            pf64 = warp_sum(pf64);
+            pb64 = warp_sum(pb64);
             if (lane == 0) {
-                sh.dl[wid] = dl;
-                sh.fb[wid] = fb;
-                sh.pf[wid] = pf;
-                sh.pb[wid] = pb;
+                sh.pf64[wid] = pf64;
+                sh.pb64[wid] = pb64;
             }
             __syncthreads();
             if (tid == 0) {
-                __int128 dlt = 0;
-                double fbt = 0.0;
-                float pft = 0.0f, pbt = 0.0f;
+                double pft = 0.0, pbt = 0.0;
                 for (int q = 0; q < nwarps; ++q) {
-                    dlt += sh.dl[q];
-                    fbt += sh.fb[q];
-                    pft += sh.pf[q];
-                    pbt += sh.pb[q];
+                    pft += sh.pf64[q];
+                    pbt += sh.pb64[q];
                 }
-                sh.dl_tot = dlt;
-                sh.fb_tot = fbt;
-                CornerVals cv;
-                cv.Mrr = Mat(md, r, r);
-                cv.Mss = Mat(md, s, s);
-                cv.Mrs = Mat(md, r, s);
-                cv.Msr = Mat(md, s, r);
-                cv.dr = md.dsum[r];
-                cv.ds = md.dsum[s];
-                corner_hastings_fast(x, cv, md.B, pft, pbt);
-                const bool has_fb = __double_as_longlong(fbt) != 0;
-                const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dlt, has_fb, fbt, pft, pbt, w.z, k);
-                sh.dec = dec;
-                if (dec >= 0) {
-                    if (dec) md.bnew[v] = s;
-                    count_result(c, dec != 0, false);
-                }
-            }
-            __syncthreads();
-            if (sh.dec < 0) {
-                double pf64 = 0.0, pb64 = 0.0;
-                for (int e = tid; e < D; e += blockDim.x) {
-                    const int slot = list[e];
-                    const int t = keys[slot];
-                    const unsigned long long cc = cnt[slot];
-                    if (t != r && t != s) entry_exact(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), pf64, pb64);
-                }
-                pf64 = warp_sum(pf64);
-                pb64 = warp_sum(pb64);
-                if (lane == 0) {
-                    sh.pf64[wid] = pf64;
-                    sh.pb64[wid] = pb64;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    double pft = 0.0, pbt = 0.0;
-                    for (int q = 0; q < nwarps; ++q) {
-                        pft += sh.pf64[q];
-                        pbt += sh.pb64[q];
-                    }
-                    CornerVals cv;
-                    cv.Mrr = Mat(md, r, r);
-                    cv.Mss = Mat(md, s, s);
-                    cv.Mrs = Mat(md, r, s);
-                    cv.Msr = Mat(md, s, r);
-                    cv.dr = md.dsum[r];
-                    cv.ds = md.dsum[s];
-                    corner_hastings_exact(x, cv, md.B, pft, pbt);
-                    const Exact e = exact_decision(a.beta, sh.dl_tot, sh.fb_tot, pft, pbt, w.z);
-                    if (e.accept) md.bnew[v] = s;
-                    count_result(c, e.accept, e.margin);
-                    write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
-                }
+                corner_hastings_exact(x, cv, md.B, pft, pbt);
+                const Exact e = exact_decision(a.beta, sh.dl_tot, sh.fb_tot, pft, pbt, mv.w2);
+                if (e.accept) md.bnew[v] = s;
+                count_result(c, e.accept, e.margin);
+                write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
             }
         }
         __syncthreads();
@@ -704,28 +747,27 @@ __global__ void __launch_bounds__(kBigThreads) k_decide_cta(DecideArgs a, int ca
 }
 
 // ---------------------------------------------------------------------------
-// batches of 32 vertices with 1 <= k <= 32 per warp
+// moves of vertices with 1 <= k <= 32: batches of 32 movers per warp
 //
-// Phases per batch (lane q <-> vertex q of the batch):
-//   P1 lane per vertex: offsets, labels, Philox; exclusive prefix of k;
+//   P1 lane per mover: record, offsets, label; exclusive prefix of k;
 //   P2 edge parallel over the batch's concatenated rows (four 32-wide
-//      chunks in flight): neighbour ids and their blocks into shared memory;
-//   P3 per vertex, warp wide: match/ballot aggregation of its row into
-//      (q, t, kout, kin) entries, compacted in place;
-//   P4 lane per vertex: proposal s from u by the CDF search;
-//   P5 entry parallel: Delta L (128-bit table sums, accumulated per vertex in
-//      64-bit fixed point at 2^-48, exact integer adds) and FP32 Hastings
-//      terms, shared-memory atomics per vertex;
-//   P6 lane per vertex: corner and degree terms, FP32 test with its band, the
-//      FP64 recheck (sequential over the vertex's entries) when needed.
-// Scalar work is spread over the lanes instead of repeated by all 32.
+//      chunks in flight): neighbour blocks into shared memory, tagged with
+//      the mover's slot;
+//   P3 windows of whole rows (at most 32 edge ends): match/ballot
+//      aggregation into (q, t, kout, kin) entries, compacted in place, in
+//      row order;
+//   P5 entry parallel: Delta L (table sums, per entry in 64-bit fixed point
+//      at 2^-48) and FP32 Hastings terms, summed per mover by a segmented
+//      warp scan (entries of a mover are contiguous);
+//   P6 lane per mover: corner and degree terms, FP32 test with its band, the
+//      FP64 recheck (sequential over the mover's entries) when needed.
 
 constexpr int kBatchEdges = 32 * kSmallDeg;
 
 struct BatchWarp {
-    int key[kBatchEdges];  // edge ends: (t << 1) | in, -2 out self-loop, -1 in self-loop; then entries
+    int key[kBatchEdges];  // edge ends (q << 26 | self << 25 | t << 1 | in), then entries
     int r[32], s[32], rsr[32], rss[32], hasfb[32];
-    unsigned long long dl[32];  // Delta L, fixed point 2^-48
+    long long dl[32];  // Delta L, fixed point 2^-48
     float pf[32], pb[32];
     double fb[32];
 };
@@ -735,54 +777,6 @@ __device__ __forceinline__ unsigned pack_entry(int q, int t, int ko, int ki) {
     return ((unsigned)q << 27) | ((unsigned)ko << 21) | ((unsigned)ki << 15) | (unsigned)t;
 }
 
-// first index i in Pu[0, len) with Pu[i] > t, searched by one lane: the 32
-// pivots with vector loads, then the segment (all loads issued together
-// while it is at most 32 long)
-__device__ __forceinline__ int lane_cdf_search(const uint32_t *__restrict__ Pu, const uint32_t *__restrict__ Pcu, int len,
-                                               int step, uint32_t t) {
-    int lo = 0, seg = len;
-    if (len > 32) {
-        uint4 pv[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) pv[i] = reinterpret_cast<const uint4 *>(Pcu)[i];
-        int fp = 31;
-#pragma unroll
-        for (int i = 7; i >= 0; --i) {
-            if (pv[i].w > t) fp = 4 * i + 3;
-            if (pv[i].z > t) fp = 4 * i + 2;
-            if (pv[i].y > t) fp = 4 * i + 1;
-            if (pv[i].x > t) fp = 4 * i;
-        }
-        lo = fp * step;
-        seg = step < len - lo ? step : len - lo;
-    }
-    if (seg <= 32) {
-        // eight loads in flight per group
-        for (int g0 = 0; g0 < seg; g0 += 8) {
-            uint32_t x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = g0 + i < seg ? Pu[lo + g0 + i] : 0xffffffffu;
-            int idx = -1;
-#pragma unroll
-            for (int i = 7; i >= 0; --i)
-                if (x[i] > t) idx = i;
-            if (idx >= 0) return lo + g0 + idx;
-        }
-        return lo + seg - 1;
-    }
-    int n = seg;
-    while (n > 0) {
-        const int half = n >> 1;
-        if (Pu[lo + half] <= t) {
-            lo += half + 1;
-            n -= half + 1;
-        } else {
-            n = half;
-        }
-    }
-    return lo;
-}
-
 __device__ __forceinline__ float fix48_to_float(long long v) {
     return fmaf((float)(int)(v >> 32), 0x1p-16f, (float)(unsigned)(v & 0xffffffffu) * 0x1p-48f);
 }
@@ -790,35 +784,34 @@ __device__ __forceinline__ double fix48_to_double(long long v) {
     return (double)(int)(v >> 32) * 0x1p-16 + (double)(unsigned)(v & 0xffffffffu) * 0x1p-48;
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_decide_batch(DecideArgs a) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_batch(DecideArgs a) {
     extern __shared__ __align__(16) unsigned char bsm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     BatchWarp &W = reinterpret_cast<BatchWarp *>(bsm)[wid];
     const GraphDev &g = a.g;
     const ModelDev &md = a.md;
     const int B = md.B;
+    const Mover *mlist = a.movers + a.mbase[0];
+    const int64_t count = *(volatile unsigned *)&a.mcount[0];
     Counts c;
-    const int64_t nbatch = (a.hi - a.lo + 31) >> 5;
+    const int64_t nbatch = (count + 31) >> 5;
     for (int64_t bt = (int64_t)blockIdx.x * nwarps + wid; bt < nbatch; bt += (int64_t)gridDim.x * nwarps) {
-        const int64_t first_i = a.lo + (bt << 5);
-        const int nv = (int)(a.hi - first_i < 32 ? a.hi - first_i : 32);
+        const int64_t first_i = bt << 5;
+        const int nv = (int)(count - first_i < 32 ? count - first_i : 32);
         // ---- P1
-        int v = 0, r = 0, o0 = 0, kout = 0, i0 = 0, kin = 0, k = 0, j = 0;
-        uint64_t w1 = 0, w2 = 0;
+        int v = 0, s = -1, r = 0, o0 = 0, kout = 0, i0 = 0, kin = 0, k = 0;
+        uint64_t w2 = 0;
         if (lane < nv) {
-            v = a.order[first_i + lane];
-            if (v >= a.v_begin && v < a.v_end) {
-                r = md.b[v];
-                o0 = g.op[v];
-                kout = g.op[v + 1] - o0;
-                i0 = g.ip[v];
-                kin = g.ip[v + 1] - i0;
-                k = kout + kin;
-                const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
-                j = (int)draw_below(w.x, (uint64_t)k);
-                w1 = w.y;
-                w2 = w.z;
-            }
+            const Mover mv = mlist[first_i + lane];
+            v = mv.v;
+            s = mv.s;
+            w2 = mv.w2;
+            r = md.b[v];
+            o0 = g.op[v];
+            kout = g.op[v + 1] - o0;
+            i0 = g.ip[v];
+            kin = g.ip[v + 1] - i0;
+            k = kout + kin;
         }
         int incl = k;
 #pragma unroll
@@ -830,7 +823,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         // ---- P2
         for (int base = 0; base < total; base += 128) {
-            int nb[4], vq[4], eo[4];
+            int nb[4], vq[4], tag[4];
 #pragma unroll
             for (int c4 = 0; c4 < 4; ++c4) {
                 const int p = base + c4 * 32 + lane;
@@ -846,7 +839,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
                 const int iq = __shfl_sync(0xffffffffu, i0, q);
                 vq[c4] = __shfl_sync(0xffffffffu, v, q);
                 const int e = p - fq;
-                eo[c4] = e < kq ? 1 : 0;
+                tag[c4] = (q << 26) | (e < kq ? 0 : 1);
                 nb[c4] = p < total ? (e < kq ? g.oc[oq + e] : g.ic[iq + e - kq]) : -1;
             }
 #pragma unroll
@@ -854,102 +847,118 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
                 const int p = base + c4 * 32 + lane;
                 if (nb[c4] >= 0) {
                     const int t = md.b[nb[c4]];
-                    W.key[p] = nb[c4] == vq[c4] ? (eo[c4] ? -2 : -1) : ((t << 1) | (eo[c4] ? 0 : 1));
+                    W.key[p] = nb[c4] == vq[c4] ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
                 }
             }
         }
         __syncwarp();
-        // ---- P3
-        int nent = 0, my_u = r, my_self = 0, my_est = 0, my_ecnt = 0;
-        for (int q = 0; q < nv; ++q) {
-            const int kq = __shfl_sync(0xffffffffu, k, q);
-            if (kq == 0) continue;
-            const int fq = __shfl_sync(0xffffffffu, first, q);
-            const int jq = __shfl_sync(0xffffffffu, j, q);
-            const int rq = __shfl_sync(0xffffffffu, r, q);
-            const int x = lane < kq ? W.key[fq + lane] : -3;
-            const int t = x >= 0 ? (x >> 1) : -1;
-            const bool in = x >= 0 && (x & 1);
-            const int uq = __shfl_sync(0xffffffffu, x >= 0 ? t : rq, jq);
-            const int selfq = __popc(__ballot_sync(0xffffffffu, x == -2));
-            const unsigned peers = __match_any_sync(0xffffffffu, t);
-            const unsigned outm = __ballot_sync(0xffffffffu, t >= 0 && !in);
-            const bool leader = t >= 0 && lane == __ffs(peers) - 1;
+        // ---- P3: windows of whole rows
+        int nent = 0, my_self = 0, my_est = 0, my_ecnt = 0;
+        for (int qa = 0; qa < nv;) {
+            const int fa = __shfl_sync(0xffffffffu, first, qa);
+            const unsigned inw = __ballot_sync(0xffffffffu, lane >= qa && lane < nv && incl - fa <= 32);
+            const int qb = 31 - __clz(inw);
+            const int wend = __shfl_sync(0xffffffffu, incl, qb);
+            const int p = fa + lane;
+            const bool valid = p < wend;
+            const int x = valid ? W.key[p] : 0;
+            const bool selfl = valid && ((x >> 25) & 1);
+            const bool in = (x & 1) != 0;
+            const bool isent = valid && !selfl;
+            const int mkey = isent ? (x >> 1) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, mkey);
+            const unsigned outm = __ballot_sync(0xffffffffu, isent && !in);
+            const unsigned sfl = __ballot_sync(0xffffffffu, selfl && !in);
+            const bool leader = isent && lane == __ffs(peers) - 1;
             const unsigned lm = __ballot_sync(0xffffffffu, leader);
             if (leader) {
                 const int ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                W.key[nent + __popc(lm & ((1u << lane) - 1u))] = (int)pack_entry(q, t, ko, ki);
+                W.key[nent + __popc(lm & ((1u << lane) - 1u))] =
+                    (int)pack_entry((x >> 26) & 31, (x >> 1) & 0xffffff, ko, ki);
             }
-            if (lane == q) {
-                my_u = uq;
-                my_self = selfq;
-                my_est = nent;
-                my_ecnt = __popc(lm);
+            if (lane >= qa && lane <= qb) {
+                const int lo_l = first - fa, hi_l = incl - fa;
+                const unsigned below = (1u << lo_l) - 1u;
+                const unsigned mq = (hi_l >= 32 ? 0xffffffffu : ((1u << hi_l) - 1u)) & ~below;
+                my_self = __popc(sfl & mq);
+                my_est = nent + __popc(lm & below);
+                my_ecnt = __popc(lm & mq);
             }
             nent += __popc(lm);
+            qa = qb + 1;
         }
-        // ---- P4
-        int s = r;
-        if (k > 0) {
-            const int64_t du = md.dsum[my_u];
-            const int64_t y = draw_below(w1, (uint64_t)(du + B));
-            if (y < B) {
-                s = (int)y;
-            } else {
-                const int idx = lane_cdf_search(md.P + (size_t)my_u * 2 * B, md.Pc + (size_t)my_u * 32, 2 * B, md.pstep,
-                                                (uint32_t)(y - B));
-                s = idx < B ? idx : idx - B;
-            }
-        }
-        const bool move = k > 0 && s != r;
         W.r[lane] = r;
-        W.s[lane] = move ? s : -1;
+        W.s[lane] = s;
         W.rsr[lane] = 0;
         W.rss[lane] = 0;
         W.hasfb[lane] = 0;
-        W.dl[lane] = 0ull;
+        W.dl[lane] = 0;
         W.pf[lane] = 0.0f;
         W.pb[lane] = 0.0f;
         W.fb[lane] = 0.0;
         __syncwarp();
-        // ---- P5
-        for (int e = lane; e < nent; e += 32) {
-            const unsigned ent = (unsigned)W.key[e];
-            const int q = (int)(ent >> 27), t = (int)(ent & 0x7fffu);
-            const int ko = (int)((ent >> 21) & 63u), ki = (int)((ent >> 15) & 63u);
-            const int sq = W.s[q];
-            if (sq < 0) continue;
-            const int rq = W.r[q];
-            if (t == rq) {
-                W.rsr[q] = ko | (ki << 8);
-                continue;
-            }
-            if (t == sq) {
-                W.rss[q] = ko | (ki << 8);
-                continue;
-            }
-            VertexCtx x;
-            x.r = rq;
-            x.s = sq;
-            __int128 d = 0;
-            double f = 0.0;
+        // ---- P5: entry parallel, segmented sums per mover
+        for (int base = 0; base < nent; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < nent;
+            const unsigned ent = valid ? (unsigned)W.key[e] : 0u;
+            const int q = valid ? (int)(ent >> 27) : 32;
+            long long d48 = 0;
             float pfe = 0.0f, pbe = 0.0f;
-            entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
-            atomicAdd(&W.dl[q], (unsigned long long)(long long)(d >> 16));
-            atomicAdd(&W.pf[q], pfe);
-            atomicAdd(&W.pb[q], pbe);
-            if (__double_as_longlong(f) != 0) {
-                atomicAdd(&W.fb[q], f);
-                W.hasfb[q] = 1;
+            double f = 0.0;
+            if (valid) {
+                const int t = (int)(ent & 0x7fffu);
+                const int ko = (int)((ent >> 21) & 63u), ki = (int)((ent >> 15) & 63u);
+                const int rq = W.r[q], sq = W.s[q];
+                if (t == rq) {
+                    W.rsr[q] = ko | (ki << 8);
+                } else if (t == sq) {
+                    W.rss[q] = ko | (ki << 8);
+                } else {
+                    VertexCtx x;
+                    x.r = rq;
+                    x.s = sq;
+                    __int128 d = 0;
+                    entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
+                    d48 = (long long)(d >> 16);
+                }
             }
+            const bool anyfb = __any_sync(0xffffffffu, __double_as_longlong(f) != 0);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int qo = __shfl_up_sync(0xffffffffu, q, o);
+                const long long d2 = __shfl_up_sync(0xffffffffu, d48, o);
+                const float p2 = __shfl_up_sync(0xffffffffu, pfe, o);
+                const float b2 = __shfl_up_sync(0xffffffffu, pbe, o);
+                if (lane >= o && qo == q) {
+                    d48 += d2;
+                    pfe += p2;
+                    pbe += b2;
+                }
+            }
+            if (anyfb) {
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int qo = __shfl_up_sync(0xffffffffu, q, o);
+                    const double f2 = __shfl_up_sync(0xffffffffu, f, o);
+                    if (lane >= o && qo == q) f += f2;
+                }
+            }
+            const int qn = __shfl_down_sync(0xffffffffu, q, 1);
+            if (valid && (lane == 31 || qn != q)) {
+                W.dl[q] += d48;
+                W.pf[q] += pfe;
+                W.pb[q] += pbe;
+                if (anyfb && __double_as_longlong(f) != 0) {
+                    W.fb[q] += f;
+                    W.hasfb[q] = 1;
+                }
+            }
+            __syncwarp();
         }
         __syncwarp();
-        // ---- P6
-        if (k > 0 && !move) {
-            c.proposed++;
-            write_trace(a, v, r, 1, 0.0, 0.0);
-        }
-        if (move) {
+        // ---- P6: lane per mover
+        if (lane < nv) {
             VertexCtx x;
             x.v = v; x.r = r; x.s = s;
             x.Kout = kout; x.Kin = kin; x.self = my_self; x.k = k;
@@ -957,8 +966,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
             x.ko_r = rsr & 0xff; x.ki_r = rsr >> 8;
             x.ko_s = rss & 0xff; x.ki_s = rss >> 8;
             __int128 d = 0;
-            double fb = W.hasfb[lane] ? W.fb[lane] : 0.0;
             bool has_fb = W.hasfb[lane] != 0;
+            double fb = has_fb ? W.fb[lane] : 0.0;
             CornerVals cv;
             cv.Mrr = special_terms(md, x, 0, d, fb);
             cv.Mss = special_terms(md, x, 1, d, fb);
@@ -969,7 +978,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
             has_fb = has_fb || __double_as_longlong(fb) != 0;
             cv.dr = md.dsum[r];
             cv.ds = md.dsum[s];
-            const long long dl48 = (long long)W.dl[lane] + (long long)(d >> 16);
+            const long long dl48 = W.dl[lane] + (long long)(d >> 16);
             float pf = W.pf[lane], pb = W.pb[lane];
             corner_hastings_fast(x, cv, B, pf, pb);
             const int dec = a.trace_on ? -1
@@ -995,20 +1004,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_de
         }
         __syncwarp();
     }
-    // warp-sum the counters, one atomic per warp
-    unsigned long long cp = c.proposed, cm = c.moves, ca = c.accepted, cg = c.margin;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cp += __shfl_xor_sync(0xffffffffu, cp, o);
-        cm += __shfl_xor_sync(0xffffffffu, cm, o);
-        ca += __shfl_xor_sync(0xffffffffu, ca, o);
-        cg += __shfl_xor_sync(0xffffffffu, cg, o);
-    }
-    if (lane == 0) {
-        Counts t;
-        t.proposed = cp; t.moves = cm; t.accepted = ca; t.margin = cg;
-        flush_counts(md, t);
-    }
+    flush_counts_warp(md, c, 0ull);
 }
 
 int sm_count() {
@@ -1049,12 +1045,24 @@ ModelDev model_dev(sbp_model *m) {
 
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace) {
     const sbp_graph *g = m->g;
+    if (!m->movers) {
+        if (cudaMalloc(&m->movers, (size_t)(g->n > 0 ? g->n : 1) * sizeof(Mover)) != cudaSuccess ||
+            cudaMalloc(&m->mcount, 4 * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SBP_ENOMEM, "cudaMalloc failed for the mover lists");
+        }
+    }
     DecideArgs a;
     a.g = g->dev();
     a.md = model_dev(m);
-    a.order = g->order;
     a.v_begin = v_begin;
     a.v_end = v_end;
+    a.movers = static_cast<Mover *>(m->movers);
+    a.mcount = m->mcount;
+    // list capacities: the sizes of the degree groups
+    a.mbase[0] = 0;
+    a.mbase[1] = g->bin[2] - g->bin[1];
+    a.mbase[2] = a.mbase[1] + (g->bin[3] - g->bin[2]);
     a.seed = m->p.seed;
     a.sweep_id = sweep_id;
     a.beta = m->p.beta;
@@ -1062,64 +1070,50 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.tr = trace ? *trace : sbp_vertex_trace{nullptr, nullptr, nullptr, nullptr};
     a.trace_on = (a.tr.s || a.tr.flags || a.tr.dH || a.tr.logA) ? 1 : 0;
     const int sms = sm_count();
-
-    auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
     const int B = m->B;
-    // k = 0 (trace only) and 33 <= k <= kWarpDeg: warp per vertex, 256-slot
-    // tables; the per-block arrays are copied to shared memory while small
+    SBP_CUDA(cudaMemsetAsync(m->mcount, 0, 4 * sizeof(unsigned), m->stream));
+
+    // proposals for every vertex of the range
     {
-        const int cache = B <= 448 ? 1 : 0;
-        const size_t smem = warp_smem(kWarpCap, kWarpsPerCta) + (cache ? (size_t)36 * B * 4 : 0);
-        SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int64_t ranges[2][2] = {{g->bin[0], a.trace_on ? g->bin[1] : g->bin[0]}, {g->bin[2], g->bin[3]}};
-        for (int rg = 0; rg < 2; ++rg) {
-            a.lo = ranges[rg][0];
-            a.hi = ranges[rg][1];
-            if (a.hi <= a.lo) continue;
-            const int64_t chunks = (a.hi - a.lo + 31) / 32;
-            int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
-            if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
-            k_decide_warp<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a, kWarpCap, 8, cache, 32);
-            SBP_CUDA(cudaGetLastError());
-        }
-    }
-    // 1 <= k <= 32: batches of 32 vertices per warp (the dense t < 2^15 fits
-    // the packed entries)
-    a.lo = g->bin[1];
-    a.hi = g->bin[2];
-    if (a.hi > a.lo) {
-        const size_t smem = sizeof(BatchWarp) * kWarpsPerCta;
-        SBP_CUDA(cudaFuncSetAttribute(k_decide_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int64_t batches = (a.hi - a.lo + 31) / 32;
-        int64_t blocks = (batches + kWarpsPerCta - 1) / kWarpsPerCta;
-        if (blocks > (int64_t)sms * 3) blocks = (int64_t)sms * 3;
-        k_decide_batch<<<(int)blocks, kWarpsPerCta * 32, smem, m->stream>>>(a);
+        int64_t blocks = (v_end - v_begin + 255) / 256;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        if (blocks < 1) blocks = 1;
+        k_propose<<<(int)blocks, 256, 0, m->stream>>>(a);
         SBP_CUDA(cudaGetLastError());
     }
-    // k > kWarpDeg: per-warp tables sized for min(max degree, B) distinct
-    // blocks while they fit, one CTA per vertex beyond that
-    a.lo = g->bin[3];
-    a.hi = g->bin[4];
-    if (a.hi > a.lo) {
-        const int64_t need = 2 * (int64_t)(g->max_deg < m->B ? g->max_deg : m->B) + 2;
+    // movers with k <= 32: batches of 32 per warp
+    if (g->bin[2] > g->bin[1]) {
+        const size_t smem = sizeof(BatchWarp) * kWarpsPerCta;
+        SBP_CUDA(cudaFuncSetAttribute(k_eval_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_eval_batch<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a);
+        SBP_CUDA(cudaGetLastError());
+    }
+    auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
+    // movers with 33 <= k <= 128: one warp each, 256-slot tables
+    if (g->bin[3] > g->bin[2]) {
+        const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
+        SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_eval_warp<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
+        SBP_CUDA(cudaGetLastError());
+    }
+    // movers with k > 128: per-warp tables sized for min(max degree, B)
+    // distinct blocks while they fit, one CTA per mover beyond that
+    if (g->bin[4] > g->bin[3]) {
+        const int64_t need = 2 * (int64_t)(g->max_deg < B ? g->max_deg : B) + 2;
         int cap_log2 = 6;
         while ((int64_t(1) << cap_log2) < need) ++cap_log2;
         const int cap = 1 << cap_log2;
         if (cap <= 4096 && g->max_deg < 65536) {
             const int nwarps = cap <= 1024 ? 8 : 4;
             const size_t smem = warp_smem(cap, nwarps);
-            SBP_CUDA(cudaFuncSetAttribute(k_decide_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            int64_t blocks = (a.hi - a.lo + nwarps - 1) / nwarps;
-            if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
-            k_decide_warp<<<(int)blocks, nwarps * 32, smem, m->stream>>>(a, cap, cap_log2, 0, 1);
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_warp<<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);
             SBP_CUDA(cudaGetLastError());
         } else {
             const size_t smem = (size_t)cap * (8 + 4 + 4);
             if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
-            SBP_CUDA(cudaFuncSetAttribute(k_decide_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            int64_t blocks = a.hi - a.lo;
-            if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
-            k_decide_cta<<<(int)blocks, kBigThreads, smem, m->stream>>>(a, cap, cap_log2);
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_cta<<<sms * 4, kBigThreads, smem, m->stream>>>(a, 2, cap, cap_log2);
             SBP_CUDA(cudaGetLastError());
         }
     }
