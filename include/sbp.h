@@ -194,6 +194,12 @@ int sbp_get_B(const sbp_model_t *m, int32_t *B_out);
 int sbp_get_dl(const sbp_model_t *m, double *dl_out);
 int sbp_get_blockmodel_dense(const sbp_model_t *m, int32_t *M_out);
 int sbp_get_degrees(const sbp_model_t *m, int32_t *dout, int32_t *din);
+
+/* The nonzeros of M in either form, as ascending keys r*B + c (int64) with
+ * their counts (int32), written to host buffers of `capacity` entries.
+ * *nnz receives the number of nonzeros; when it exceeds capacity nothing is
+ * written and SBP_EINVAL is returned. */
+int sbp_get_blockmodel_coo(const sbp_model_t *m, int64_t capacity, int64_t *keys, int32_t *counts, int64_t *nnz);
 int sbp_sync(const sbp_model_t *m);
 void sbp_free_model(sbp_model_t *m);
 

@@ -25,7 +25,7 @@ __all__ = [
     "sbp_load_graph", "sbp_free_graph", "sbp_graph_info", "sbp_build_blockmodel", "sbp_set_assignment",
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
-    "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_sync", "sbp_free_model", "sbp_philox_check",
+    "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
     "Graph", "Model", "deal_vertices",
 ]
 
@@ -115,6 +115,7 @@ def load(path: str | None = None):
         "sbp_get_dl": (C.c_int, [vp, vp]),
         "sbp_get_blockmodel_dense": (C.c_int, [vp, vp]),
         "sbp_get_degrees": (C.c_int, [vp, vp, vp]),
+        "sbp_get_blockmodel_coo": (C.c_int, [vp, i64, vp, vp, P(i64)]),
         "sbp_sync": (C.c_int, [vp]),
         "sbp_free_model": (None, [vp]),
         "sbp_philox_check": (C.c_int, [u64, u64, u64, u64, u64, u64, i32, vp]),
@@ -270,6 +271,16 @@ def sbp_get_degrees(m: int, dout, din) -> None:
     _check(lib().sbp_get_degrees(m, _ptr(dout, np.int32), _ptr(din, np.int32)))
 
 
+def sbp_get_blockmodel_coo(m: int):
+    nnz = C.c_int64()
+    rc = lib().sbp_get_blockmodel_coo(m, 0, None, None, C.byref(nnz))
+    n = nnz.value
+    keys = np.zeros(max(n, 1), np.int64)
+    cnt = np.zeros(max(n, 1), np.int32)
+    _check(lib().sbp_get_blockmodel_coo(m, n, keys.ctypes.data, cnt.ctypes.data, C.byref(nnz)))
+    return keys[:n], cnt[:n]
+
+
 def sbp_sync(m: int) -> None:
     _check(lib().sbp_sync(m))
 
@@ -340,6 +351,9 @@ class Model:
         M = np.zeros(B * B, np.int32)
         sbp_get_blockmodel_dense(self.h, M)
         return M.reshape(B, B)
+
+    def coo(self):
+        return sbp_get_blockmodel_coo(self.h)
 
     def degrees(self):
         B = self.B

@@ -152,6 +152,7 @@ int relabel_and_rebuild(sbp_model *m, const std::vector<int32_t> &map, int32_t B
     SBP_CUDA(cudaMemcpyAsync(m->map, map.data(), map.size() * 4, cudaMemcpyHostToDevice, m->stream));
     SBP_TRY(launch_relabel(m, m->map));
     SBP_CUDA(cudaStreamSynchronize(m->stream));
+    SBP_TRY(ensure_capacity(m, B_new));  // dense or sparse for the new B
     m->B = B_new;
     return rebuild_blockmodel(m);
 }
@@ -206,6 +207,7 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     cudaFree(m->vcount);
     cudaFree(m->movers);
     cudaFree(m->mcount);
+    free_sparse(m);
     cudaFreeHost(m->pinned);
     delete m;
 }
@@ -492,6 +494,43 @@ extern "C" int sbp_get_blockmodel_dense(const sbp_model_t *m, int32_t *M_out) {
     if (!m->dense) return fail(SBP_ESTATE, "sbp_get_blockmodel_dense: model is not dense");
     SBP_CUDA(cudaMemcpyAsync(M_out, m->M, (size_t)m->B * m->B * 4, kind_from_dev(M_out), m->stream));
     return check_status(m);
+}
+
+extern "C" int sbp_get_blockmodel_coo(const sbp_model_t *m, int64_t capacity, int64_t *keys, int32_t *counts,
+                                      int64_t *nnz) {
+    if (!m || !nnz) return fail(SBP_EINVAL, "sbp_get_blockmodel_coo: NULL argument");
+    SBP_TRY(check_status(m));
+    const int64_t B = m->B;
+    std::vector<int64_t> k;
+    std::vector<int32_t> c;
+    if (m->dense) {
+        std::vector<int32_t> M((size_t)(B * B));
+        SBP_CUDA(cudaMemcpy(M.data(), m->M, M.size() * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < B * B; ++i)
+            if (M[(size_t)i]) {
+                k.push_back(i);
+                c.push_back(M[(size_t)i]);
+            }
+    } else {
+        const int64_t z = m->sp.nnz;
+        std::vector<uint32_t> rp((size_t)B + 1);
+        std::vector<int32_t> rc((size_t)z), rv((size_t)z);
+        SBP_CUDA(cudaMemcpy(rp.data(), m->sp.rp, rp.size() * 4, cudaMemcpyDeviceToHost));
+        if (z > 0) {
+            SBP_CUDA(cudaMemcpy(rc.data(), m->sp.rc, (size_t)z * 4, cudaMemcpyDeviceToHost));
+            SBP_CUDA(cudaMemcpy(rv.data(), m->sp.rv, (size_t)z * 4, cudaMemcpyDeviceToHost));
+        }
+        for (int64_t r = 0; r < B; ++r)
+            for (uint32_t i = rp[(size_t)r]; i < rp[(size_t)r + 1]; ++i) {
+                k.push_back(r * B + rc[i]);
+                c.push_back(rv[i]);
+            }
+    }
+    *nnz = (int64_t)k.size();
+    if ((int64_t)k.size() > capacity) return fail(SBP_EINVAL, "sbp_get_blockmodel_coo: capacity too small");
+    if (keys && !k.empty()) std::memcpy(keys, k.data(), k.size() * 8);
+    if (counts && !c.empty()) std::memcpy(counts, c.data(), c.size() * 4);
+    return SBP_OK;
 }
 
 extern "C" int sbp_get_degrees(const sbp_model_t *m, int32_t *dout, int32_t *din) {

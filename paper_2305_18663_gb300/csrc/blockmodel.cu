@@ -222,60 +222,81 @@ int num_sms() {
 }  // namespace
 
 int ensure_capacity(sbp_model *m, int32_t B) {
-    if (B > m->p.dense_max_B)
-        return fail(SBP_ESTATE, "B = " + std::to_string(B) + " exceeds dense_max_B; only dense blockmodels are built");
-    m->dense = true;
-    if (B <= m->Bcap) return SBP_OK;
-    cudaFree(m->M);
-    cudaFree(m->P);
-    cudaFree(m->Pc);
-    cudaFree(m->dout);
-    cudaFree(m->din);
-    cudaFree(m->rcp);
-    cudaFree(m->rcp32);
-    cudaFree(m->dsum);
-    cudaFree(m->best_s);
-    cudaFree(m->best_d);
-    cudaFree(m->map);
-    cudaFree(m->vcount);
-    m->M = nullptr; m->P = nullptr; m->Pc = nullptr; m->dout = m->din = nullptr; m->rcp = nullptr; m->rcp32 = nullptr; m->dsum = nullptr;
-    m->best_s = m->map = m->vcount = nullptr; m->best_d = nullptr;
-    m->Bcap = 0;
-    const size_t BB = (size_t)B * B;
-    if (cudaMalloc(&m->M, BB * 4) != cudaSuccess || cudaMalloc(&m->P, BB * 8) != cudaSuccess ||
-        cudaMalloc(&m->Pc, (size_t)B * 32 * 4) != cudaSuccess ||
-        cudaMalloc(&m->dout, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->din, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->rcp32, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&m->dsum, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&m->best_d, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->map, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&m->vcount, (size_t)B * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(SBP_ENOMEM, "cudaMalloc failed for a blockmodel of B = " + std::to_string(B));
+    m->dense = B <= m->p.dense_max_B;
+    if (!m->dense) SBP_TRY(ensure_sparse_capacity(m, B));
+    const bool need_dense = m->dense && B > m->Bdense;
+    if (B <= m->Bcap && !need_dense) return SBP_OK;
+    if (need_dense) {
+        cudaFree(m->M);
+        cudaFree(m->P);
+        cudaFree(m->Pc);
+        m->M = nullptr; m->P = nullptr; m->Pc = nullptr;
+        m->Bdense = 0;
+        const size_t BB = (size_t)B * B;
+        if (cudaMalloc(&m->M, BB * 4) != cudaSuccess || cudaMalloc(&m->P, BB * 8) != cudaSuccess ||
+            cudaMalloc(&m->Pc, (size_t)B * 32 * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SBP_ENOMEM, "cudaMalloc failed for a dense blockmodel of B = " + std::to_string(B));
+        }
+        m->Bdense = B;
     }
-    m->Bcap = B;
+    if (B > m->Bcap) {
+        cudaFree(m->dout);
+        cudaFree(m->din);
+        cudaFree(m->rcp);
+        cudaFree(m->rcp32);
+        cudaFree(m->dsum);
+        cudaFree(m->best_s);
+        cudaFree(m->best_d);
+        cudaFree(m->map);
+        cudaFree(m->vcount);
+        m->dout = m->din = nullptr; m->rcp = nullptr; m->rcp32 = nullptr; m->dsum = nullptr;
+        m->best_s = m->map = m->vcount = nullptr; m->best_d = nullptr;
+        m->Bcap = 0;
+        if (cudaMalloc(&m->dout, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->din, (size_t)B * 4) != cudaSuccess ||
+            cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->rcp32, (size_t)B * 4) != cudaSuccess ||
+            cudaMalloc(&m->dsum, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
+            cudaMalloc(&m->best_d, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->map, (size_t)B * 4) != cudaSuccess ||
+            cudaMalloc(&m->vcount, (size_t)B * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SBP_ENOMEM, "cudaMalloc failed for the block arrays of B = " + std::to_string(B));
+        }
+        m->Bcap = B;
+    }
     return SBP_OK;
 }
 
 int rebuild_blockmodel(sbp_model *m) {
     const sbp_graph *g = m->g;
     const int B = m->B;
-    const int64_t BB = (int64_t)B * B;
     const int sms = num_sms();
     SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
-    SBP_CUDA(cudaMemsetAsync(m->M, 0, (size_t)BB * 4, m->stream));
-    if (g->m > 0) {
-        const size_t smem = (size_t)B * 4;
-        if (smem > 48 * 1024) SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B);
+    const int32_t *vals;
+    int64_t nvals;
+    if (m->dense) {
+        const int64_t BB = (int64_t)B * B;
+        SBP_CUDA(cudaMemsetAsync(m->M, 0, (size_t)BB * 4, m->stream));
+        if (g->m > 0) {
+            const size_t smem = (size_t)B * 4;
+            if (smem > 48 * 1024)
+                SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M,
+                                                                                                      B);
+            SBP_CUDA(cudaGetLastError());
+        }
+        k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
+            m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
         SBP_CUDA(cudaGetLastError());
+        vals = m->M;
+        nvals = BB;
+    } else {
+        SBP_TRY(rebuild_sparse(m));
+        vals = m->sp.rv;
+        nvals = m->sp.nnz;
     }
-    k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(m->M, B, m->P, m->dout,
-                                                                                          m->din, m->rcp, m->rcp32, m->dsum, m->Pc,
-                                                                                          (2 * B + 31) / 32);
-    SBP_CUDA(cudaGetLastError());
-    const int np = grid_for(BB, kThreads * 4, m->npartials);
+    const int np = grid_for(nvals > B ? nvals : B, kThreads * 4, m->npartials);
     DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
-    k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->T, m->XT, parts);
+    k_dl_partial<<<np, kThreads, 0, m->stream>>>(vals, nvals, m->dout, m->din, B, m->T, m->XT, parts);
     SBP_CUDA(cudaGetLastError());
     k_dl_final<<<1, 32, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
     SBP_CUDA(cudaGetLastError());

@@ -92,6 +92,14 @@ struct ModelDev {
     const int32_t *dsum;    // dout_t + din_t
     const __int128 *T;      // round(x ln x * 2^64), x < XT
     int64_t XT;
+    // sparse form (B > dense_max_B): CSR and CSC of M with per-row / per-column
+    // inclusive count prefixes, and per-row open-addressing tables
+    int sparse;
+    const uint32_t *rp, *cp, *hoff;   // [B+1]
+    const int32_t *rc, *cr;           // column of each row entry, row of each column entry
+    const int32_t *rv, *cv;           // their counts
+    const uint32_t *rpre, *cpre;      // inclusive count prefixes inside each row / column
+    const int32_t *hk, *hv;           // table keys (-1 empty) and counts
     int32_t *status;
     DevCounters *counters;
 };
@@ -99,10 +107,23 @@ struct ModelDev {
 }  // namespace sbp
 
 struct sbp_model {
+    struct Sparse {
+        int64_t cap_e = 0, nnz = 0;
+        int32_t cap_b = 0;
+        uint64_t *key0 = nullptr, *key1 = nullptr;
+        uint32_t *flag = nullptr, *pos = nullptr, *start = nullptr, *scratch = nullptr;
+        int32_t *rc = nullptr, *rv = nullptr, *rowof = nullptr, *cr = nullptr, *cv = nullptr;
+        uint32_t *rpre = nullptr, *cpre = nullptr;
+        uint32_t *ckey0 = nullptr, *ckey1 = nullptr;
+        uint64_t *cval0 = nullptr, *cval1 = nullptr;
+        int32_t *hk = nullptr, *hv = nullptr;
+        uint32_t *rp = nullptr, *cp = nullptr, *hoff = nullptr, *cnt = nullptr;
+    };
+    Sparse sp;
     const sbp_graph *g = nullptr;
     sbp_params p{};
     cudaStream_t stream = nullptr;
-    int32_t B = 0, Bcap = 0;
+    int32_t B = 0, Bcap = 0, Bdense = 0;
     int32_t *b = nullptr, *bnew = nullptr;
     int32_t *M = nullptr;
     uint32_t *P = nullptr;
@@ -276,6 +297,69 @@ __device__ __forceinline__ int warp_cdf_search(const uint32_t *__restrict__ Pu, 
 }
 
 // ---------------------------------------------------------------------------
+// blockmodel access (dense or sparse, a kernel-wide flag)
+
+__device__ __forceinline__ unsigned sparse_hash(int key) { return (unsigned)key * 0x9E3779B1u; }
+
+// M[r][c] from row r's table (bounded probe; absent = 0)
+__device__ __forceinline__ int sparse_at(const ModelDev &md, int r, int c) {
+    const uint32_t off = md.hoff[r], cap = md.hoff[r + 1] - off;
+    uint32_t h = sparse_hash(c) & (cap - 1);
+    for (uint32_t q = 0; q < cap; ++q) {
+        const int k = md.hk[off + h];
+        if (k == c) return md.hv[off + h];
+        if (k < 0) return 0;
+        h = (h + 1) & (cap - 1);
+    }
+    return 0;
+}
+
+__device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) {
+    return md.sparse ? sparse_at(md, r, c) : md.M[(size_t)r * md.B + c];
+}
+
+// first i in a[lo, hi) with a[i] > t (one lane, binary search)
+__device__ __forceinline__ uint32_t lane_upper(const uint32_t *__restrict__ a, uint32_t lo, uint32_t hi, uint32_t t) {
+    uint32_t n = hi - lo;
+    while (n > 0) {
+        const uint32_t half = n >> 1;
+        if (a[lo + half] <= t) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// first i in a[lo, hi) with a[i] >= t (one lane)
+__device__ __forceinline__ uint32_t lane_lower_i32(const int32_t *__restrict__ a, uint32_t lo, uint32_t hi, int32_t t) {
+    uint32_t n = hi - lo;
+    while (n > 0) {
+        const uint32_t half = n >> 1;
+        if (a[lo + half] < t) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// Sparse inverse CDF over row u then column u of M (weights M[u][c], then
+// M[c][u]), t < dout_u + din_u: the block at that position.  One lane.
+__device__ __forceinline__ int sparse_cdf_block(const ModelDev &md, int u, uint32_t t, uint32_t dout_u) {
+    if (t < dout_u) {
+        const uint32_t i = lane_upper(md.rpre, md.rp[u], md.rp[u + 1], t);
+        return md.rc[i];
+    }
+    const uint32_t i = lane_upper(md.cpre, md.cp[u], md.cp[u + 1], t - dout_u);
+    return md.cr[i];
+}
+
+// ---------------------------------------------------------------------------
 // host-side launch helpers implemented in the .cu files
 int rebuild_blockmodel(sbp_model *m);  // M, P, degrees, rcp, DL from m->b
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
@@ -285,5 +369,9 @@ int launch_vertex_count(sbp_model *m);
 int ensure_capacity(sbp_model *m, int32_t B);
 int check_status(const sbp_model *m);
 int xlogx_table(int64_t need, const __int128 **table, int64_t *size);
+int ensure_sparse_capacity(sbp_model *m, int32_t B);
+int rebuild_sparse(sbp_model *m);
+void free_sparse(sbp_model *m);
+ModelDev model_dev(sbp_model *m);
 
 }  // namespace sbp

@@ -19,31 +19,47 @@
 #include "common.cuh"
 
 namespace sbp {
-ModelDev model_dev(sbp_model *m);
-
 namespace {
-
-__device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) { return md.M[(size_t)r * md.B + c]; }
 
 __device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1) {
     const int B = md.B;
-    const uint32_t *Pr = md.P + (size_t)r * 2 * B;
     const int64_t dr = (int64_t)md.dout[r] + md.din[r];
     if (dr == 0) {
         const int64_t y = draw_below(w1, (uint64_t)(B - 1));
         return (int)(y + (y >= r));
     }
     const int64_t t0 = draw_below(w0, (uint64_t)dr);
-    int u = warp_cdf_search(Pr, md.Pc + (size_t)r * 32, 2 * B, md.pstep, (uint32_t)t0);
-    if (u >= B) u -= B;
+    int u;
+    if (md.sparse) {
+        u = sparse_cdf_block(md, r, (uint32_t)t0, (uint32_t)md.dout[r]);
+    } else {
+        u = warp_cdf_search(md.P + (size_t)r * 2 * B, md.Pc + (size_t)r * 32, 2 * B, md.pstep, (uint32_t)t0);
+        if (u >= B) u -= B;
+    }
     const int64_t Mur = Mat(md, u, r), Mru = Mat(md, r, u);
     const int64_t du_out = md.dout[u], du = du_out + md.din[u];
     const int64_t W = (B - 1) + du - Mur - Mru;
     const int64_t y = draw_below(w1, (uint64_t)W);
     if (y < B - 1) return (int)(y + (y >= r));
-    const uint32_t *Pu = md.P + (size_t)u * 2 * B;
     const int64_t t = y - (B - 1);
     const int64_t row_w = du_out - Mur;
+    if (md.sparse) {
+        // the same walks over the nonzeros of row u / column u, entry r left out
+        if (t < row_w) {
+            const uint32_t a = md.rp[u], z = md.rp[u + 1];
+            const uint32_t pos = lane_lower_i32(md.rc, a, z, r);
+            const int64_t pre = pos > a ? (int64_t)md.rpre[pos - 1] : 0;
+            const int64_t tt = t >= pre ? t + Mur : t;
+            return md.rc[lane_upper(md.rpre, a, z, (uint32_t)tt)];
+        }
+        const int64_t tc = t - row_w;
+        const uint32_t a = md.cp[u], z = md.cp[u + 1];
+        const uint32_t pos = lane_lower_i32(md.cr, a, z, r);
+        const int64_t pre = pos > a ? (int64_t)md.cpre[pos - 1] : 0;
+        const int64_t tt = tc >= pre ? tc + Mru : tc;
+        return md.cr[lane_upper(md.cpre, a, z, (uint32_t)tt)];
+    }
+    const uint32_t *Pu = md.P + (size_t)u * 2 * B;
     if (t < row_w) {
         // row u with column r left out
         const int64_t pre = r > 0 ? (int64_t)Pu[r - 1] : 0;
@@ -60,12 +76,25 @@ __device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1
 __device__ double merge_delta(const ModelDev &md, int r, int s) {
     const int B = md.B, lane = threadIdx.x & 31;
     double acc = 0.0;
-    for (int t = lane; t < B; t += 32) {
-        if (t == r || t == s) continue;
-        const int Mrt = Mat(md, r, t);
-        if (Mrt) acc += gmerge(Mat(md, s, t), Mrt);
-        const int Mtr = Mat(md, t, r);
-        if (Mtr) acc += gmerge(Mat(md, t, s), Mtr);
+    if (md.sparse) {
+        for (uint32_t i = md.rp[r] + lane; i < md.rp[r + 1]; i += 32) {
+            const int t = md.rc[i];
+            if (t == r || t == s) continue;
+            acc += gmerge(Mat(md, s, t), md.rv[i]);
+        }
+        for (uint32_t i = md.cp[r] + lane; i < md.cp[r + 1]; i += 32) {
+            const int t = md.cr[i];
+            if (t == r || t == s) continue;
+            acc += gmerge(Mat(md, t, s), md.cv[i]);
+        }
+    } else {
+        for (int t = lane; t < B; t += 32) {
+            if (t == r || t == s) continue;
+            const int Mrt = Mat(md, r, t);
+            if (Mrt) acc += gmerge(Mat(md, s, t), Mrt);
+            const int Mtr = Mat(md, t, r);
+            if (Mtr) acc += gmerge(Mat(md, t, s), Mtr);
+        }
     }
     acc = warp_sum(acc);
     const int64_t a = Mat(md, r, r), b = Mat(md, r, s), c = Mat(md, s, r), d = Mat(md, s, s);

@@ -70,7 +70,6 @@ __device__ __forceinline__ void write_trace(const DecideArgs &a, int v, int s, i
     if (a.tr.logA) a.tr.logA[v] = logA;
 }
 
-__device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) { return md.M[(size_t)r * md.B + c]; }
 
 // Per-vertex scalars shared by the evaluation steps.
 struct VertexCtx {
@@ -114,7 +113,7 @@ __device__ __forceinline__ int special_terms(const ModelDev &md, const VertexCtx
     const int rowi = (j == 0 || j == 2) ? r : s;
     const int coli = (j == 0 || j == 3) ? r : s;
     const int blk = (j == 4 || j == 6) ? r : s;
-    const int *ptr = j < 4 ? md.M + (size_t)rowi * B + coli : (j < 6 ? md.dout + blk : md.din + blk);
+    (void)B;
     const int kk = j == 0   ? -(cr + x.self)
                    : j == 1 ? cs + x.self
                    : j == 2 ? x.ki_r - x.ko_s
@@ -123,7 +122,8 @@ __device__ __forceinline__ int special_terms(const ModelDev &md, const VertexCtx
                    : j == 5 ? x.Kout
                    : j == 6 ? -x.Kin
                             : x.Kin;
-    const int val = *ptr;
+    // the corner entries through the blockmodel accessor (dense or sparse)
+    const int val = j < 4 ? Mat(md, rowi, coli) : (j < 6 ? md.dout[blk] : md.din[blk]);
     double f2 = 0.0;
     const __int128 d = dT(md.T, md.XT, val, kk, f2);
     dl += j < 4 ? d : -d;
@@ -356,6 +356,8 @@ __global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
                 const int64_t y = draw_below(w.y, (uint64_t)(du + B));
                 if (y < B) {
                     s = (int)y;
+                } else if (md.sparse) {
+                    s = sparse_cdf_block(md, u, (uint32_t)(y - B), (uint32_t)md.dout[u]);
                 } else {
                     const int idx = lane_cdf_search(md.P + (size_t)u * 2 * B, md.Pc + (size_t)u * 32, 2 * B, md.pstep,
                                                     (uint32_t)(y - B));
@@ -765,17 +767,14 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
 constexpr int kBatchEdges = 32 * kSmallDeg;
 
 struct BatchWarp {
-    int key[kBatchEdges];  // edge ends (q << 26 | self << 25 | t << 1 | in), then entries
+    int key[kBatchEdges];  // edge ends (q << 26 | self << 25 | t << 1 | in), then entries (q << 26 | t)
+    unsigned short ec[kBatchEdges];  // entry counts ko | ki << 8
     int r[32], s[32], rsr[32], rss[32], hasfb[32];
     long long dl[32];  // Delta L, fixed point 2^-48
     float pf[32], pb[32];
     double fb[32];
 };
 
-// entry: q (5 bits) | ko (6) | ki (6) | t (15)
-__device__ __forceinline__ unsigned pack_entry(int q, int t, int ko, int ki) {
-    return ((unsigned)q << 27) | ((unsigned)ko << 21) | ((unsigned)ki << 15) | (unsigned)t;
-}
 
 __device__ __forceinline__ float fix48_to_float(long long v) {
     return fmaf((float)(int)(v >> 32), 0x1p-16f, (float)(unsigned)(v & 0xffffffffu) * 0x1p-48f);
@@ -873,8 +872,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             const unsigned lm = __ballot_sync(0xffffffffu, leader);
             if (leader) {
                 const int ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                W.key[nent + __popc(lm & ((1u << lane) - 1u))] =
-                    (int)pack_entry((x >> 26) & 31, (x >> 1) & 0xffffff, ko, ki);
+                const int pos = nent + __popc(lm & ((1u << lane) - 1u));
+                W.key[pos] = (x & (31 << 26)) | ((x >> 1) & 0xffffff);
+                W.ec[pos] = (unsigned short)(ko | (ki << 8));
             }
             if (lane >= qa && lane <= qb) {
                 const int lo_l = first - fa, hi_l = incl - fa;
@@ -902,13 +902,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             const int e = base + lane;
             const bool valid = e < nent;
             const unsigned ent = valid ? (unsigned)W.key[e] : 0u;
-            const int q = valid ? (int)(ent >> 27) : 32;
+            const int q = valid ? (int)(ent >> 26) : 32;
             long long d48 = 0;
             float pfe = 0.0f, pbe = 0.0f;
             double f = 0.0;
             if (valid) {
-                const int t = (int)(ent & 0x7fffu);
-                const int ko = (int)((ent >> 21) & 63u), ki = (int)((ent >> 15) & 63u);
+                const int t = (int)(ent & 0x3ffffffu);
+                const unsigned ec = W.ec[e];
+                const int ko = (int)(ec & 0xffu), ki = (int)(ec >> 8);
                 const int rq = W.r[q], sq = W.s[q];
                 if (t == rq) {
                     W.rsr[q] = ko | (ki << 8);
@@ -990,10 +991,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             } else {
                 double pf64 = 0.0, pb64 = 0.0;
                 for (int e = my_est; e < my_est + my_ecnt; ++e) {
-                    const unsigned ent = (unsigned)W.key[e];
-                    const int t = (int)(ent & 0x7fffu);
+                    const int t = (int)((unsigned)W.key[e] & 0x3ffffffu);
                     if (t == r || t == s) continue;
-                    entry_exact(md, x, t, (int)((ent >> 21) & 63u), (int)((ent >> 15) & 63u), pf64, pb64);
+                    const unsigned ec = W.ec[e];
+                    entry_exact(md, x, t, (int)(ec & 0xffu), (int)(ec >> 8), pf64, pb64);
                 }
                 corner_hastings_exact(x, cv, B, pf64, pb64);
                 const Exact ex = exact_decision_d(a.beta, fix48_to_double(dl48) + (has_fb ? fb : 0.0), pf64, pb64, w2);
@@ -1038,6 +1039,18 @@ ModelDev model_dev(sbp_model *m) {
     d.dsum = m->dsum;
     d.T = m->T;
     d.XT = m->XT;
+    d.sparse = m->dense ? 0 : 1;
+    d.rp = m->sp.rp;
+    d.cp = m->sp.cp;
+    d.hoff = m->sp.hoff;
+    d.rc = m->sp.rc;
+    d.cr = m->sp.cr;
+    d.rv = m->sp.rv;
+    d.cv = m->sp.cv;
+    d.rpre = m->sp.rpre;
+    d.cpre = m->sp.cpre;
+    d.hk = m->sp.hk;
+    d.hv = m->sp.hv;
     d.status = m->status;
     d.counters = m->counters;
     return d;
@@ -1071,6 +1084,7 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.trace_on = (a.tr.s || a.tr.flags || a.tr.dH || a.tr.logA) ? 1 : 0;
     const int sms = sm_count();
     const int B = m->B;
+    if (B >= (1 << 24)) return fail(SBP_ESTATE, "nodal pass: B must be below 2^24");
     SBP_CUDA(cudaMemsetAsync(m->mcount, 0, 4 * sizeof(unsigned), m->stream));
 
     // proposals for every vertex of the range
@@ -1099,12 +1113,13 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     // movers with k > 128: per-warp tables sized for min(max degree, B)
     // distinct blocks while they fit, one CTA per mover beyond that
     if (g->bin[4] > g->bin[3]) {
-        const int64_t need = 2 * (int64_t)(g->max_deg < B ? g->max_deg : B) + 2;
+        const int64_t dmax = g->max_deg < B ? g->max_deg : B;
+        const int64_t need = dmax + dmax / 4 + 2;
         int cap_log2 = 6;
         while ((int64_t(1) << cap_log2) < need) ++cap_log2;
         const int cap = 1 << cap_log2;
         if (cap <= 4096 && g->max_deg < 65536) {
-            const int nwarps = cap <= 1024 ? 8 : 4;
+            const int nwarps = cap <= 2048 ? 8 : 4;
             const size_t smem = warp_smem(cap, nwarps);
             SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_eval_warp<<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);

@@ -62,18 +62,20 @@ def compare_decisions(od, gd, b, idx):
 
 def check_blockmodel(pm, om):
     assert pm.B == om.B
-    assert np.array_equal(pm.dense().astype(np.int64), om.dense())
+    keys, cnt = pm.coo()
+    okeys, ocnt = om.coo()
+    assert np.array_equal(keys, okeys) and np.array_equal(cnt.astype(np.int64), ocnt)
     dout, din = pm.degrees()
     odout, odin = om.degrees()
     assert np.array_equal(dout, odout) and np.array_equal(din, odin)
     assert pm.dl() == pytest.approx(om.dl(), rel=1e-12)
 
 
-def run_sweeps(g, B, b, sweeps, seed=7, first_sweep=0):
+def run_sweeps(g, B, b, sweeps, seed=7, first_sweep=0, dense_max_B=4096):
     G = O.Graph(g.n, g.src, g.dst)
     om = O.Model(G, B, b)
     pg = P.Graph(g.n, g.src, g.dst)
-    pm = P.Model(pg, B, b, P.Params.default(seed=seed))
+    pm = P.Model(pg, B, b, P.Params.default(seed=seed, dense_max_B=dense_max_B))
     check_blockmodel(pm, om)
     total_margin = 0
     for sw in range(first_sweep, first_sweep + sweeps):
@@ -108,22 +110,35 @@ def test_philox_device_matches_oracle():
             assert np.array_equal(got[i], O.philox4x64(c, key))
 
 
-@pytest.mark.parametrize("B", [1, 8, 64, 1000])
-def test_blockmodel_rebuild_matches_oracle(B):
+@pytest.mark.parametrize("B,dmax", [(1, 4096), (8, 4096), (64, 4096), (1000, 4096), (8, 4), (64, 16), (1000, 16)])
+def test_blockmodel_rebuild_matches_oracle(B, dmax):
     g = make_config("plain_1k")
     b = random_labels(g.n, B, seed=B) if B < g.n else np.arange(g.n, dtype=np.int32)
     G = O.Graph(g.n, g.src, g.dst)
     om = O.Model(G, B, b)
     pg = P.Graph(g.n, g.src, g.dst)
-    pm = P.Model(pg, B, b)
+    pm = P.Model(pg, B, b, P.Params.default(dense_max_B=dmax))
     check_blockmodel(pm, om)
-    assert pm.dense().sum() == g.m
+    assert pm.coo()[1].sum() == g.m
 
 
 @pytest.mark.parametrize("B", [8, 64])
 def test_nodal_sweeps_plain_1k(B):
     g = make_config("plain_1k")
     run_sweeps(g, B, random_labels(g.n, B, seed=B), sweeps=10)
+
+
+@pytest.mark.parametrize("B", [8, 64, 500])
+def test_nodal_sweeps_sparse_blockmodel(B):
+    # dense_max_B below B: per-row hashed sparse rows and CSR/CSC searches
+    g = make_config("plain_1k")
+    run_sweeps(g, B, random_labels(g.n, B, seed=B + 1), sweeps=6, dense_max_B=4)
+
+
+def test_nodal_sweeps_sparse_scaled_dcsbm():
+    g = make_config("plain_200k", scale=0.1)
+    b = perturb(g.planted, 100, 0.3, seed=0)
+    run_sweeps(g, 100, b, sweeps=2, dense_max_B=32)
 
 
 def test_nodal_sweeps_self_loops_duplicates_isolated():
@@ -246,14 +261,14 @@ def test_device_pointers_accepted():
 # ---------------------------------------------------------------------------
 # merge phase
 
-@pytest.mark.parametrize("B", [40, 1000])
-def test_merge_proposals_match_oracle(B):
+@pytest.mark.parametrize("B,dmax", [(40, 4096), (1000, 4096), (40, 8), (1000, 8)])
+def test_merge_proposals_match_oracle(B, dmax):
     g = make_config("plain_1k")
     b = random_labels(g.n, B, seed=5) if B < g.n else np.arange(g.n, dtype=np.int32)
     G = O.Graph(g.n, g.src, g.dst)
     om = O.Model(G, B, b)
     pg = P.Graph(g.n, g.src, g.dst)
-    pm = P.Model(pg, B, b, P.Params.default(seed=9))
+    pm = P.Model(pg, B, b, P.Params.default(seed=9, dense_max_B=dmax))
     bs = np.zeros(B, np.int32)
     bd = np.zeros(B, np.float64)
     P.sbp_merge_proposals(pm.h, 4, bs, bd)
@@ -267,12 +282,13 @@ def test_merge_proposals_match_oracle(B):
     assert diff.size <= max(2, B // 200)
 
 
-def test_merge_blocks_matches_oracle_application():
+@pytest.mark.parametrize("dmax", [4096, 16])
+def test_merge_blocks_matches_oracle_application(dmax):
     g = make_config("plain_1k")
     B = 200
     b = random_labels(g.n, B, seed=6)
     pg = P.Graph(g.n, g.src, g.dst)
-    pm = P.Model(pg, B, b, P.Params.default(seed=2))
+    pm = P.Model(pg, B, b, P.Params.default(seed=2, dense_max_B=dmax))
     bs = np.zeros(B, np.int32)
     bd = np.zeros(B, np.float64)
     P.sbp_merge_proposals(pm.h, 8, bs, bd)
@@ -296,12 +312,14 @@ def test_compact_drops_empty_blocks():
     assert Bo == 10 and np.array_equal(pm.assignment(), bo)
 
 
-def test_partition_plain_1k_matches_oracle():
+@pytest.mark.parametrize("dmax", [4096, 64])
+def test_partition_plain_1k_matches_oracle(dmax):
+    # dmax = 64: the run starts sparse at B = N and turns dense below 64
     g = make_config("plain_1k")
     G = O.Graph(g.n, g.src, g.dst)
     ob, oB, odl, ons = O.partition(G, O.Params(), nthreads=NT)
     pg = P.Graph(g.n, g.src, g.dst)
-    b, B, dl, ns = pg.partition(P.Params.default())
+    b, B, dl, ns = pg.partition(P.Params.default(dense_max_B=dmax))
     assert B == oB == 8
     assert dl == pytest.approx(odl, rel=1e-12)
     assert np.array_equal(b, ob)
