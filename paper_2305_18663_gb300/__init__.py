@@ -26,6 +26,7 @@ __all__ = [
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
+    "sbp_dense_dl_noalloc",
     "Graph", "Model", "deal_vertices",
 ]
 
@@ -119,6 +120,7 @@ def load(path: str | None = None):
         "sbp_sync": (C.c_int, [vp]),
         "sbp_free_model": (None, [vp]),
         "sbp_philox_check": (C.c_int, [u64, u64, u64, u64, u64, u64, i32, vp]),
+        "sbp_dense_dl_noalloc": (C.c_int, [vp, i32, vp, vp, i64, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -287,6 +289,13 @@ def sbp_sync(m: int) -> None:
 
 def sbp_free_model(m: int) -> None:
     lib().sbp_free_model(m)
+
+
+def sbp_dense_dl_noalloc(M, B: int, dout, din, E: int, N: int, dl_out, stream=None) -> None:
+    """DL of a dense blockmodel from caller-owned device buffers, without
+    allocating device memory (see include/sbp.h)."""
+    _check(lib().sbp_dense_dl_noalloc(_ptr(M, np.int32), B, _ptr(dout, np.int32), _ptr(din, np.int32), E, N,
+                                      _ptr(dl_out, np.float64), _stream_ptr(stream)))
 
 
 def sbp_philox_check(ctr, key, count: int = 1) -> np.ndarray:
