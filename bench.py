@@ -264,6 +264,47 @@ def run_cpu_oracle(args, name, scale, steps=1, warmup=0):
                       f"+ one full rebuild of M ({t_rebuild:.2f} s, single-threaded), scaled to a whole sweep"}, g, B
 
 
+def nmi(a, b) -> float:
+    """Normalised mutual information (arithmetic mean normalisation)."""
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    n = a.size
+    _, ai = np.unique(a, return_inverse=True)
+    _, bi = np.unique(b, return_inverse=True)
+    joint = np.zeros((ai.max() + 1, bi.max() + 1))
+    np.add.at(joint, (ai, bi), 1.0)
+    pa, pb, pj = joint.sum(1) / n, joint.sum(0) / n, joint / n
+    nz = pj > 0
+    mi = float(np.sum(pj[nz] * np.log(pj[nz] / np.outer(pa, pb)[nz])))
+    ha = -float(np.sum(pa[pa > 0] * np.log(pa[pa > 0])))
+    hb = -float(np.sum(pb[pb > 0] * np.log(pb[pb > 0])))
+    return 2 * mi / (ha + hb) if ha + hb > 0 else 1.0
+
+
+def run_partition(args):
+    """Full run (golden-ratio search from B = N) on one graph: wall time
+    through the C ABI with host buffers (graph upload included)."""
+    import torch
+
+    import paper_2305_18663_gb300 as P
+
+    torch.cuda.set_device(0)
+    P.load()
+    g = make_config(args.config, seed=0, scale=args.scale)
+    params = P.Params.default(seed=args.seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    graph = P.Graph(g.n, g.src, g.dst)
+    b, B, dl, sweeps = graph.partition(params)
+    wall = time.perf_counter() - t0
+    res = {"metric": "full partition runs/s", "value": 1.0 / wall, "unit": "graphs/s", "n_gpus": 1, "steps": 1,
+           "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": describe(args.config, g, CONFIGS[args.config]["n_blocks"], args.scale),
+           "result": {"B": B, "dl": dl, "sweeps": sweeps, "nmi_vs_planted": nmi(b, g.planted),
+                      "planted_B": CONFIGS[args.config]["n_blocks"]}}
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,7 +316,11 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--oracle-sample", type=int, default=50_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "partition"])
     args = ap.parse_args()
+    if args.mode == "partition":
+        run_partition(args)
+        return
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -324,3 +324,18 @@ def test_partition_plain_1k_matches_oracle(dmax):
     assert dl == pytest.approx(odl, rel=1e-12)
     assert np.array_equal(b, ob)
     assert ns == ons
+
+
+@pytest.mark.slow
+def test_partition_sparse_start_dcsbm_5k_matches_oracle():
+    # 5,000 vertices / 100,000 edges with the 2:1 weak structure: the run
+    # starts sparse at B = N = 5000, crosses to dense at B <= 256
+    g = make_config("plain_200k", scale=0.025)
+    G = O.Graph(g.n, g.src, g.dst)
+    ob, oB, odl, ons = O.partition(G, O.Params(), nthreads=NT)
+    pg = P.Graph(g.n, g.src, g.dst)
+    b, B, dl, ns = pg.partition(P.Params.default(dense_max_B=256))
+    assert B == oB
+    assert dl == pytest.approx(odl, rel=1e-12)
+    assert np.array_equal(b, ob)
+    assert ns == ons
