@@ -58,7 +58,10 @@ typedef struct sbp_model sbp_model_t;
  * merge_proposals: x of Alg. 1; reduction: share of blocks merged per merge
  * phase before the golden-ratio bracket exists; t_pre / t_post: convergence
  * threshold t of Alg. 2 before / after the bracket exists; max_sweeps: x of
- * Alg. 2; dense_max_B: largest B held as a dense B x B matrix. */
+ * Alg. 2; dense_max_B: largest B held as a dense B x B matrix;
+ * full_rebuild: 0 lets a commit of a dense model update M from the moved
+ * vertices' rows when they hold at most E/8 edge ends (the apply step of
+ * Alg. 5, same result), 1 always recounts M from all edges. */
 typedef struct sbp_params {
     uint64_t seed;
     double beta;
@@ -68,7 +71,7 @@ typedef struct sbp_params {
     double t_pre;
     double t_post;
     int32_t dense_max_B;
-    int32_t reserved;
+    int32_t full_rebuild;
 } sbp_params;
 
 /* Counters of one nodal pass.  n_proposed: vertices with at least one edge

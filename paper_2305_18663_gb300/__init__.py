@@ -49,7 +49,7 @@ class Params(C.Structure):
         ("t_pre", C.c_double),
         ("t_post", C.c_double),
         ("dense_max_B", C.c_int32),
-        ("reserved", C.c_int32),
+        ("full_rebuild", C.c_int32),
     ]
 
     @classmethod

@@ -61,6 +61,7 @@ int validate_params(const sbp_params &p) {
     if (!(p.reduction > 0 && p.reduction < 1)) return fail(SBP_EINVAL, "params: reduction must be in (0, 1)");
     if (!(p.t_pre > 0) || !(p.t_post > 0)) return fail(SBP_EINVAL, "params: thresholds must be > 0");
     if (p.dense_max_B < 1 || p.dense_max_B > 16384) return fail(SBP_EINVAL, "params: dense_max_B must be in [1, 16384]");
+    if (p.full_rebuild != 0 && p.full_rebuild != 1) return fail(SBP_EINVAL, "params: full_rebuild must be 0 or 1");
     return SBP_OK;
 }
 
@@ -230,7 +231,7 @@ extern "C" int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32
     const size_t n = (size_t)g->n;
     if (cudaMalloc(&m->b, n * 4) != cudaSuccess || cudaMalloc(&m->bnew, n * 4) != cudaSuccess ||
         cudaMalloc(&m->dl, 16) != cudaSuccess || cudaMalloc(&m->partials, (size_t)m->npartials * 32) != cudaSuccess ||
-        cudaMalloc(&m->counters, sizeof(DevCounters)) != cudaSuccess || cudaMalloc(&m->status, 4) != cudaSuccess ||
+        cudaMalloc(&m->counters, sizeof(DevCounters)) != cudaSuccess || cudaMalloc(&m->status, 8) != cudaSuccess ||
         cudaMallocHost(&m->pinned, 4096) != cudaSuccess) {
         cudaGetLastError();
         sbp_free_model(m);
@@ -270,7 +271,7 @@ extern "C" int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats) {
     if (!m) return fail(SBP_EINVAL, "sbp_commit: NULL model");
     std::swap(m->b, m->bnew);
     SBP_CUDA(cudaMemcpyAsync(m->dl + 1, m->dl, 8, cudaMemcpyDeviceToDevice, m->stream));
-    SBP_TRY(rebuild_blockmodel(m));
+    SBP_TRY(commit_blockmodel(m));
     if (stats) SBP_TRY(read_stats(m, stats));
     SBP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream));
     return SBP_OK;

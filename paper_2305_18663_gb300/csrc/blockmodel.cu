@@ -33,7 +33,8 @@ __device__ __forceinline__ void hist_add(int32_t *__restrict__ M, int *diag, int
 }
 
 __global__ void __launch_bounds__(kThreads) k_hist_dense(GraphDev g, const int32_t *__restrict__ b,
-                                                         int32_t *__restrict__ M, int B) {
+                                                         int32_t *__restrict__ M, int B, const int32_t *__restrict__ skip) {
+    if (skip && *skip == 1) return;
     extern __shared__ int diag[];
     for (int i = threadIdx.x; i < B; i += blockDim.x) diag[i] = 0;
     __syncthreads();
@@ -170,23 +171,84 @@ __global__ void __launch_bounds__(kThreads) k_dl_partial(const int32_t *__restri
     }
 }
 
-// Eq. 2: DL = E h(B^2/E) + N ln B - L, h(x) = (1+x) ln(1+x) - x ln x
-__global__ void k_dl_final(const DlPartial *__restrict__ partials, int np, int64_t E, int64_t N, int B,
-                           double *__restrict__ dl) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Eq. 2: DL = E h(B^2/E) + N ln B - L, h(x) = (1+x) ln(1+x) - x ln x.  The
+// partials are summed in a fixed order (strided per thread, then a fixed
+// tree), so the result is reproducible bit for bit.
+__global__ void __launch_bounds__(kThreads) k_dl_final(const DlPartial *__restrict__ partials, int np, int64_t E,
+                                                       int64_t N, int B, double *__restrict__ dl) {
+    __shared__ __int128 sfix[kThreads];
+    __shared__ double sfb[kThreads];
     __int128 f = 0;
     double d = 0.0;
-    for (int i = 0; i < np; ++i) {
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
         f += partials[i].fix;
         d += partials[i].fb;
     }
-    const double L = fix_to_double(f) + d;
-    double model = 0.0;
-    if (E > 0) {
-        const double x = (double)B * (double)B / (double)E;
-        model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
+    sfix[threadIdx.x] = f;
+    sfb[threadIdx.x] = d;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sfix[threadIdx.x] += sfix[threadIdx.x + o];
+            sfb[threadIdx.x] += sfb[threadIdx.x + o];
+        }
+        __syncthreads();
     }
-    dl[0] = model + (double)N * log((double)B) - L;
+    if (threadIdx.x == 0) {
+        const double L = fix_to_double(sfix[0]) + sfb[0];
+        double model = 0.0;
+        if (E > 0) {
+            const double x = (double)B * (double)B / (double)E;
+            model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
+        }
+        dl[0] = model + (double)N * log((double)B) - L;
+    }
+}
+
+// commit plan: 1 = update M from the moved vertices' rows, 0 = recount
+__global__ void k_commit_plan(const DevCounters *__restrict__ c, int64_t E, int32_t *__restrict__ flag) {
+    flag[0] = (c->acc_edges * 8ull <= (unsigned long long)E) ? 1 : 0;
+}
+
+__global__ void k_zero_if(int32_t *__restrict__ M, int64_t n, const int32_t *__restrict__ flag, int want) {
+    if (*flag != want) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) M[i] = 0;
+}
+
+// Apply step of Alg. 5 on a dense M: every edge with a moved end leaves its
+// old (block, block) cell and enters the new one.  An edge is visited once:
+// through the out-row of its moved source, or through the in-row of its
+// moved target when the source stayed.
+__global__ void __launch_bounds__(kThreads) k_delta_dense(GraphDev g, const int32_t *__restrict__ bnew,
+                                                          const int32_t *__restrict__ bold, int32_t *__restrict__ M,
+                                                          int B, const int32_t *__restrict__ flag) {
+    if (*flag != 1) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; base < g.n; base += nw * 32) {
+        const int64_t vv = base + lane;
+        const bool moved = vv < g.n && bnew[vv] != bold[vv];
+        unsigned mm = __ballot_sync(0xffffffffu, moved);
+        while (mm) {
+            const int q = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int v = (int)(base + q);
+            const int r = bold[v], s = bnew[v];
+            for (int e = g.op[v] + lane; e < g.op[v + 1]; e += 32) {
+                const int w = g.oc[e];
+                atomicAdd(&M[(size_t)r * B + bold[w]], -1);
+                atomicAdd(&M[(size_t)s * B + bnew[w]], 1);
+            }
+            for (int e = g.ip[v] + lane; e < g.ip[v + 1]; e += 32) {
+                const int w = g.ic[e];
+                const int t = bold[w];
+                if (bnew[w] == t) {
+                    atomicAdd(&M[(size_t)t * B + r], -1);
+                    atomicAdd(&M[(size_t)t * B + s], 1);
+                }
+            }
+        }
+    }
 }
 
 __global__ void k_relabel(int32_t *__restrict__ b, int32_t *__restrict__ bnew, int n, const int32_t *__restrict__ map) {
@@ -281,7 +343,7 @@ int rebuild_blockmodel(sbp_model *m) {
             if (smem > 48 * 1024)
                 SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M,
-                                                                                                      B);
+                                                                                                      B, nullptr);
             SBP_CUDA(cudaGetLastError());
         }
         k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
@@ -298,7 +360,46 @@ int rebuild_blockmodel(sbp_model *m) {
     DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
     k_dl_partial<<<np, kThreads, 0, m->stream>>>(vals, nvals, m->dout, m->din, B, m->T, m->XT, parts);
     SBP_CUDA(cudaGetLastError());
-    k_dl_final<<<1, 32, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
+    k_dl_final<<<1, kThreads, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
+    SBP_CUDA(cudaGetLastError());
+    SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
+    return SBP_OK;
+}
+
+// After a nodal pass (m->b: new labels, m->bnew: the previous ones).  A
+// dense model takes the incremental update when the plan kernel finds few
+// moved edges (decided on the device, no host round trip); the result is
+// the same M as a recount.
+int commit_blockmodel(sbp_model *m) {
+    if (!m->dense || m->p.full_rebuild) return rebuild_blockmodel(m);
+    const sbp_graph *g = m->g;
+    const int B = m->B;
+    const int sms = num_sms();
+    const int64_t BB = (int64_t)B * B;
+    int32_t *flag = m->status + 1;
+    SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
+    k_commit_plan<<<1, 1, 0, m->stream>>>(m->counters, g->m, flag);
+    SBP_CUDA(cudaGetLastError());
+    k_zero_if<<<grid_for(BB, kThreads, sms * 8), kThreads, 0, m->stream>>>(m->M, BB, flag, 0);
+    SBP_CUDA(cudaGetLastError());
+    if (g->m > 0) {
+        const size_t smem = (size_t)B * 4;
+        if (smem > 48 * 1024)
+            SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B,
+                                                                                                  flag);
+        SBP_CUDA(cudaGetLastError());
+        k_delta_dense<<<sms * 4, kThreads, 0, m->stream>>>(g->dev(), m->b, m->bnew, m->M, B, flag);
+        SBP_CUDA(cudaGetLastError());
+    }
+    k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
+        m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
+    SBP_CUDA(cudaGetLastError());
+    const int np = grid_for(BB > B ? BB : B, kThreads * 4, m->npartials);
+    DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
+    k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->T, m->XT, parts);
+    SBP_CUDA(cudaGetLastError());
+    k_dl_final<<<1, kThreads, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
     SBP_CUDA(cudaGetLastError());
     SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
     return SBP_OK;

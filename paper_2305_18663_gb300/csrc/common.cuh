@@ -73,7 +73,7 @@ namespace sbp {
 
 // device-side counters of a decision pass: proposed, moves, accepted, margin
 struct DevCounters {
-    unsigned long long proposed, moves, accepted, margin, move_edges;
+    unsigned long long proposed, moves, accepted, margin, move_edges, acc_edges;
 };
 
 struct ModelDev {
@@ -362,6 +362,7 @@ __device__ __forceinline__ int sparse_cdf_block(const ModelDev &md, int u, uint3
 // ---------------------------------------------------------------------------
 // host-side launch helpers implemented in the .cu files
 int rebuild_blockmodel(sbp_model *m);  // M, P, degrees, rcp, DL from m->b
+int commit_blockmodel(sbp_model *m);   // the same after a pass: m->b new labels, m->bnew the previous ones
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
 int launch_merge_proposals(sbp_model *m, uint64_t round_id);
 int launch_relabel(sbp_model *m, const int32_t *map_dev);

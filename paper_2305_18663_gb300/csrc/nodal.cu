@@ -60,7 +60,7 @@ struct DecideArgs {
 };
 
 struct Counts {
-    unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0;
+    unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0;
 };
 
 __device__ __forceinline__ void write_trace(const DecideArgs &a, int v, int s, int flags, double dH, double logA) {
@@ -245,11 +245,12 @@ __device__ __forceinline__ bool table_add32(int *keys, unsigned *cnt, unsigned s
     return false;
 }
 
-__device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin) {
+__device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin, int k) {
     c.proposed++;
     c.moves++;
     c.accepted += accept;
     c.margin += margin;
+    c.acc_edges += accept ? (unsigned long long)k : 0ull;
 }
 
 // ---------------------------------------------------------------------------
@@ -261,6 +262,7 @@ __device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c
         atomicAdd(&md.counters->moves, c.moves);
         atomicAdd(&md.counters->accepted, c.accepted);
         atomicAdd(&md.counters->margin, c.margin);
+        if (c.acc_edges) atomicAdd(&md.counters->acc_edges, c.acc_edges);
     }
 }
 
@@ -271,6 +273,7 @@ __device__ __forceinline__ void flush_counts_warp(const ModelDev &md, Counts c, 
         c.moves += __shfl_xor_sync(0xffffffffu, c.moves, o);
         c.accepted += __shfl_xor_sync(0xffffffffu, c.accepted, o);
         c.margin += __shfl_xor_sync(0xffffffffu, c.margin, o);
+        c.acc_edges += __shfl_xor_sync(0xffffffffu, c.acc_edges, o);
         extra_edges += __shfl_xor_sync(0xffffffffu, extra_edges, o);
     }
     if ((threadIdx.x & 31) == 0) {
@@ -453,7 +456,7 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     if (dec >= 0) {
         if (lane == 0) {
             if (dec) md.bnew[x.v] = x.s;
-            count_result(c, dec != 0, false);
+            count_result(c, dec != 0, false, x.k);
         }
         return;
     }
@@ -467,7 +470,7 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     if (lane == 0) {
         const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
         if (e.accept) md.bnew[x.v] = x.s;
-        count_result(c, e.accept, e.margin);
+        count_result(c, e.accept, e.margin, x.k);
         write_trace(a, x.v, x.s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
     }
 }
@@ -701,7 +704,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
             sh.dec = dec;
             if (dec >= 0) {
                 if (dec) md.bnew[v] = s;
-                count_result(c, dec != 0, false);
+                count_result(c, dec != 0, false, x.k);
             }
         }
         __syncthreads();
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
                 corner_hastings_exact(x, cv, md.B, pft, pbt);
                 const Exact e = exact_decision(a.beta, sh.dl_tot, sh.fb_tot, pft, pbt, mv.w2);
                 if (e.accept) md.bnew[v] = s;
-                count_result(c, e.accept, e.margin);
+                count_result(c, e.accept, e.margin, k);
                 write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
             }
         }
@@ -765,6 +768,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
 //      FP64 recheck (sequential over the mover's entries) when needed.
 
 constexpr int kBatchEdges = 32 * kSmallDeg;
+constexpr int kDirectMaxB = 2048;  // direct-mapped per-warp counts up to this B
 
 struct BatchWarp {
     int key[kBatchEdges];  // edge ends (q << 26 | self << 25 | t << 1 | in), then entries (q << 26 | t)
@@ -783,15 +787,28 @@ __device__ __forceinline__ double fix48_to_double(long long v) {
     return (double)(int)(v >> 32) * 0x1p-16 + (double)(unsigned)(v & 0xffffffffu) * 0x1p-48;
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_batch(DecideArgs a) {
+// MODE 0: rows of at most 32 edges (aggregated in windows of whole rows);
+// MODE 1: rows of 33..128 edges (aggregated per mover in a direct-mapped
+// count array of B entries, which follows the warp's BatchWarp in shared
+// memory).  Movers are processed in sub-batches of at most kBatchEdges
+// edge ends.
+template <int MODE>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_batch(DecideArgs a, int bin,
+                                                                                     int warp_bytes) {
     extern __shared__ __align__(16) unsigned char bsm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    BatchWarp &W = reinterpret_cast<BatchWarp *>(bsm)[wid];
+    BatchWarp &W = *reinterpret_cast<BatchWarp *>(bsm + (size_t)wid * warp_bytes);
+    unsigned *dcnt = reinterpret_cast<unsigned *>(bsm + (size_t)wid * warp_bytes + sizeof(BatchWarp));
     const GraphDev &g = a.g;
     const ModelDev &md = a.md;
     const int B = md.B;
-    const Mover *mlist = a.movers + a.mbase[0];
-    const int64_t count = *(volatile unsigned *)&a.mcount[0];
+    int *dlist = reinterpret_cast<int *>(dcnt + B);
+    if (MODE == 1) {
+        for (int i = lane; i < B; i += 32) dcnt[i] = 0u;
+        __syncwarp();
+    }
+    const Mover *mlist = a.movers + a.mbase[bin];
+    const int64_t count = *(volatile unsigned *)&a.mcount[bin];
     Counts c;
     const int64_t nbatch = (count + 31) >> 5;
     for (int64_t bt = (int64_t)blockIdx.x * nwarps + wid; bt < nbatch; bt += (int64_t)gridDim.x * nwarps) {
@@ -819,13 +836,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             if (lane >= o) incl += y;
         }
         const int first = incl - k;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        // sub-batches of whole rows with at most kBatchEdges edge ends
+        for (int sa = 0; sa < nv;) {
+        const int fs = __shfl_sync(0xffffffffu, first, sa);
+        const unsigned fit = __ballot_sync(0xffffffffu, lane >= sa && lane < nv && incl - fs <= kBatchEdges);
+        const int sb = 31 - __clz(fit);
+        const int total = __shfl_sync(0xffffffffu, incl, sb) - fs;
+        const bool act = lane >= sa && lane <= sb;
         // ---- P2
         for (int base = 0; base < total; base += 128) {
             int nb[4], vq[4], tag[4];
 #pragma unroll
             for (int c4 = 0; c4 < 4; ++c4) {
-                const int p = base + c4 * 32 + lane;
+                const int pp = base + c4 * 32 + lane;
+                const int p = fs + pp;
                 int q = 0;
 #pragma unroll
                 for (int st = 16; st >= 1; st >>= 1) {
@@ -839,28 +863,29 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                 vq[c4] = __shfl_sync(0xffffffffu, v, q);
                 const int e = p - fq;
                 tag[c4] = (q << 26) | (e < kq ? 0 : 1);
-                nb[c4] = p < total ? (e < kq ? g.oc[oq + e] : g.ic[iq + e - kq]) : -1;
+                nb[c4] = pp < total ? (e < kq ? g.oc[oq + e] : g.ic[iq + e - kq]) : -1;
             }
 #pragma unroll
             for (int c4 = 0; c4 < 4; ++c4) {
-                const int p = base + c4 * 32 + lane;
+                const int pp = base + c4 * 32 + lane;
                 if (nb[c4] >= 0) {
                     const int t = md.b[nb[c4]];
-                    W.key[p] = nb[c4] == vq[c4] ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
+                    W.key[pp] = nb[c4] == vq[c4] ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
                 }
             }
         }
         __syncwarp();
-        // ---- P3: windows of whole rows
         int nent = 0, my_self = 0, my_est = 0, my_ecnt = 0;
-        for (int qa = 0; qa < nv;) {
+        if (MODE == 0) {
+        // ---- P3: windows of whole rows
+        for (int qa = sa; qa <= sb;) {
             const int fa = __shfl_sync(0xffffffffu, first, qa);
-            const unsigned inw = __ballot_sync(0xffffffffu, lane >= qa && lane < nv && incl - fa <= 32);
+            const unsigned inw = __ballot_sync(0xffffffffu, lane >= qa && lane <= sb && incl - fa <= 32);
             const int qb = 31 - __clz(inw);
             const int wend = __shfl_sync(0xffffffffu, incl, qb);
             const int p = fa + lane;
             const bool valid = p < wend;
-            const int x = valid ? W.key[p] : 0;
+            const int x = valid ? W.key[p - fs] : 0;
             const bool selfl = valid && ((x >> 25) & 1);
             const bool in = (x & 1) != 0;
             const bool isent = valid && !selfl;
@@ -887,8 +912,52 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             nent += __popc(lm);
             qa = qb + 1;
         }
+        } else {
+        // ---- P3: per mover, direct-mapped counts; first touches kept in
+        // order of appearance (ballot compaction), so entries are deterministic
+        for (int q = sa; q <= sb; ++q) {
+            const int kq = __shfl_sync(0xffffffffu, k, q);
+            const int fq = __shfl_sync(0xffffffffu, first, q) - fs;
+            int nl = 0, selfq = 0;
+            for (int c0 = 0; c0 < kq; c0 += 32) {
+                const bool valid = c0 + lane < kq;
+                const int x = valid ? W.key[fq + c0 + lane] : 0;
+                const bool selfl = valid && ((x >> 25) & 1);
+                const bool in = (x & 1) != 0;
+                const bool isent = valid && !selfl;
+                const int t = isent ? ((x >> 1) & 0xffffff) : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, t);
+                const unsigned outm = __ballot_sync(0xffffffffu, isent && !in);
+                selfq += __popc(__ballot_sync(0xffffffffu, selfl && !in));
+                const bool leader = isent && lane == __ffs(peers) - 1;
+                bool fresh = false;
+                if (leader) {
+                    const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
+                    fresh = atomicAdd(&dcnt[t], ko | (ki << 16)) == 0u;
+                }
+                const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+                if (fresh) dlist[nl + __popc(fm & ((1u << lane) - 1u))] = t;
+                nl += __popc(fm);
+                __syncwarp();
+            }
+            for (int e = lane; e < nl; e += 32) {
+                const int t = dlist[e];
+                const unsigned cc = dcnt[t];
+                dcnt[t] = 0u;
+                W.key[nent + e] = (q << 26) | t;
+                W.ec[nent + e] = (unsigned short)((cc & 0xffu) | ((cc >> 16) << 8));
+            }
+            if (lane == q) {
+                my_self = selfq;
+                my_est = nent;
+                my_ecnt = nl;
+            }
+            nent += nl;
+            __syncwarp();
+        }
+        }
         W.r[lane] = r;
-        W.s[lane] = s;
+        W.s[lane] = act ? s : -1;
         W.rsr[lane] = 0;
         W.rss[lane] = 0;
         W.hasfb[lane] = 0;
@@ -959,7 +1028,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
         }
         __syncwarp();
         // ---- P6: lane per mover
-        if (lane < nv) {
+        if (act) {
             VertexCtx x;
             x.v = v; x.r = r; x.s = s;
             x.Kout = kout; x.Kin = kin; x.self = my_self; x.k = k;
@@ -987,7 +1056,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                                                          w2, k);
             if (dec >= 0) {
                 if (dec) md.bnew[v] = s;
-                count_result(c, dec != 0, false);
+                count_result(c, dec != 0, false, k);
             } else {
                 double pf64 = 0.0, pb64 = 0.0;
                 for (int e = my_est; e < my_est + my_ecnt; ++e) {
@@ -999,11 +1068,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                 corner_hastings_exact(x, cv, B, pf64, pb64);
                 const Exact ex = exact_decision_d(a.beta, fix48_to_double(dl48) + (has_fb ? fb : 0.0), pf64, pb64, w2);
                 if (ex.accept) md.bnew[v] = s;
-                count_result(c, ex.accept, ex.margin);
+                count_result(c, ex.accept, ex.margin, k);
                 write_trace(a, v, s, 1 | (ex.accept ? 2 : 0) | (ex.margin ? 4 : 0), ex.dH, ex.logA);
             }
         }
         __syncwarp();
+            sa = sb + 1;
+        }
     }
     flush_counts_warp(md, c, 0ull);
 }
@@ -1097,18 +1168,29 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     }
     // movers with k <= 32: batches of 32 per warp
     if (g->bin[2] > g->bin[1]) {
-        const size_t smem = sizeof(BatchWarp) * kWarpsPerCta;
-        SBP_CUDA(cudaFuncSetAttribute(k_eval_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_eval_batch<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a);
+        const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
+        const size_t smem = (size_t)wb * kWarpsPerCta;
+        SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_eval_batch<0><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 0, wb);
         SBP_CUDA(cudaGetLastError());
     }
     auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
-    // movers with 33 <= k <= 128: one warp each, 256-slot tables
+    // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
+    // small, otherwise one warp each with a 256-slot table
     if (g->bin[3] > g->bin[2]) {
-        const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
-        SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_eval_warp<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
-        SBP_CUDA(cudaGetLastError());
+        if (B <= kDirectMaxB) {
+            const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
+            const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
+            const size_t smem = (size_t)wb * nwarps;
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_batch<1><<<sms * 3, nwarps * 32, smem, m->stream>>>(a, 1, wb);
+            SBP_CUDA(cudaGetLastError());
+        } else {
+            const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_warp<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
+            SBP_CUDA(cudaGetLastError());
+        }
     }
     // movers with k > 128: per-warp tables sized for min(max degree, B)
     // distinct blocks while they fit, one CTA per mover beyond that

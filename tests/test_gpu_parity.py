@@ -339,3 +339,24 @@ def test_partition_sparse_start_dcsbm_5k_matches_oracle():
     assert dl == pytest.approx(odl, rel=1e-12)
     assert np.array_equal(b, ob)
     assert ns == ons
+
+
+def test_incremental_commit_equals_full_rebuild():
+    # the dense apply step updates M from the moved vertices' rows when few
+    # moved; recounting from all edges must give the same M and DL
+    g = make_config("dcsbm_1m", scale=0.05)
+    b = perturb(g.planted, 316, 0.3, seed=0)
+    pg = P.Graph(g.n, g.src, g.dst)
+    inc = P.Model(pg, 316, b, P.Params.default(seed=5))
+    full = P.Model(pg, 316, b, P.Params.default(seed=5, full_rebuild=1))
+    G = O.Graph(g.n, g.src, g.dst)
+    om = O.Model(G, 316, b)
+    for sw in range(4):
+        si = inc.sweep(sw)
+        sf = full.sweep(sw)
+        assert si.n_accepted == sf.n_accepted
+        assert np.array_equal(inc.assignment(), full.assignment())
+        assert np.array_equal(inc.dense(), full.dense())
+        assert inc.dl() == full.dl()
+    om.set_b(316, inc.assignment())
+    check_blockmodel(inc, om)
