@@ -51,12 +51,14 @@ def workload(name: str, scale: float):
     return g, B, b0
 
 
-def describe(name, g, B, scale):
+def describe(name, g, B, scale, m_form="dense"):
     c = CONFIGS[name]
+    form = "sparse hashed M rows (CSR+CSC, per-row hash tables)" if m_form == "sparse" else "dense M"
     return {
         "workload": f"{name}: directed DCSBM N={g.n:,} E={g.m:,}, {B} planted {c['sizes']} blocks, "
         f"degree exponent {c['gamma']} clipped [{c['kmin']},{c['kmax']}], intra:inter {c['ratio']:g}:1, "
-        f"nodal sweeps at B={B} from planted labels with 30% reassigned, FP64 Delta DL, beta=3",
+        f"nodal sweeps at B={B} from planted labels with 30% reassigned, {form}, beta=3",
+        "m_form": m_form,
         "n": g.n,
         "e": g.m,
         "B": B,
@@ -120,6 +122,12 @@ def algorithmic_bytes(n, m, B, move_edges):
     return decide, rebuild
 
 
+def dense_max_b(args) -> int:
+    """dense: M held dense while B <= 4096; sparse: per-row hashed sparse
+    rows at every B (dense_max_B = 1)."""
+    return 1 if args.m_form == "sparse" else 4096
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -131,7 +139,7 @@ def run_ours(args, rank, world, local_rank):
     g, B, b0 = workload(args.config, args.scale)
     stream = torch.cuda.current_stream(dev)
     graph = P.Graph(g.n, g.src, g.dst)
-    params = P.Params.default(seed=args.seed)
+    params = P.Params.default(seed=args.seed, dense_max_B=dense_max_b(args))
     model = P.Model(graph, B, b0, params, stream)
 
     def barrier():
@@ -155,6 +163,7 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    launches0 = P.sbp_kernel_launches()
     t_start.record(stream)
     for k in range(args.steps):
         ev[k][0].record(stream)
@@ -164,6 +173,7 @@ def run_ours(args, rank, world, local_rank):
         ev[k][2].record(stream)
         sweep_id += 1
     t_end.record(stream)
+    launches = P.sbp_kernel_launches() - launches0
     torch.cuda.synchronize(dev)
     ck = clocks.stop()
     P.sbp_sync(model.h)
@@ -220,11 +230,11 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic (seeded directed DCSBM generator; the paper's graphs are not available)",
-            "config": describe(args.config, g, B, args.scale),
+            "config": describe(args.config, g, B, args.scale, args.m_form),
             "impl": "ours",
             "e2e": {"value": g.n * e2e_steps * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * g.n, "d2h_bytes_per_step": 4 * g.n + 48},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": launches,
             "roofline": {"kernel": "nodal decide pass (k_propose, k_eval_batch, k_eval_warp, k_eval_cta)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_kind": hbm_kind, "algorithmic_bytes": dec_b, "traffic": None},
@@ -317,6 +327,7 @@ def main():
     ap.add_argument("--oracle-sample", type=int, default=50_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "partition"])
+    ap.add_argument("--m-form", default="dense", choices=["dense", "sparse"])
     args = ap.parse_args()
     if args.mode == "partition":
         run_partition(args)
@@ -333,7 +344,7 @@ def main():
         res = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * g.n / cb["value"], "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": describe(args.config, g, B, args.scale), "impl": "reference", "cpu_baseline": cb,
+               "config": describe(args.config, g, B, args.scale, args.m_form), "impl": "reference", "cpu_baseline": cb,
                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(res))
         return

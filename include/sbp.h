@@ -231,6 +231,12 @@ int sbp_dense_dl_noalloc(const int32_t *M, int32_t B, const int32_t *dout, const
 int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1, int32_t count,
                      uint64_t *out);
 
+/* Number of kernel launches the library has issued in this process, over
+ * all handles and devices (a host-side counter, incremented as each launch
+ * is enqueued, whether or not the kernel then finds work to do).  For
+ * accounting only: read it before and after a region of calls. */
+int sbp_kernel_launches(uint64_t *out);
+
 #ifdef __cplusplus
 }
 #endif

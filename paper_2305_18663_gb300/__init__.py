@@ -26,7 +26,7 @@ __all__ = [
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
-    "sbp_dense_dl_noalloc",
+    "sbp_dense_dl_noalloc", "sbp_kernel_launches",
     "Graph", "Model", "deal_vertices",
 ]
 
@@ -121,6 +121,7 @@ def load(path: str | None = None):
         "sbp_free_model": (None, [vp]),
         "sbp_philox_check": (C.c_int, [u64, u64, u64, u64, u64, u64, i32, vp]),
         "sbp_dense_dl_noalloc": (C.c_int, [vp, i32, vp, vp, i64, i64, vp, vp]),
+        "sbp_kernel_launches": (C.c_int, [P(u64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -296,6 +297,13 @@ def sbp_dense_dl_noalloc(M, B: int, dout, din, E: int, N: int, dl_out, stream=No
     allocating device memory (see include/sbp.h)."""
     _check(lib().sbp_dense_dl_noalloc(_ptr(M, np.int32), B, _ptr(dout, np.int32), _ptr(din, np.int32), E, N,
                                       _ptr(dl_out, np.float64), _stream_ptr(stream)))
+
+
+def sbp_kernel_launches() -> int:
+    """Kernel launches issued by the library so far in this process."""
+    n = C.c_uint64(0)
+    _check(lib().sbp_kernel_launches(C.byref(n)))
+    return int(n.value)
 
 
 def sbp_philox_check(ctr, key, count: int = 1) -> np.ndarray:

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libsbp: handles, passes, merge phase and driver.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -11,6 +12,9 @@
 namespace sbp {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -564,9 +568,16 @@ extern "C" int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t 
     uint64_t *d = nullptr;
     SBP_CUDA(cudaMalloc(&d, (size_t)count * 32));
     k_philox<<<(count + 255) / 256, 256>>>(c0, c1, c2, c3, k0, k1, count, d);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)count * 32, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "sbp_philox_check");
+    return SBP_OK;
+}
+
+extern "C" int sbp_kernel_launches(uint64_t *out) {
+    if (!out) return sbp::fail(SBP_EINVAL, "sbp_kernel_launches: NULL out");
+    *out = sbp::g_launches.load(std::memory_order_relaxed);
     return SBP_OK;
 }

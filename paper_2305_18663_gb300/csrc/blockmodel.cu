@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_dl_final(const DlPartial *__restri
 
 // commit plan: 1 = update M from the moved vertices' rows, 0 = recount
 __global__ void k_commit_plan(const DevCounters *__restrict__ c, int64_t E, int32_t *__restrict__ flag) {
-    flag[0] = (c->acc_edges * 8ull <= (unsigned long long)E) ? 1 : 0;
+    flag[0] = (c->acc_edges * 4ull <= (unsigned long long)E) ? 1 : 0;
 }
 
 __global__ void k_zero_if(int32_t *__restrict__ M, int64_t n, const int32_t *__restrict__ flag, int want) {
@@ -218,36 +218,102 @@ __global__ void k_zero_if(int32_t *__restrict__ M, int64_t n, const int32_t *__r
 // Apply step of Alg. 5 on a dense M: every edge with a moved end leaves its
 // old (block, block) cell and enters the new one.  An edge is visited once:
 // through the out-row of its moved source, or through the in-row of its
-// moved target when the source stayed.
-__global__ void __launch_bounds__(kThreads) k_delta_dense(GraphDev g, const int32_t *__restrict__ bnew,
+// moved target when the source stayed.  Lanes take the edges of one row,
+// four loads in flight per lane; lanes that hit the same cell add once.
+// (a dense M has B <= 16384, so a cell index fits 32 bits)
+__device__ __forceinline__ void delta_add(int32_t *__restrict__ M, bool valid, int key, int d) {
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!act) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? key : -1);
+    if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&M[key], d * __popc(peers));
+}
+
+// out-row [a, z) of a vertex moved r -> s
+__device__ __forceinline__ void delta_out_row(const int32_t *__restrict__ oc, int a, int z, int r, int s,
+                                              const int32_t *__restrict__ bnew, const int32_t *__restrict__ bold,
+                                              int32_t *__restrict__ M, int B) {
+    const int lane = threadIdx.x & 31;
+    for (int e0 = a; e0 < z; e0 += 128) {
+        int w[4], t[4], u[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = e0 + 32 * j + lane;
+            ok[j] = e < z;
+            w[j] = ok[j] ? oc[e] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            t[j] = ok[j] ? bold[w[j]] : 0;
+            u[j] = ok[j] ? bnew[w[j]] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            delta_add(M, ok[j], r * B + t[j], -1);
+            delta_add(M, ok[j], s * B + u[j], 1);
+        }
+    }
+}
+
+// in-row [a, z) of a vertex moved r -> s; only sources that stayed
+__device__ __forceinline__ void delta_in_row(const int32_t *__restrict__ ic, int a, int z, int r, int s,
+                                             const int32_t *__restrict__ bnew, const int32_t *__restrict__ bold,
+                                             int32_t *__restrict__ M, int B) {
+    const int lane = threadIdx.x & 31;
+    for (int e0 = a; e0 < z; e0 += 128) {
+        int w[4], t[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e = e0 + 32 * j + lane;
+            ok[j] = e < z;
+            w[j] = ok[j] ? ic[e] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            t[j] = ok[j] ? bold[w[j]] : 0;
+            ok[j] = ok[j] && bnew[w[j]] == t[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            delta_add(M, ok[j], t[j] * B + r, -1);
+            delta_add(M, ok[j], t[j] * B + s, 1);
+        }
+    }
+}
+
+// Warps [0, n_big) take one vertex each of the largest-degree group (in
+// descending degree, so the longest rows start first); the remaining warps
+// take 32 consecutive vertex ids each and skip the ones of that group.
+__global__ void __launch_bounds__(kThreads) k_delta_dense(GraphDev g, const int32_t *__restrict__ order, int big_begin,
+                                                          int n_big, const int32_t *__restrict__ bnew,
                                                           const int32_t *__restrict__ bold, int32_t *__restrict__ M,
                                                           int B, const int32_t *__restrict__ flag) {
     if (*flag != 1) return;
     const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; base < g.n; base += nw * 32) {
-        const int64_t vv = base + lane;
-        const bool moved = vv < g.n && bnew[vv] != bold[vv];
-        unsigned mm = __ballot_sync(0xffffffffu, moved);
-        while (mm) {
-            const int q = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const int v = (int)(base + q);
-            const int r = bold[v], s = bnew[v];
-            for (int e = g.op[v] + lane; e < g.op[v + 1]; e += 32) {
-                const int w = g.oc[e];
-                atomicAdd(&M[(size_t)r * B + bold[w]], -1);
-                atomicAdd(&M[(size_t)s * B + bnew[w]], 1);
-            }
-            for (int e = g.ip[v] + lane; e < g.ip[v + 1]; e += 32) {
-                const int w = g.ic[e];
-                const int t = bold[w];
-                if (bnew[w] == t) {
-                    atomicAdd(&M[(size_t)t * B + r], -1);
-                    atomicAdd(&M[(size_t)t * B + s], 1);
-                }
-            }
-        }
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w < n_big) {
+        const int v = order[big_begin + w];
+        const int r = bold[v], s = bnew[v];
+        if (r == s) return;
+        delta_out_row(g.oc, g.op[v], g.op[v + 1], r, s, bnew, bold, M, B);
+        delta_in_row(g.ic, g.ip[v], g.ip[v + 1], r, s, bnew, bold, M, B);
+        return;
+    }
+    const int64_t base = (w - n_big) * 32;
+    if (base >= g.n) return;
+    const int64_t vv = base + lane;
+    const bool moved = vv < g.n && bnew[vv] != bold[vv];
+    unsigned mm = __ballot_sync(0xffffffffu, moved);
+    while (mm) {
+        const int q = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int v = (int)(base + q);
+        const int o0 = g.op[v], o1 = g.op[v + 1], i0 = g.ip[v], i1 = g.ip[v + 1];
+        if ((o1 - o0) + (i1 - i0) > kWarpDeg) continue;  // a warp of its own took it
+        const int r = bold[v], s = bnew[v];
+        delta_out_row(g.oc, o0, o1, r, s, bnew, bold, M, B);
+        delta_in_row(g.ic, i0, i1, r, s, bnew, bold, M, B);
     }
 }
 
@@ -344,11 +410,11 @@ int rebuild_blockmodel(sbp_model *m) {
                 SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M,
                                                                                                       B, nullptr);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
         }
         k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
             m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
         vals = m->M;
         nvals = BB;
     } else {
@@ -359,9 +425,9 @@ int rebuild_blockmodel(sbp_model *m) {
     const int np = grid_for(nvals > B ? nvals : B, kThreads * 4, m->npartials);
     DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
     k_dl_partial<<<np, kThreads, 0, m->stream>>>(vals, nvals, m->dout, m->din, B, m->T, m->XT, parts);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     k_dl_final<<<1, kThreads, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
     return SBP_OK;
 }
@@ -379,28 +445,31 @@ int commit_blockmodel(sbp_model *m) {
     int32_t *flag = m->status + 1;
     SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
     k_commit_plan<<<1, 1, 0, m->stream>>>(m->counters, g->m, flag);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     k_zero_if<<<grid_for(BB, kThreads, sms * 8), kThreads, 0, m->stream>>>(m->M, BB, flag, 0);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     if (g->m > 0) {
         const size_t smem = (size_t)B * 4;
         if (smem > 48 * 1024)
             SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B,
                                                                                                   flag);
-        SBP_CUDA(cudaGetLastError());
-        k_delta_dense<<<sms * 4, kThreads, 0, m->stream>>>(g->dev(), m->b, m->bnew, m->M, B, flag);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
+        const int64_t n_big = g->n - g->bin[3];
+        const int64_t warps = n_big + (g->n + 31) / 32;
+        k_delta_dense<<<grid_for(warps * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
+            g->dev(), g->order, (int)g->bin[3], (int)n_big, m->b, m->bnew, m->M, B, flag);
+        SBP_LAUNCHED();
     }
     k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
         m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     const int np = grid_for(BB > B ? BB : B, kThreads * 4, m->npartials);
     DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
     k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->T, m->XT, parts);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     k_dl_final<<<1, kThreads, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
     return SBP_OK;
 }
@@ -408,7 +477,7 @@ int commit_blockmodel(sbp_model *m) {
 int launch_relabel(sbp_model *m, const int32_t *map_dev) {
     const int n = (int)m->g->n;
     k_relabel<<<grid_for(n, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(m->b, m->bnew, n, map_dev);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     return SBP_OK;
 }
 
@@ -416,7 +485,7 @@ int launch_vertex_count(sbp_model *m) {
     const int n = (int)m->g->n;
     SBP_CUDA(cudaMemsetAsync(m->vcount, 0, (size_t)m->B * 4, m->stream));
     k_vertex_count<<<grid_for(n, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(m->b, n, m->vcount);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     return SBP_OK;
 }
 

@@ -22,6 +22,15 @@ int cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return sbp::cuda_fail(_e, #call); \
     } while (0)
 
+// every kernel launch of the library goes through SBP_LAUNCHED(), which
+// counts it (sbp_kernel_launches) and checks the launch error
+void count_launch();
+#define SBP_LAUNCHED()                           \
+    do {                                         \
+        sbp::count_launch();                     \
+        SBP_CUDA(cudaGetLastError());            \
+    } while (0)
+
 #define SBP_TRY(call)                \
     do {                             \
         int _rc = (call);            \

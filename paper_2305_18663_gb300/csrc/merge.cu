@@ -142,7 +142,7 @@ int launch_merge_proposals(sbp_model *m, uint64_t round_id) {
     if (blocks < 1) blocks = 1;
     k_merge_proposals<<<(int)blocks, 256, 0, m->stream>>>(model_dev(m), m->p.seed, round_id, m->p.merge_proposals,
                                                           m->best_s, m->best_d);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     return SBP_OK;
 }
 

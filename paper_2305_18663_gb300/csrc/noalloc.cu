@@ -119,8 +119,8 @@ extern "C" int sbp_dense_dl_noalloc(const int32_t *M, int32_t B, const int32_t *
     const int64_t deg_blocks = ((int64_t)B + kNaThreads - 1) / kNaThreads;
     if (np < deg_blocks) np = deg_blocks;
     k_dl_partial_noalloc<<<(unsigned)np, kNaThreads, 0, st>>>(M, BB, dout, din, B, partials);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     k_dl_final_noalloc<<<1, kNaThreads, 0, st>>>(partials, (int)np, E, N, B, dl_out);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     return SBP_OK;
 }

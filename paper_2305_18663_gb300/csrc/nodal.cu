@@ -1164,7 +1164,7 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         if (blocks < 1) blocks = 1;
         k_propose<<<(int)blocks, 256, 0, m->stream>>>(a);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     // movers with k <= 32: batches of 32 per warp
     if (g->bin[2] > g->bin[1]) {
@@ -1172,7 +1172,7 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
         const size_t smem = (size_t)wb * kWarpsPerCta;
         SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_eval_batch<0><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 0, wb);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
     // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
@@ -1184,12 +1184,12 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
             const size_t smem = (size_t)wb * nwarps;
             SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_eval_batch<1><<<sms * 3, nwarps * 32, smem, m->stream>>>(a, 1, wb);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
         } else {
             const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
             SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_eval_warp<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
         }
     }
     // movers with k > 128: per-warp tables sized for min(max degree, B)
@@ -1205,13 +1205,13 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
             const size_t smem = warp_smem(cap, nwarps);
             SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_eval_warp<<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
         } else {
             const size_t smem = (size_t)cap * (8 + 4 + 4);
             if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
             SBP_CUDA(cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_eval_cta<<<sms * 4, kBigThreads, smem, m->stream>>>(a, 2, cap, cap_log2);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
         }
     }
     return SBP_OK;

@@ -200,11 +200,11 @@ int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *t
     }
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, scratch);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     k_scan_sums<<<1, kScanThreads, 0, st>>>(scratch, nb, total_dev);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, scratch, out);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     return SBP_OK;
 }
 
@@ -228,10 +228,10 @@ int radix_sort(K *k0, K *k1, V *v0, V *v1, int64_t n, int bits, uint32_t *scratc
         for (int p = 0; p < passes; ++p) {
             const int shift = 8 * p;
             k_digit_hist<K><<<(unsigned)ntiles, kSortThreads, 0, st>>>(ks, n, shift, ntiles, hist);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
             SBP_TRY(exclusive_scan_u32(hist, hist, 256 * ntiles, nullptr, sscr, st));
             k_digit_scatter<K, V><<<(unsigned)ntiles, kSortThreads, 0, st>>>(ks, vs, n, shift, ntiles, hist, kd, vd);
-            SBP_CUDA(cudaGetLastError());
+            SBP_LAUNCHED();
             std::swap(ks, kd);
             std::swap(vs, vd);
         }

@@ -223,7 +223,7 @@ int rebuild_sparse(sbp_model *m) {
     const int bits = bits_for((uint64_t)B * (uint64_t)B - 1);
     if (E > 0) {
         k_edge_keys<<<grid_of(E, cap), kT, 0, st>>>(g->dev(), m->b, B, S.key0);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     bool in_first = true;
     SBP_TRY((radix_sort<uint64_t, uint64_t>(S.key0, S.key1, nullptr, nullptr, E, bits, S.scratch, st, &in_first)));
@@ -235,50 +235,50 @@ int rebuild_sparse(sbp_model *m) {
     SBP_CUDA(cudaMemsetAsync(S.cnt, 0, ((size_t)B + 1) * 4, st));
     if (E > 0) {
         k_run_heads<<<grid_of(E, cap), kT, 0, st>>>(keys, E, S.flag);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
         SBP_TRY(exclusive_scan_u32(S.flag, S.pos, E, tot, sscr, st));
         uint32_t h = 0;
         SBP_CUDA(cudaMemcpyAsync(&h, tot, 4, cudaMemcpyDeviceToHost, st));
         SBP_CUDA(cudaStreamSynchronize(st));
         nnz = h;
         k_run_scatter<<<grid_of(E, cap), kT, 0, st>>>(keys, E, S.flag, S.pos, B, S.start, S.rc, S.cnt, S.rowof);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
         k_run_counts<<<grid_of(nnz, cap), kT, 0, st>>>(S.start, nnz, E, S.rv);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     S.nnz = nnz;
     // 3. CSR offsets and row prefixes, dout
     SBP_TRY(exclusive_scan_u32(S.cnt, S.rp, (int64_t)B + 1, nullptr, sscr, st));
     k_row_prefix<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.rp, S.rv, B, S.rpre, m->dout);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     // 4. CSC by a stable sort on the column
     SBP_CUDA(cudaMemsetAsync(S.cnt, 0, ((size_t)B + 1) * 4, st));
     if (nnz > 0) {
         k_csc_src<<<grid_of(nnz, cap), kT, 0, st>>>(S.rc, S.rowof, S.rv, nnz, S.ckey0, S.cval0, S.cnt);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     bool cfirst = true;
     SBP_TRY((radix_sort<uint32_t, uint64_t>(S.ckey0, S.ckey1, S.cval0, S.cval1, nnz, bits_for((uint64_t)B - 1), S.scratch,
                                             st, &cfirst)));
     if (nnz > 0) {
         k_csc_unpack<<<grid_of(nnz, cap), kT, 0, st>>>(cfirst ? S.cval0 : S.cval1, nnz, S.cr, S.cv);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     SBP_TRY(exclusive_scan_u32(S.cnt, S.cp, (int64_t)B + 1, nullptr, sscr, st));
     k_row_prefix<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.cp, S.cv, B, S.cpre, m->din);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     // 5. per-row hash tables
     k_hash_caps<<<grid_of(B, cap), kT, 0, st>>>(S.rp, B, S.cnt);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     SBP_TRY(exclusive_scan_u32(S.cnt, S.hoff, (int64_t)B + 1, nullptr, sscr, st));
     SBP_CUDA(cudaMemsetAsync(S.hk, 0xff, (size_t)(4 * S.cap_e + 2 * g->n) * 4, st));
     if (nnz > 0) {
         k_hash_fill<<<grid_of(nnz, cap), kT, 0, st>>>(S.rp, S.rc, S.rv, S.rowof, nnz, S.hoff, S.hk, S.hv, m->status);
-        SBP_CUDA(cudaGetLastError());
+        SBP_LAUNCHED();
     }
     // 6. per-block scalars
     k_block_scalars<<<grid_of(B, cap), kT, 0, st>>>(m->dout, m->din, B, m->dsum, m->rcp, m->rcp32);
-    SBP_CUDA(cudaGetLastError());
+    SBP_LAUNCHED();
     return SBP_OK;
 }
 
