@@ -19,17 +19,14 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Warp-aggregated atomic histogram of (b[src], b[dst]) over the out-edges,
-// four consecutive edges per thread (16-byte loads, eight independent
-// gathers in flight).  Diagonal counts (intra-block edges, the large
-// majority) go to a per-CTA shared-memory copy of the diagonal first.
+// Atomic histogram of (b[src], b[dst]) over the out-edges, four
+// consecutive edges per thread (16-byte loads, eight independent gathers in
+// flight).  Diagonal counts (intra-block edges, the large majority) go to a
+// per-CTA shared-memory copy of the diagonal first.
 __device__ __forceinline__ void hist_add(int32_t *__restrict__ M, int *diag, int B, bool valid, int r, int t) {
-    const int key = valid ? r * B + t : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-        if (r == t) atomicAdd(&diag[r], __popc(peers));
-        else atomicAdd(&M[key], __popc(peers));
-    }
+    if (!valid) return;
+    if (r == t) atomicAdd(&diag[r], 1);
+    else atomicAdd(&M[(size_t)r * B + t], 1);
 }
 
 __global__ void __launch_bounds__(kThreads) k_hist_dense(GraphDev g, const int32_t *__restrict__ b,
@@ -394,31 +391,77 @@ int ensure_capacity(sbp_model *m, int32_t B) {
     return SBP_OK;
 }
 
-int rebuild_blockmodel(sbp_model *m) {
+// cells[r * B + t] = number of edges from block r to block t (all B * B
+// cells are written); B <= 16384
+int count_cells(sbp_model *m, int32_t *cells) {
+    const sbp_graph *g = m->g;
+    const int B = m->B;
+    SBP_CUDA(cudaMemsetAsync(cells, 0, (size_t)B * B * 4, m->stream));
+    if (g->m > 0) {
+        const size_t smem = (size_t)B * 4;
+        if (smem > 48 * 1024)
+            SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, num_sms() * 8), kThreads, smem, m->stream>>>(g->dev(), m->b,
+                                                                                                        cells, B, nullptr);
+        SBP_LAUNCHED();
+    }
+    return SBP_OK;
+}
+
+// cells (the counts of the previous assignment m->bnew) brought to the
+// counts of m->b: the plan kernel picks, on the device, either the update
+// from the moved vertices' rows (few moved edges) or a recount; both give
+// the same counts
+int update_cells(sbp_model *m, int32_t *cells) {
     const sbp_graph *g = m->g;
     const int B = m->B;
     const int sms = num_sms();
+    const int64_t BB = (int64_t)B * B;
+    int32_t *flag = m->status + 1;
+    k_commit_plan<<<1, 1, 0, m->stream>>>(m->counters, g->m, flag);
+    SBP_LAUNCHED();
+    k_zero_if<<<grid_for(BB, kThreads, sms * 8), kThreads, 0, m->stream>>>(cells, BB, flag, 0);
+    SBP_LAUNCHED();
+    if (g->m > 0) {
+        const size_t smem = (size_t)B * 4;
+        if (smem > 48 * 1024)
+            SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, cells, B,
+                                                                                                  flag);
+        SBP_LAUNCHED();
+        const int64_t n_big = g->n - g->bin[3];
+        const int64_t warps = n_big + (g->n + 31) / 32;
+        k_delta_dense<<<grid_for(warps * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
+            g->dev(), g->order, (int)g->bin[3], (int)n_big, m->b, m->bnew, cells, B, flag);
+        SBP_LAUNCHED();
+    }
+    return SBP_OK;
+}
+
+namespace {
+
+// M (dense, or sparse rows), P, degrees, rcp and DL from m->b.  after_pass:
+// m->bnew holds the assignment the current M was built from, and the counts
+// may be updated from the moves instead of recounted.
+int build_blockmodel(sbp_model *m, bool after_pass) {
+    const sbp_graph *g = m->g;
+    const int B = m->B;
     SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
     const int32_t *vals;
     int64_t nvals;
     if (m->dense) {
         const int64_t BB = (int64_t)B * B;
-        SBP_CUDA(cudaMemsetAsync(m->M, 0, (size_t)BB * 4, m->stream));
-        if (g->m > 0) {
-            const size_t smem = (size_t)B * 4;
-            if (smem > 48 * 1024)
-                SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M,
-                                                                                                      B, nullptr);
-            SBP_LAUNCHED();
-        }
+        if (after_pass)
+            SBP_TRY(update_cells(m, m->M));
+        else
+            SBP_TRY(count_cells(m, m->M));
         k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
             m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
         SBP_LAUNCHED();
         vals = m->M;
         nvals = BB;
     } else {
-        SBP_TRY(rebuild_sparse(m));
+        SBP_TRY(rebuild_sparse(m, after_pass));
         vals = m->sp.rv;
         nvals = m->sp.nnz;
     }
@@ -432,47 +475,16 @@ int rebuild_blockmodel(sbp_model *m) {
     return SBP_OK;
 }
 
-// After a nodal pass (m->b: new labels, m->bnew: the previous ones).  A
-// dense model takes the incremental update when the plan kernel finds few
+}  // namespace
+
+int rebuild_blockmodel(sbp_model *m) { return build_blockmodel(m, false); }
+
+// After a nodal pass (m->b: new labels, m->bnew: the previous ones).  The
+// counts (dense M, or the cell counts of a sparse model rebuilt by
+// counting) take the incremental update when the plan kernel finds few
 // moved edges (decided on the device, no host round trip); the result is
 // the same M as a recount.
-int commit_blockmodel(sbp_model *m) {
-    if (!m->dense || m->p.full_rebuild) return rebuild_blockmodel(m);
-    const sbp_graph *g = m->g;
-    const int B = m->B;
-    const int sms = num_sms();
-    const int64_t BB = (int64_t)B * B;
-    int32_t *flag = m->status + 1;
-    SBP_TRY(xlogx_table(g->m + 1, &m->T, &m->XT));
-    k_commit_plan<<<1, 1, 0, m->stream>>>(m->counters, g->m, flag);
-    SBP_LAUNCHED();
-    k_zero_if<<<grid_for(BB, kThreads, sms * 8), kThreads, 0, m->stream>>>(m->M, BB, flag, 0);
-    SBP_LAUNCHED();
-    if (g->m > 0) {
-        const size_t smem = (size_t)B * 4;
-        if (smem > 48 * 1024)
-            SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, m->M, B,
-                                                                                                  flag);
-        SBP_LAUNCHED();
-        const int64_t n_big = g->n - g->bin[3];
-        const int64_t warps = n_big + (g->n + 31) / 32;
-        k_delta_dense<<<grid_for(warps * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
-            g->dev(), g->order, (int)g->bin[3], (int)n_big, m->b, m->bnew, m->M, B, flag);
-        SBP_LAUNCHED();
-    }
-    k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
-        m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
-    SBP_LAUNCHED();
-    const int np = grid_for(BB > B ? BB : B, kThreads * 4, m->npartials);
-    DlPartial *parts = reinterpret_cast<DlPartial *>(m->partials);
-    k_dl_partial<<<np, kThreads, 0, m->stream>>>(m->M, BB, m->dout, m->din, B, m->T, m->XT, parts);
-    SBP_LAUNCHED();
-    k_dl_final<<<1, kThreads, 0, m->stream>>>(parts, np, g->m, g->n, B, m->dl);
-    SBP_LAUNCHED();
-    SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
-    return SBP_OK;
-}
+int commit_blockmodel(sbp_model *m) { return build_blockmodel(m, !m->p.full_rebuild); }
 
 int launch_relabel(sbp_model *m, const int32_t *map_dev) {
     const int n = (int)m->g->n;

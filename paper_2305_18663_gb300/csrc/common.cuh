@@ -54,6 +54,13 @@ constexpr int64_t kMaxTable = int64_t(1) << 22;  // largest x ln x table (entrie
 
 // ---------------------------------------------------------------------------
 // graph and model state
+// keys computed on the fly from the out-edge list: key of out-edge e is
+// b[esrc[e]] * B + b[oc[e]] (row block, column block)
+struct EdgeKeys {
+    const int32_t *esrc = nullptr, *oc = nullptr, *b = nullptr;
+    uint64_t B = 0;
+};
+
 struct GraphDev {
     int32_t n;
     int64_t m;
@@ -120,13 +127,16 @@ struct sbp_model {
         int64_t cap_e = 0, nnz = 0;
         int32_t cap_b = 0;
         uint64_t *key0 = nullptr, *key1 = nullptr;
-        uint32_t *flag = nullptr, *pos = nullptr, *start = nullptr, *scratch = nullptr;
+        uint32_t *start = nullptr, *scratch = nullptr;
         int32_t *rc = nullptr, *rv = nullptr, *rowof = nullptr, *cr = nullptr, *cv = nullptr;
         uint32_t *rpre = nullptr, *cpre = nullptr;
         uint32_t *ckey0 = nullptr, *ckey1 = nullptr;
         uint64_t *cval0 = nullptr, *cval1 = nullptr;
         int32_t *hk = nullptr, *hv = nullptr;
         uint32_t *rp = nullptr, *cp = nullptr, *hoff = nullptr, *cnt = nullptr;
+        int32_t *cells = nullptr;  // B x B counts of the counting-sort rebuild
+        int64_t cap_cells = 0;
+        int32_t cells_B = 0;       // B the cells hold the counts of m->bnew for, else 0
     };
     Sparse sp;
     const sbp_graph *g = nullptr;
@@ -371,6 +381,8 @@ __device__ __forceinline__ int sparse_cdf_block(const ModelDev &md, int u, uint3
 // ---------------------------------------------------------------------------
 // host-side launch helpers implemented in the .cu files
 int rebuild_blockmodel(sbp_model *m);  // M, P, degrees, rcp, DL from m->b
+int count_cells(sbp_model *m, int32_t *cells);  // cells[r * B + t] = edges r -> t
+int update_cells(sbp_model *m, int32_t *cells);  // counts of m->bnew -> counts of m->b
 int commit_blockmodel(sbp_model *m);   // the same after a pass: m->b new labels, m->bnew the previous ones
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
 int launch_merge_proposals(sbp_model *m, uint64_t round_id);
@@ -380,8 +392,20 @@ int ensure_capacity(sbp_model *m, int32_t B);
 int check_status(const sbp_model *m);
 int xlogx_table(int64_t need, const __int128 **table, int64_t *size);
 int ensure_sparse_capacity(sbp_model *m, int32_t B);
-int rebuild_sparse(sbp_model *m);
+int rebuild_sparse(sbp_model *m, bool after_pass);
 void free_sparse(sbp_model *m);
+
+// sort.cu: exclusive scan of n uint32 (in may equal out; *total_dev, device,
+// may be NULL) and the stable LSD radix sort with its scratch sizes
+int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *scratch,
+                       cudaStream_t st);
+int64_t scan_scratch_words(int64_t n);
+int64_t sort_scratch_words(int64_t n);
+int sort_chunk_count(int64_t n);
+int64_t sort_chunk_length(int64_t n);
+template <class K, class V>
+int radix_sort(K *k0, K *k1, V *v0, V *v1, int64_t n, int bits, uint32_t *scratch, cudaStream_t st, bool *in_first,
+               const EdgeKeys *edges = nullptr);
 ModelDev model_dev(sbp_model *m);
 
 }  // namespace sbp

@@ -2,7 +2,10 @@
 //
 // Section III-A (a)-(b): M held as per-row hashed sparse rows plus a stored
 // transpose.  Rebuilt from the assignment by sort plus segmented count:
-//   1. key of every edge = b[src] * B + b[dst]; radix sort;
+//   1. key of every edge = b[src] * B + b[dst], sorted.  The sort is a
+//      counting sort over the B x B key space when that space is small
+//      (the edge keys need no values, so its histogram already holds the
+//      run lengths); otherwise an LSD radix sort of the keys;
 //   2. run-length encoding gives the nonzeros (r, c, M[r][c]) in row order;
 //   3. CSR: row offsets by a row histogram and scan, the inclusive prefix of
 //      the counts inside each row (the proposal CDF over row u);
@@ -18,13 +21,6 @@
 
 namespace sbp {
 
-int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *scratch,
-                       cudaStream_t st);
-int64_t scan_scratch_words(int64_t n);
-int64_t sort_scratch_words(int64_t n);
-template <class K, class V>
-int radix_sort(K *k0, K *k1, V *v0, V *v1, int64_t n, int bits, uint32_t *scratch, cudaStream_t st, bool *in_first);
-
 namespace {
 
 constexpr int kT = 256;
@@ -36,30 +32,162 @@ int grid_of(int64_t work, int cap) {
     return (int)g;
 }
 
-__global__ void k_edge_keys(GraphDev g, const int32_t *__restrict__ b, int64_t B, uint64_t *__restrict__ keys) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x)
-        keys[e] = (uint64_t)b[g.esrc[e]] * (uint64_t)B + (uint64_t)b[g.oc[e]];
+// Run-length encoding of the sorted keys, chunk by chunk: count the run
+// heads per chunk, scan, then write each run's start, column and row.  A
+// thread takes 16 consecutive keys per round (a round is 4096 keys; chunks
+// are whole rounds).
+constexpr int kRleItems = 16;
+constexpr int kRleRound = kT * kRleItems;
+
+// keys [i0, i0 + 16) with i0 a multiple of 16, as 16-byte loads
+template <class K>
+__device__ __forceinline__ void load16(const K *__restrict__ keys, int64_t i0, K (&k)[kRleItems]) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(keys + i0);
+    constexpr int nv = kRleItems * (int)sizeof(K) / 16;
+    uint4 tmp[nv];
+#pragma unroll
+    for (int x = 0; x < nv; ++x) tmp[x] = p[x];
+    const K *t = reinterpret_cast<const K *>(tmp);
+#pragma unroll
+    for (int j = 0; j < kRleItems; ++j) k[j] = t[j];
 }
 
-__global__ void k_run_heads(const uint64_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ flag) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+// head flags of the thread's keys in the round starting at base: bit j set
+// when key i0 + j starts a run
+template <class K>
+__device__ __forceinline__ uint32_t rle_heads(const K *__restrict__ keys, int64_t i0, int64_t end, K (&k)[kRleItems]) {
+    uint32_t hm = 0;
+    if (i0 >= end) return 0;
+    if (i0 + kRleItems <= end) {
+        load16<K>(keys, i0, k);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kRleItems; ++j) k[j] = i0 + j < end ? keys[i0 + j] : (K)0;
+    }
+    K prev = i0 > 0 ? keys[i0 - 1] : (K)0;
+#pragma unroll
+    for (int j = 0; j < kRleItems; ++j) {
+        if (i0 + j < end && (i0 + j == 0 || k[j] != prev)) hm |= 1u << j;
+        prev = k[j];
+    }
+    return hm;
 }
 
-// heads: unique key, start position; row counts
-__global__ void k_run_scatter(const uint64_t *__restrict__ keys, int64_t n, const uint32_t *__restrict__ flag,
-                              const uint32_t *__restrict__ pos, int64_t B, uint32_t *__restrict__ start,
-                              int32_t *__restrict__ col, uint32_t *__restrict__ rowcnt, int32_t *__restrict__ rowof) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (flag[i]) {
-            const uint32_t p = pos[i];
-            const uint64_t k = keys[i];
-            const int r = (int)(k / (uint64_t)B), c = (int)(k % (uint64_t)B);
-            start[p] = (uint32_t)i;
-            col[p] = c;
-            rowof[p] = r;
-            atomicAdd(&rowcnt[r], 1u);
+template <class K>
+__global__ void __launch_bounds__(kT) k_rle_count(const K *__restrict__ keys, int64_t n, int64_t chunk,
+                                                  uint32_t *__restrict__ cnt) {
+    __shared__ uint32_t sh[kT / 32];
+    const int64_t begin = (int64_t)blockIdx.x * chunk;
+    const int64_t end = begin + chunk < n ? begin + chunk : n;
+    uint32_t c = 0;
+    for (int64_t base = begin; base < end; base += kRleRound) {
+        K k[kRleItems];
+        c += (uint32_t)__popc(rle_heads<K>(keys, base + (int64_t)threadIdx.x * kRleItems, end, k));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(kT) k_rle_emit(const K *__restrict__ keys, int64_t n, int64_t chunk,
+                                                 const uint32_t *__restrict__ cstart, uint64_t B,
+                                                 uint32_t *__restrict__ start, int32_t *__restrict__ col,
+                                                 int32_t *__restrict__ rowof, uint32_t *__restrict__ rowcnt) {
+    __shared__ uint32_t wsum[kT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t begin = (int64_t)blockIdx.x * chunk;
+    const int64_t end = begin + chunk < n ? begin + chunk : n;
+    uint32_t running = cstart[blockIdx.x];
+    for (int64_t base = begin; base < end; base += kRleRound) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kRleItems;
+        K k[kRleItems];
+        uint32_t hm = rle_heads<K>(keys, i0, end, k);
+        const uint32_t c = (uint32_t)__popc(hm);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        uint32_t before = incl - c, total = 0;
+#pragma unroll
+        for (int x = 0; x < kT / 32; ++x) {
+            const uint32_t t = wsum[x];
+            before += x < w ? t : 0u;
+            total += t;
+        }
+        uint32_t p = running + before;
+#pragma unroll
+        for (int j = 0; j < kRleItems; ++j) {
+            if ((hm >> j) & 1u) {
+                const uint64_t key = (uint64_t)k[j];
+                const uint64_t r = key / B;
+                start[p] = (uint32_t)(i0 + j);
+                col[p] = (int32_t)(key - r * B);
+                rowof[p] = (int32_t)r;
+                atomicAdd(&rowcnt[r], 1u);
+                ++p;
+            }
+        }
+        running += total;
+        __syncthreads();
+    }
+}
+
+// Counting-sort form (small B x B key space): the cell counts are the run
+// lengths.  One warp per row: number of nonzero cells, then (after the scan
+// of those numbers) the row's nonzeros in ascending column with their
+// in-row inclusive prefix; the row total is dout.
+__global__ void k_cell_rowcount(const int32_t *__restrict__ cells, int B, uint32_t *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < B; r += nw) {
+        uint32_t c = 0;
+        for (int c0 = 0; c0 < B; c0 += 32) {
+            const int col = c0 + lane;
+            c += (uint32_t)__popc(__ballot_sync(0xffffffffu, col < B && cells[r * B + col] != 0));
+        }
+        if (lane == 0) cnt[r] = c;
+    }
+}
+
+__global__ void k_cell_compact(const int32_t *__restrict__ cells, int B, const uint32_t *__restrict__ rp,
+                               int32_t *__restrict__ rc, int32_t *__restrict__ rv, int32_t *__restrict__ rowof,
+                               uint32_t *__restrict__ rpre, int32_t *__restrict__ dout) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < B; r += nw) {
+        uint32_t p = rp[r], carry = 0;
+        for (int c0 = 0; c0 < B; c0 += 32) {
+            const int col = c0 + lane;
+            const uint32_t v = col < B ? (uint32_t)cells[r * B + col] : 0u;
+            const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (v != 0) {
+                const uint32_t q = p + (uint32_t)__popc(nz & ((1u << lane) - 1u));
+                rc[q] = col;
+                rv[q] = (int32_t)v;
+                rowof[q] = (int32_t)r;
+                rpre[q] = carry + incl;
+            }
+            p += (uint32_t)__popc(nz);
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) dout[r] = (int32_t)carry;
     }
 }
 
@@ -173,14 +301,20 @@ int alloc(T **p, int64_t count) {
 
 }  // namespace
 
+// The rebuild counts cells instead of sorting keys when the B x B key space
+// is small: at most 2^26 cells (B <= 8192) and at most 8 E + 2^20, so that
+// zeroing and scanning the cells stays cheaper than sorting E keys.
+bool sparse_by_count(int64_t B, int64_t E) {
+    const int64_t cells = B * B;
+    return cells <= (int64_t(1) << 26) && cells <= 8 * E + (int64_t(1) << 20);
+}
+
 int ensure_sparse_capacity(sbp_model *m, int32_t B) {
     sbp_model::Sparse &S = m->sp;
     const int64_t E = m->g->m > 0 ? m->g->m : 1;
     if (S.cap_e < E) {
         SBP_TRY(alloc(&S.key0, E));
         SBP_TRY(alloc(&S.key1, E));
-        SBP_TRY(alloc(&S.flag, E));
-        SBP_TRY(alloc(&S.pos, E));
         SBP_TRY(alloc(&S.start, E));
         SBP_TRY(alloc(&S.rc, E));
         SBP_TRY(alloc(&S.rv, E));
@@ -200,6 +334,10 @@ int ensure_sparse_capacity(sbp_model *m, int32_t B) {
         SBP_TRY(alloc(&S.scratch, w + 1024));
         S.cap_e = E;
     }
+    if (sparse_by_count(B, m->g->m) && S.cap_cells < (int64_t)B * B) {
+        SBP_TRY(alloc(&S.cells, (int64_t)B * B));
+        S.cap_cells = (int64_t)B * B;
+    }
     if (S.cap_b < B) {
         SBP_TRY(alloc(&S.rp, (int64_t)B + 1));
         SBP_TRY(alloc(&S.cp, (int64_t)B + 1));
@@ -210,47 +348,93 @@ int ensure_sparse_capacity(sbp_model *m, int32_t B) {
     return SBP_OK;
 }
 
+namespace {
+
+// steps 1-2 for keys of type K: sort the edge keys (the first pass makes
+// them from the edge list), run-length encode; returns the nonzero count
+template <class K>
+int sort_and_encode(sbp_model *m, int bits, int64_t *nnz_out) {
+    const sbp_graph *g = m->g;
+    sbp_model::Sparse &S = m->sp;
+    const int64_t E = g->m;
+    cudaStream_t st = m->stream;
+    K *k0 = reinterpret_cast<K *>(S.key0), *k1 = reinterpret_cast<K *>(S.key1);
+    EdgeKeys ek;
+    ek.esrc = g->esrc;
+    ek.oc = g->oc;
+    ek.b = m->b;
+    ek.B = (uint64_t)m->B;
+    bool in_first = true;
+    SBP_TRY((radix_sort<K, uint32_t>(k0, k1, nullptr, nullptr, E, bits, S.scratch, st, &in_first, &ek)));
+    const K *keys = in_first ? k0 : k1;
+    const int G = sort_chunk_count(E);
+    const int64_t chunk = sort_chunk_length(E);
+    uint32_t *tot = S.scratch, *cnt = S.scratch + 4, *cstart = S.scratch + 4 + 2 * (int64_t)G + 4;
+    uint32_t *sscr = cstart + 2 * (int64_t)G + 4;
+    k_rle_count<K><<<G, kT, 0, st>>>(keys, E, chunk, cnt);
+    SBP_LAUNCHED();
+    SBP_TRY(exclusive_scan_u32(cnt, cstart, G, tot, sscr, st));
+    uint32_t h = 0;
+    SBP_CUDA(cudaMemcpyAsync(&h, tot, 4, cudaMemcpyDeviceToHost, st));
+    k_rle_emit<K><<<G, kT, 0, st>>>(keys, E, chunk, cstart, (uint64_t)m->B, S.start, S.rc, S.rowof, S.cnt);
+    SBP_LAUNCHED();
+    SBP_CUDA(cudaStreamSynchronize(st));
+    *nnz_out = h;
+    return SBP_OK;
+}
+
+}  // namespace
+
 // Rebuild of the sparse blockmodel from m->b; fills the model's degree and
 // per-block arrays.  One host read-back (the nonzero count) per rebuild.
-int rebuild_sparse(sbp_model *m) {
+// after_pass: m->bnew holds the previous assignment, and cell counts kept
+// from the previous rebuild may be updated from the moves.
+int rebuild_sparse(sbp_model *m, bool after_pass) {
     const sbp_graph *g = m->g;
     sbp_model::Sparse &S = m->sp;
     const int B = m->B;
     const int64_t E = g->m;
     cudaStream_t st = m->stream;
     const int cap = 152 * 8;
-    // 1. keys, sort
-    const int bits = bits_for((uint64_t)B * (uint64_t)B - 1);
-    if (E > 0) {
-        k_edge_keys<<<grid_of(E, cap), kT, 0, st>>>(g->dev(), m->b, B, S.key0);
-        SBP_LAUNCHED();
-    }
-    bool in_first = true;
-    SBP_TRY((radix_sort<uint64_t, uint64_t>(S.key0, S.key1, nullptr, nullptr, E, bits, S.scratch, st, &in_first)));
-    const uint64_t *keys = in_first ? S.key0 : S.key1;
-    // 2. run-length
-    uint32_t *tot = S.scratch;  // word 0: nonzero count (scratch tail used by the scans below)
     uint32_t *sscr = S.scratch + 4;
+    // 1-3. the nonzeros of M in row order: CSR offsets, columns, counts,
+    // in-row prefixes, dout
     int64_t nnz = 0;
     SBP_CUDA(cudaMemsetAsync(S.cnt, 0, ((size_t)B + 1) * 4, st));
-    if (E > 0) {
-        k_run_heads<<<grid_of(E, cap), kT, 0, st>>>(keys, E, S.flag);
+    if (sparse_by_count(B, E)) {
+        // counting sort over the B x B keys: the counts are the run lengths
+        if (after_pass && S.cells_B == B)
+            SBP_TRY(update_cells(m, S.cells));
+        else
+            SBP_TRY(count_cells(m, S.cells));
+        S.cells_B = B;
+        k_cell_rowcount<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.cells, B, S.cnt);
         SBP_LAUNCHED();
-        SBP_TRY(exclusive_scan_u32(S.flag, S.pos, E, tot, sscr, st));
+        SBP_TRY(exclusive_scan_u32(S.cnt, S.rp, (int64_t)B + 1, S.scratch, sscr, st));
         uint32_t h = 0;
-        SBP_CUDA(cudaMemcpyAsync(&h, tot, 4, cudaMemcpyDeviceToHost, st));
+        SBP_CUDA(cudaMemcpyAsync(&h, S.scratch, 4, cudaMemcpyDeviceToHost, st));
+        k_cell_compact<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.cells, B, S.rp, S.rc, S.rv, S.rowof, S.rpre,
+                                                                        m->dout);
+        SBP_LAUNCHED();
         SBP_CUDA(cudaStreamSynchronize(st));
         nnz = h;
-        k_run_scatter<<<grid_of(E, cap), kT, 0, st>>>(keys, E, S.flag, S.pos, B, S.start, S.rc, S.cnt, S.rowof);
-        SBP_LAUNCHED();
-        k_run_counts<<<grid_of(nnz, cap), kT, 0, st>>>(S.start, nnz, E, S.rv);
+    } else {
+        S.cells_B = 0;
+        // radix sort of the (row, column) keys of the edges, run-length encoding
+        const int bits = bits_for((uint64_t)B * (uint64_t)B - 1);
+        if (E > 0) {
+            if (bits <= 32)
+                SBP_TRY(sort_and_encode<uint32_t>(m, bits, &nnz));
+            else
+                SBP_TRY(sort_and_encode<uint64_t>(m, bits, &nnz));
+            k_run_counts<<<grid_of(nnz, cap), kT, 0, st>>>(S.start, nnz, E, S.rv);
+            SBP_LAUNCHED();
+        }
+        SBP_TRY(exclusive_scan_u32(S.cnt, S.rp, (int64_t)B + 1, nullptr, sscr, st));
+        k_row_prefix<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.rp, S.rv, B, S.rpre, m->dout);
         SBP_LAUNCHED();
     }
     S.nnz = nnz;
-    // 3. CSR offsets and row prefixes, dout
-    SBP_TRY(exclusive_scan_u32(S.cnt, S.rp, (int64_t)B + 1, nullptr, sscr, st));
-    k_row_prefix<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.rp, S.rv, B, S.rpre, m->dout);
-    SBP_LAUNCHED();
     // 4. CSC by a stable sort on the column
     SBP_CUDA(cudaMemsetAsync(S.cnt, 0, ((size_t)B + 1) * 4, st));
     if (nnz > 0) {
@@ -271,7 +455,8 @@ int rebuild_sparse(sbp_model *m) {
     k_hash_caps<<<grid_of(B, cap), kT, 0, st>>>(S.rp, B, S.cnt);
     SBP_LAUNCHED();
     SBP_TRY(exclusive_scan_u32(S.cnt, S.hoff, (int64_t)B + 1, nullptr, sscr, st));
-    SBP_CUDA(cudaMemsetAsync(S.hk, 0xff, (size_t)(4 * S.cap_e + 2 * g->n) * 4, st));
+    // capacities are powers of two below 4 len + 2 per row
+    SBP_CUDA(cudaMemsetAsync(S.hk, 0xff, (size_t)(4 * nnz + 2 * (int64_t)B) * 4, st));
     if (nnz > 0) {
         k_hash_fill<<<grid_of(nnz, cap), kT, 0, st>>>(S.rp, S.rc, S.rv, S.rowof, nnz, S.hoff, S.hk, S.hv, m->status);
         SBP_LAUNCHED();
@@ -284,8 +469,8 @@ int rebuild_sparse(sbp_model *m) {
 
 void free_sparse(sbp_model *m) {
     sbp_model::Sparse &S = m->sp;
-    void *ps[] = {S.key0, S.key1, S.flag, S.pos, S.start, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv, S.cpre, S.ckey0,
-                  S.ckey1, S.cval0, S.cval1, S.hk, S.hv, S.scratch, S.rp, S.cp, S.hoff, S.cnt};
+    void *ps[] = {S.key0, S.key1, S.start, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv, S.cpre, S.ckey0,
+                  S.ckey1, S.cval0, S.cval1, S.hk, S.hv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells};
     for (void *p : ps) cudaFree(p);
     S = sbp_model::Sparse();
 }

@@ -122,6 +122,20 @@ def test_blockmodel_rebuild_matches_oracle(B, dmax):
     assert pm.coo()[1].sum() == g.m
 
 
+@pytest.mark.parametrize("B", [2, 300, 20000, 70000])
+def test_sparse_rebuild_many_chunks_matches_oracle(B):
+    # 150k vertices, 3M edges.  B = 2 and 300: counting sort over the B^2
+    # cells; B = 20000: radix sort of 32-bit keys (4 passes, every chunk
+    # spans several rounds); B = 70000: 64-bit keys (B^2 > 2^32)
+    g = make_config("dcsbm_1m", seed=0, scale=0.15)
+    b = random_labels(g.n, B, seed=5)
+    G = O.Graph(g.n, g.src, g.dst)
+    om = O.Model(G, B, b)
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, B, b, P.Params.default(dense_max_B=1))
+    check_blockmodel(pm, om)
+
+
 @pytest.mark.parametrize("B", [8, 64])
 def test_nodal_sweeps_plain_1k(B):
     g = make_config("plain_1k")
@@ -341,22 +355,26 @@ def test_partition_sparse_start_dcsbm_5k_matches_oracle():
     assert ns == ons
 
 
-def test_incremental_commit_equals_full_rebuild():
-    # the dense apply step updates M from the moved vertices' rows when few
+@pytest.mark.parametrize("dmax", [4096, 1])
+def test_incremental_commit_equals_full_rebuild(dmax):
+    # the apply step updates the counts (dense M, or the cell counts of the
+    # sparse rows' counting rebuild) from the moved vertices' rows when few
     # moved; recounting from all edges must give the same M and DL
     g = make_config("dcsbm_1m", scale=0.05)
     b = perturb(g.planted, 316, 0.3, seed=0)
     pg = P.Graph(g.n, g.src, g.dst)
-    inc = P.Model(pg, 316, b, P.Params.default(seed=5))
-    full = P.Model(pg, 316, b, P.Params.default(seed=5, full_rebuild=1))
+    inc = P.Model(pg, 316, b, P.Params.default(seed=5, dense_max_B=dmax))
+    full = P.Model(pg, 316, b, P.Params.default(seed=5, dense_max_B=dmax, full_rebuild=1))
     G = O.Graph(g.n, g.src, g.dst)
     om = O.Model(G, 316, b)
-    for sw in range(4):
+    for sw in range(8):
         si = inc.sweep(sw)
         sf = full.sweep(sw)
         assert si.n_accepted == sf.n_accepted
         assert np.array_equal(inc.assignment(), full.assignment())
-        assert np.array_equal(inc.dense(), full.dense())
+        ki, ci = inc.coo()
+        kf, cf = full.coo()
+        assert np.array_equal(ki, kf) and np.array_equal(ci, cf)
         assert inc.dl() == full.dl()
     om.set_b(316, inc.assignment())
     check_blockmodel(inc, om)
