@@ -139,7 +139,7 @@ def run_ours(args, rank, world, local_rank):
     g, B, b0 = workload(args.config, args.scale)
     stream = torch.cuda.current_stream(dev)
     graph = P.Graph(g.n, g.src, g.dst)
-    params = P.Params.default(seed=args.seed, dense_max_B=dense_max_b(args))
+    params = P.Params.default(seed=args.seed, dense_max_B=dense_max_b(args), dl_fp32=1 if args.dl == "fp32" else 0)
     model = P.Model(graph, B, b0, params, stream)
 
     def barrier():
@@ -328,6 +328,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "partition"])
     ap.add_argument("--m-form", default="dense", choices=["dense", "sparse"])
+    ap.add_argument("--dl", default="fp32", choices=["fp32", "exact"],
+                    help="fp32: x ln x terms in FP32 with the exact recheck inside the error band; "
+                         "exact: fixed-point/FP64 terms for every proposal")
     args = ap.parse_args()
     if args.mode == "partition":
         run_partition(args)

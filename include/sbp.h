@@ -59,9 +59,15 @@ typedef struct sbp_model sbp_model_t;
  * phase before the golden-ratio bracket exists; t_pre / t_post: convergence
  * threshold t of Alg. 2 before / after the bracket exists; max_sweeps: x of
  * Alg. 2; dense_max_B: largest B held as a dense B x B matrix;
- * full_rebuild: 0 lets a commit of a dense model update M from the moved
- * vertices' rows when they hold at most E/8 edge ends (the apply step of
- * Alg. 5, same result), 1 always recounts M from all edges. */
+ * full_rebuild: 0 lets a commit update the block counts (dense M, or the
+ * cell counts behind sparse rows when B * B is small) from the moved
+ * vertices' rows when they hold at most E/4 edge ends (the apply step of
+ * Alg. 5, same result), 1 always recounts them from all edges;
+ * dl_fp32: 1 evaluates the x ln x terms of Delta DL in FP32 with a rigorous
+ * error bound and redoes them exactly (fixed point and FP64) only for the
+ * proposals whose log(u) falls within the resulting band of logA, so every
+ * decision equals the FP64 one (Eq. 1-2; the precision form); 0 evaluates
+ * them exactly for every proposal. */
 typedef struct sbp_params {
     uint64_t seed;
     double beta;
@@ -72,6 +78,7 @@ typedef struct sbp_params {
     double t_post;
     int32_t dense_max_B;
     int32_t full_rebuild;
+    int32_t dl_fp32;
 } sbp_params;
 
 /* Counters of one nodal pass.  n_proposed: vertices with at least one edge
@@ -81,7 +88,8 @@ typedef struct sbp_params {
  * comparison with another FP64 implementation can excuse them);
  * n_move_edges: sum of the degrees of the vertices with s != current block
  * (the rows the pass had to aggregate); dl_before / dl_after: DL (Eq. 2)
- * before and after the rebuild. */
+ * before and after the rebuild; n_recheck: moves decided by the exact
+ * (FP64) evaluation because the fast one could not settle them. */
 typedef struct sbp_sweep_stats {
     int64_t n_proposed;
     int64_t n_moves;
@@ -90,6 +98,7 @@ typedef struct sbp_sweep_stats {
     int64_t n_move_edges;
     double dl_before;
     double dl_after;
+    int64_t n_recheck;
 } sbp_sweep_stats;
 
 /* Optional per-vertex outputs of a nodal decision pass: each member is NULL
@@ -110,7 +119,8 @@ typedef struct sbp_vertex_trace {
 size_t sbp_last_error(char *buf, size_t len);
 
 /* Fills p with the defaults: seed 0, beta 3, 10 merge proposals, 100
- * sweeps, reduction 0.5, t 5e-4 / 1e-4, dense_max_B 4096. */
+ * sweeps, reduction 0.5, t 5e-4 / 1e-4, dense_max_B 4096, full_rebuild 0,
+ * dl_fp32 1. */
 int sbp_default_params(sbp_params *p);
 
 /* Loads a directed graph given as COO (src[e] -> dst[e], e < m; host or

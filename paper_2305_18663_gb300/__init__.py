@@ -50,6 +50,7 @@ class Params(C.Structure):
         ("t_post", C.c_double),
         ("dense_max_B", C.c_int32),
         ("full_rebuild", C.c_int32),
+        ("dl_fp32", C.c_int32),
     ]
 
     @classmethod
@@ -70,6 +71,7 @@ class SweepStats(C.Structure):
         ("n_move_edges", C.c_int64),
         ("dl_before", C.c_double),
         ("dl_after", C.c_double),
+        ("n_recheck", C.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -66,6 +66,7 @@ int validate_params(const sbp_params &p) {
     if (!(p.t_pre > 0) || !(p.t_post > 0)) return fail(SBP_EINVAL, "params: thresholds must be > 0");
     if (p.dense_max_B < 1 || p.dense_max_B > 16384) return fail(SBP_EINVAL, "params: dense_max_B must be in [1, 16384]");
     if (p.full_rebuild != 0 && p.full_rebuild != 1) return fail(SBP_EINVAL, "params: full_rebuild must be 0 or 1");
+    if (p.dl_fp32 != 0 && p.dl_fp32 != 1) return fail(SBP_EINVAL, "params: dl_fp32 must be 0 or 1");
     return SBP_OK;
 }
 
@@ -91,6 +92,7 @@ int read_stats(sbp_model *m, sbp_sweep_stats *out) {
     out->n_accepted = (int64_t)h->c.accepted;
     out->n_margin = (int64_t)h->c.margin;
     out->n_move_edges = (int64_t)h->c.move_edges;
+    out->n_recheck = (int64_t)h->c.recheck;
     out->dl_after = h->dl[0];
     out->dl_before = h->dl[1];
     return SBP_OK;
@@ -188,6 +190,8 @@ extern "C" int sbp_default_params(sbp_params *p) {
     p->t_pre = 5e-4;
     p->t_post = 1e-4;
     p->dense_max_B = 4096;
+    p->full_rebuild = 0;
+    p->dl_fp32 = 1;
     return SBP_OK;
 }
 

@@ -89,7 +89,7 @@ namespace sbp {
 
 // device-side counters of a decision pass: proposed, moves, accepted, margin
 struct DevCounters {
-    unsigned long long proposed, moves, accepted, margin, move_edges, acc_edges;
+    unsigned long long proposed, moves, accepted, margin, move_edges, acc_edges, recheck;
 };
 
 struct ModelDev {

@@ -60,7 +60,7 @@ struct DecideArgs {
 };
 
 struct Counts {
-    unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0;
+    unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0, recheck = 0;
 };
 
 __device__ __forceinline__ void write_trace(const DecideArgs &a, int v, int s, int flags, double dH, double logA) {
@@ -102,6 +102,67 @@ __device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx 
     pb += c * (double)((Mtr - ki) + (Mrt - ko) + 1) / den;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Delta L (the precision form).  f(x+k) - f(x), f(x) = x ln x, for
+// integer counts x >= 0 and x + k >= 0, from logf / log1pf (at most 2 ulp
+// each): k ln(x+k) + x log1p(k/x) when x + k >= x/2 (k/x > -1/2, so the
+// log1p argument's rounding is not amplified), else (x+k) ln(x+k) - x ln x
+// (no cancellation left to avoid).  Either way the result is within
+// 14 * 2^-24 of the sum of the magnitudes of its two parts, which is added
+// to am.  Summed over n terms in FP32 with at most d additions between any
+// term and the total, the error of Delta L stays below
+// 2^-24 (14 + d) sum(am): kDl32Base + k/32 bounds d + 14 for every kernel
+// (entries per lane or per chunk, the warp tree, the eight corner and degree
+// terms, the final additions).
+constexpr float kDl32Base = 40.0f;
+
+__device__ __forceinline__ float dxlogx32(int x, int k, float &am) {
+    if (k == 0) return 0.0f;
+    const int y = x + k;
+    const float xf = (float)x, yf = (float)y;
+    if (x == 0 || 2 * y < x) {
+        const float fy = y > 1 ? yf * logf(yf) : 0.0f;
+        const float fx = x > 1 ? xf * logf(xf) : 0.0f;
+        am += fabsf(fy) + fabsf(fx);
+        return fy - fx;
+    }
+    const float kf = (float)k;
+    const float t1 = kf * logf(yf);
+    const float t2 = xf * log1pf(kf / xf);
+    am += fabsf(t1) + fabsf(t2);
+    return t1 + t2;
+}
+
+// bound on |Delta L (FP32) - Delta L| for a move of a degree-k vertex
+__device__ __forceinline__ float dl32_error(float am, int k) {
+    return 0x1p-24f * (kDl32Base + (float)k * (1.0f / 32.0f)) * am * 1.01f + 1e-30f;
+}
+
+// entry_fast with the FP32 Delta L terms
+__device__ __forceinline__ void entry_fast32(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, float &dl,
+                                             float &am, float &pf, float &pb) {
+    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    dl += dxlogx32(Mrt, -ko, am) + dxlogx32(Mst, ko, am);
+    dl += dxlogx32(Mtr, -ki, am) + dxlogx32(Mts, ki, am);
+    const float rc = md.rcp32[t];
+    const float c = (float)(ko + ki);
+    pf += c * (float)(Mts + Mst + 1) * rc;
+    pb += c * (float)((Mtr - ki) + (Mrt - ko) + 1) * rc;
+}
+
+// the exact Delta L terms and the FP64 Hastings terms of one entry (the
+// recheck of the precision form)
+__device__ __forceinline__ void entry_exact_all(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki,
+                                                __int128 &dl, double &fb, double &pf, double &pb) {
+    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
+    dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
+    const double den = (double)((int64_t)md.dsum[t] + md.B);
+    const double c = (double)(ko + ki);
+    pf += c * (double)((int64_t)Mts + Mst + 1) / den;
+    pb += c * (double)(((int64_t)Mtr - ki) + ((int64_t)Mrt - ko) + 1) / den;
+}
+
 // Delta L terms of the 2x2 corner (j = 0..3: (r,r) (s,s) (r,s) (s,r)) and of
 // the block degrees (j = 4..7: dout_r dout_s din_r din_s, subtracted), one
 // per lane, selected without divergence.  Returns the count it read (lanes
@@ -128,6 +189,28 @@ __device__ __forceinline__ int special_terms(const ModelDev &md, const VertexCtx
     const __int128 d = dT(md.T, md.XT, val, kk, f2);
     dl += j < 4 ? d : -d;
     fb += j < 4 ? f2 : -f2;
+    return val;
+}
+
+// special_terms with the FP32 Delta L terms
+__device__ __forceinline__ int special_terms32(const ModelDev &md, const VertexCtx &x, int j, float &dl, float &am) {
+    if (j >= 8) return 0;
+    const int r = x.r, s = x.s;
+    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s;
+    const int rowi = (j == 0 || j == 2) ? r : s;
+    const int coli = (j == 0 || j == 3) ? r : s;
+    const int blk = (j == 4 || j == 6) ? r : s;
+    const int kk = j == 0   ? -(cr + x.self)
+                   : j == 1 ? cs + x.self
+                   : j == 2 ? x.ki_r - x.ko_s
+                   : j == 3 ? x.ko_r - x.ki_s
+                   : j == 4 ? -x.Kout
+                   : j == 5 ? x.Kout
+                   : j == 6 ? -x.Kin
+                            : x.Kin;
+    const int val = j < 4 ? Mat(md, rowi, coli) : (j < 6 ? md.dout[blk] : md.din[blk]);
+    const float d = dxlogx32(val, kk, am);
+    dl += j < 4 ? d : -d;
     return val;
 }
 
@@ -161,7 +244,7 @@ __device__ __forceinline__ void corner_hastings_exact(const VertexCtx &x, const 
 // FP32 decision with its error band.  Returns 1 accept, 0 reject, -1 when
 // the band does not settle it (FP64 needed).
 __device__ __forceinline__ int fast_decision_f(float b32, float dl32, float fb32, float pf, float pb, uint64_t w2,
-                                               int k) {
+                                               int k, float eps_dl = 0.0f) {
     const uint64_t um = w2 >> 11;
     if (um == 0) return 1;  // u = 0: ln u = -inf
     const float lnpf = logf(pf), lnpb = logf(pb);
@@ -169,7 +252,7 @@ __device__ __forceinline__ int fast_decision_f(float b32, float dl32, float fb32
     const float u32 = fmaf((float)(unsigned)(um >> 21), 0x1p-32f, (float)(unsigned)(um & 0x1fffffu) * 0x1p-53f);
     const float lnu = logf(u32);
     const float diff = logA - lnu;
-    const float e = b32 * 3.0f * 0x1p-24f * (fabsf(dl32) + fabsf(fb32) + 1.0f) + 2.0f * (float)(k + 9) * 0x1p-24f +
+    const float e = b32 * (eps_dl + 3.0f * 0x1p-24f * (fabsf(dl32) + fabsf(fb32) + 1.0f)) + 2.0f * (float)(k + 9) * 0x1p-24f +
                     0x1p-23f * (fabsf(lnpf) + fabsf(lnpb) + 2.0f * fabsf(lnu) + fabsf(logA) + 1.0f);
     const float band = 4.0f * e + 1e-6f;
     if (!(fabsf(diff) > band)) return -1;  // also catches NaN / inf
@@ -253,6 +336,12 @@ __device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin
     c.acc_edges += accept ? (unsigned long long)k : 0ull;
 }
 
+// a move decided by the exact evaluation
+__device__ __forceinline__ void count_exact(Counts &c, bool accept, bool margin, int k) {
+    count_result(c, accept, margin, k);
+    c.recheck++;
+}
+
 // ---------------------------------------------------------------------------
 // proposals: one lane per vertex, all vertices of the range
 
@@ -263,6 +352,7 @@ __device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c
         atomicAdd(&md.counters->accepted, c.accepted);
         atomicAdd(&md.counters->margin, c.margin);
         if (c.acc_edges) atomicAdd(&md.counters->acc_edges, c.acc_edges);
+        if (c.recheck) atomicAdd(&md.counters->recheck, c.recheck);
     }
 }
 
@@ -274,6 +364,7 @@ __device__ __forceinline__ void flush_counts_warp(const ModelDev &md, Counts c, 
         c.accepted += __shfl_xor_sync(0xffffffffu, c.accepted, o);
         c.margin += __shfl_xor_sync(0xffffffffu, c.margin, o);
         c.acc_edges += __shfl_xor_sync(0xffffffffu, c.acc_edges, o);
+        c.recheck += __shfl_xor_sync(0xffffffffu, c.recheck, o);
         extra_edges += __shfl_xor_sync(0xffffffffu, extra_edges, o);
     }
     if ((threadIdx.x & 31) == 0) {
@@ -402,7 +493,7 @@ __global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
 // Evaluates the move v: r -> s once the entries are aggregated.
 // each_entry(f) calls f(t, ko, ki) for each entry the calling lane holds.
 // All 32 lanes call this; the result is written by lane 0.
-template <class EachEntry>
+template <bool DL32, class EachEntry>
 __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
                                               EachEntry each_entry, Counts &c) {
     const int lane = threadIdx.x & 31;
@@ -435,10 +526,19 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     __int128 dl = 0;
     double fb = 0.0;
     float pf = 0.0f, pb = 0.0f;
-    each_entry([&](int t, int ko, int ki) {
-        if (t != x.r && t != x.s) entry_fast(md, x, t, ko, ki, dl, fb, pf, pb);
-    });
-    const int val = special_terms(md, x, lane, dl, fb);
+    float dlf = 0.0f, am = 0.0f;
+    int val;
+    if (DL32) {
+        each_entry([&](int t, int ko, int ki) {
+            if (t != x.r && t != x.s) entry_fast32(md, x, t, ko, ki, dlf, am, pf, pb);
+        });
+        val = special_terms32(md, x, lane, dlf, am);
+    } else {
+        each_entry([&](int t, int ko, int ki) {
+            if (t != x.r && t != x.s) entry_fast(md, x, t, ko, ki, dl, fb, pf, pb);
+        });
+        val = special_terms(md, x, lane, dl, fb);
+    }
     CornerVals cv;
     cv.Mrr = __shfl_sync(0xffffffffu, val, 0);
     cv.Mss = __shfl_sync(0xffffffffu, val, 1);
@@ -446,13 +546,21 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     cv.Msr = __shfl_sync(0xffffffffu, val, 3);
     cv.dr = md.dsum[x.r];
     cv.ds = md.dsum[x.s];
-    dl = warp_sum_128(dl);
     pf = warp_sum_f(pf);
     pb = warp_sum_f(pb);
     corner_hastings_fast(x, cv, md.B, pf, pb);
-    const bool has_fb = __any_sync(0xffffffffu, __double_as_longlong(fb) != 0);
-    if (has_fb) fb = warp_sum(fb);
-    const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
+    int dec = -1;
+    bool has_fb = false;
+    if (DL32) {
+        dlf = warp_sum_f(dlf);
+        am = warp_sum_f(am);
+        if (!a.trace_on) dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, x.k, dl32_error(am, x.k));
+    } else {
+        dl = warp_sum_128(dl);
+        has_fb = __any_sync(0xffffffffu, __double_as_longlong(fb) != 0);
+        if (has_fb) fb = warp_sum(fb);
+        if (!a.trace_on) dec = fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
+    }
     if (dec >= 0) {
         if (lane == 0) {
             if (dec) md.bnew[x.v] = x.s;
@@ -461,16 +569,28 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
         return;
     }
     double pf64 = 0.0, pb64 = 0.0;
-    each_entry([&](int t, int ko, int ki) {
-        if (t != x.r && t != x.s) entry_exact(md, x, t, ko, ki, pf64, pb64);
-    });
+    if (DL32) {
+        // the exact Delta L as well
+        dl = 0;
+        fb = 0.0;
+        each_entry([&](int t, int ko, int ki) {
+            if (t != x.r && t != x.s) entry_exact_all(md, x, t, ko, ki, dl, fb, pf64, pb64);
+        });
+        special_terms(md, x, lane, dl, fb);
+        dl = warp_sum_128(dl);
+        if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
+    } else {
+        each_entry([&](int t, int ko, int ki) {
+            if (t != x.r && t != x.s) entry_exact(md, x, t, ko, ki, pf64, pb64);
+        });
+    }
     pf64 = warp_sum(pf64);
     pb64 = warp_sum(pb64);
     corner_hastings_exact(x, cv, md.B, pf64, pb64);
     if (lane == 0) {
         const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
         if (e.accept) md.bnew[x.v] = x.s;
-        count_result(c, e.accept, e.margin, x.k);
+        count_exact(c, e.accept, e.margin, x.k);
         write_trace(a, x.v, x.s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
     }
 }
@@ -479,6 +599,7 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
 // warp: cap int keys, cap 32-bit counts (ko | ki << 16, degrees below
 // 65536), cap 16-bit list entries, one list length.  Warps take chunks of
 // `chunk` movers and prefetch their records with one lane per mover.
+template <bool DL32>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_warp(DecideArgs a, int bin, int cap,
                                                                                     int cap_log2, int chunk) {
     extern __shared__ int dsm[];
@@ -560,7 +681,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             VertexCtx x;
             x.v = v; x.r = r; x.s = s;
             x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
-            evaluate_warp(a, md, x, w2, [&](auto &&f) {
+            evaluate_warp<DL32>(a, md, x, w2, [&](auto &&f) {
                 for (int e = lane; e < D; e += 32) {
                     const int slot = list[e];
                     const unsigned cc = cnt[slot];
@@ -587,13 +708,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
 struct CtaScratch {
     __int128 dl[kBigThreads / 32];
     double fb[kBigThreads / 32], pf64[kBigThreads / 32], pb64[kBigThreads / 32];
-    float pf[kBigThreads / 32], pb[kBigThreads / 32];
+    float pf[kBigThreads / 32], pb[kBigThreads / 32], dlf[kBigThreads / 32], am[kBigThreads / 32];
     __int128 dl_tot;
     double fb_tot;
     int rs[4];
     int nlist, self, ok, dec;
 };
 
+template <bool DL32>
 __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin, int cap, int cap_log2) {
     extern __shared__ unsigned long long smem_u64[];
     unsigned long long *cnt = smem_u64;
@@ -660,23 +782,40 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         x.ko_r = sh.rs[0]; x.ki_r = sh.rs[1]; x.ko_s = sh.rs[2]; x.ki_s = sh.rs[3];
         __int128 dl = 0;
         double fb = 0.0;
-        float pf = 0.0f, pb = 0.0f;
+        float pf = 0.0f, pb = 0.0f, dlf = 0.0f, am = 0.0f;
         for (int e = tid; e < D; e += blockDim.x) {
             const int slot = list[e];
             const int t = keys[slot];
             const unsigned long long cc = cnt[slot];
-            if (t != r && t != s) entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
+            if (t != r && t != s) {
+                if (DL32)
+                    entry_fast32(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dlf, am, pf, pb);
+                else
+                    entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
+            }
         }
-        if (tid < 32) special_terms(md, x, tid, dl, fb);
-        dl = warp_sum_128(dl);
+        if (tid < 32) {
+            if (DL32)
+                special_terms32(md, x, tid, dlf, am);
+            else
+                special_terms(md, x, tid, dl, fb);
+        }
         pf = warp_sum_f(pf);
         pb = warp_sum_f(pb);
-        if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
+        if (DL32) {
+            dlf = warp_sum_f(dlf);
+            am = warp_sum_f(am);
+        } else {
+            dl = warp_sum_128(dl);
+            if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
+        }
         if (lane == 0) {
             sh.dl[wid] = dl;
             sh.fb[wid] = fb;
             sh.pf[wid] = pf;
             sh.pb[wid] = pb;
+            sh.dlf[wid] = dlf;
+            sh.am[wid] = am;
         }
         __syncthreads();
         CornerVals cv;
@@ -689,18 +828,25 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         if (tid == 0) {
             __int128 dlt = 0;
             double fbt = 0.0;
-            float pft = 0.0f, pbt = 0.0f;
+            float pft = 0.0f, pbt = 0.0f, dlft = 0.0f, amt = 0.0f;
             for (int q = 0; q < nwarps; ++q) {
                 dlt += sh.dl[q];
                 fbt += sh.fb[q];
                 pft += sh.pf[q];
                 pbt += sh.pb[q];
+                dlft += sh.dlf[q];
+                amt += sh.am[q];
             }
             sh.dl_tot = dlt;
             sh.fb_tot = fbt;
             corner_hastings_fast(x, cv, md.B, pft, pbt);
-            const bool has_fb = __double_as_longlong(fbt) != 0;
-            const int dec = a.trace_on ? -1 : fast_decision(a.beta32, dlt, has_fb, fbt, pft, pbt, mv.w2, k);
+            int dec = -1;
+            if (!a.trace_on) {
+                if (DL32)
+                    dec = fast_decision_f(a.beta32, dlft, 0.0f, pft, pbt, mv.w2, k, dl32_error(amt, k));
+                else
+                    dec = fast_decision(a.beta32, dlt, __double_as_longlong(fbt) != 0, fbt, pft, pbt, mv.w2, k);
+            }
             sh.dec = dec;
             if (dec >= 0) {
                 if (dec) md.bnew[v] = s;
@@ -710,11 +856,27 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         __syncthreads();
         if (sh.dec < 0) {
             double pf64 = 0.0, pb64 = 0.0;
+            __int128 dle = 0;
+            double fbe = 0.0;
             for (int e = tid; e < D; e += blockDim.x) {
                 const int slot = list[e];
                 const int t = keys[slot];
                 const unsigned long long cc = cnt[slot];
-                if (t != r && t != s) entry_exact(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), pf64, pb64);
+                if (t != r && t != s) {
+                    if (DL32)
+                        entry_exact_all(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dle, fbe, pf64, pb64);
+                    else
+                        entry_exact(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), pf64, pb64);
+                }
+            }
+            if (DL32) {
+                if (tid < 32) special_terms(md, x, tid, dle, fbe);
+                dle = warp_sum_128(dle);
+                if (__any_sync(0xffffffffu, __double_as_longlong(fbe) != 0)) fbe = warp_sum(fbe);
+                if (lane == 0) {
+                    sh.dl[wid] = dle;
+                    sh.fb[wid] = fbe;
+                }
             }
             pf64 = warp_sum(pf64);
             pb64 = warp_sum(pb64);
@@ -725,14 +887,24 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
             __syncthreads();
             if (tid == 0) {
                 double pft = 0.0, pbt = 0.0;
+                __int128 dlt = sh.dl_tot;
+                double fbt = sh.fb_tot;
+                if (DL32) {
+                    dlt = 0;
+                    fbt = 0.0;
+                    for (int q = 0; q < nwarps; ++q) {
+                        dlt += sh.dl[q];
+                        fbt += sh.fb[q];
+                    }
+                }
                 for (int q = 0; q < nwarps; ++q) {
                     pft += sh.pf64[q];
                     pbt += sh.pb64[q];
                 }
                 corner_hastings_exact(x, cv, md.B, pft, pbt);
-                const Exact e = exact_decision(a.beta, sh.dl_tot, sh.fb_tot, pft, pbt, mv.w2);
+                const Exact e = exact_decision(a.beta, dlt, fbt, pft, pbt, mv.w2);
                 if (e.accept) md.bnew[v] = s;
-                count_result(c, e.accept, e.margin, k);
+                count_exact(c, e.accept, e.margin, k);
                 write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
             }
         }
@@ -776,6 +948,7 @@ struct BatchWarp {
     int r[32], s[32], rsr[32], rss[32], hasfb[32];
     long long dl[32];  // Delta L, fixed point 2^-48
     float pf[32], pb[32];
+    float dlf[32], am[32];  // FP32 Delta L and its magnitude sum (precision form)
     double fb[32];
 };
 
@@ -792,7 +965,7 @@ __device__ __forceinline__ double fix48_to_double(long long v) {
 // count array of B entries, which follows the warp's BatchWarp in shared
 // memory).  Movers are processed in sub-batches of at most kBatchEdges
 // edge ends.
-template <int MODE>
+template <int MODE, bool DL32>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_batch(DecideArgs a, int bin,
                                                                                      int warp_bytes) {
     extern __shared__ __align__(16) unsigned char bsm[];
@@ -964,6 +1137,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
         W.dl[lane] = 0;
         W.pf[lane] = 0.0f;
         W.pb[lane] = 0.0f;
+        W.dlf[lane] = 0.0f;
+        W.am[lane] = 0.0f;
         W.fb[lane] = 0.0;
         __syncwarp();
         // ---- P5: entry parallel, segmented sums per mover
@@ -973,7 +1148,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             const unsigned ent = valid ? (unsigned)W.key[e] : 0u;
             const int q = valid ? (int)(ent >> 26) : 32;
             long long d48 = 0;
-            float pfe = 0.0f, pbe = 0.0f;
+            float pfe = 0.0f, pbe = 0.0f, dlf = 0.0f, am = 0.0f;
             double f = 0.0;
             if (valid) {
                 const int t = (int)(ent & 0x3ffffffu);
@@ -988,20 +1163,33 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                     VertexCtx x;
                     x.r = rq;
                     x.s = sq;
-                    __int128 d = 0;
-                    entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
-                    d48 = (long long)(d >> 16);
+                    if (DL32) {
+                        entry_fast32(md, x, t, ko, ki, dlf, am, pfe, pbe);
+                    } else {
+                        __int128 d = 0;
+                        entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
+                        d48 = (long long)(d >> 16);
+                    }
                 }
             }
-            const bool anyfb = __any_sync(0xffffffffu, __double_as_longlong(f) != 0);
+            const bool anyfb = !DL32 && __any_sync(0xffffffffu, __double_as_longlong(f) != 0);
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int qo = __shfl_up_sync(0xffffffffu, q, o);
-                const long long d2 = __shfl_up_sync(0xffffffffu, d48, o);
                 const float p2 = __shfl_up_sync(0xffffffffu, pfe, o);
                 const float b2 = __shfl_up_sync(0xffffffffu, pbe, o);
+                if (DL32) {
+                    const float l2 = __shfl_up_sync(0xffffffffu, dlf, o);
+                    const float a2 = __shfl_up_sync(0xffffffffu, am, o);
+                    if (lane >= o && qo == q) {
+                        dlf += l2;
+                        am += a2;
+                    }
+                } else {
+                    const long long d2 = __shfl_up_sync(0xffffffffu, d48, o);
+                    if (lane >= o && qo == q) d48 += d2;
+                }
                 if (lane >= o && qo == q) {
-                    d48 += d2;
                     pfe += p2;
                     pbe += b2;
                 }
@@ -1016,7 +1204,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             }
             const int qn = __shfl_down_sync(0xffffffffu, q, 1);
             if (valid && (lane == 31 || qn != q)) {
-                W.dl[q] += d48;
+                if (DL32) {
+                    W.dlf[q] += dlf;
+                    W.am[q] += am;
+                } else {
+                    W.dl[q] += d48;
+                }
                 W.pf[q] += pfe;
                 W.pb[q] += pbe;
                 if (anyfb && __double_as_longlong(f) != 0) {
@@ -1038,37 +1231,64 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             __int128 d = 0;
             bool has_fb = W.hasfb[lane] != 0;
             double fb = has_fb ? W.fb[lane] : 0.0;
+            float dlf = W.dlf[lane], am = W.am[lane];
             CornerVals cv;
-            cv.Mrr = special_terms(md, x, 0, d, fb);
-            cv.Mss = special_terms(md, x, 1, d, fb);
-            cv.Mrs = special_terms(md, x, 2, d, fb);
-            cv.Msr = special_terms(md, x, 3, d, fb);
+            if (DL32) {
+                cv.Mrr = special_terms32(md, x, 0, dlf, am);
+                cv.Mss = special_terms32(md, x, 1, dlf, am);
+                cv.Mrs = special_terms32(md, x, 2, dlf, am);
+                cv.Msr = special_terms32(md, x, 3, dlf, am);
 #pragma unroll
-            for (int jj = 4; jj < 8; ++jj) special_terms(md, x, jj, d, fb);
-            has_fb = has_fb || __double_as_longlong(fb) != 0;
+                for (int jj = 4; jj < 8; ++jj) special_terms32(md, x, jj, dlf, am);
+            } else {
+                cv.Mrr = special_terms(md, x, 0, d, fb);
+                cv.Mss = special_terms(md, x, 1, d, fb);
+                cv.Mrs = special_terms(md, x, 2, d, fb);
+                cv.Msr = special_terms(md, x, 3, d, fb);
+#pragma unroll
+                for (int jj = 4; jj < 8; ++jj) special_terms(md, x, jj, d, fb);
+                has_fb = has_fb || __double_as_longlong(fb) != 0;
+            }
             cv.dr = md.dsum[r];
             cv.ds = md.dsum[s];
-            const long long dl48 = W.dl[lane] + (long long)(d >> 16);
+            long long dl48 = W.dl[lane] + (long long)(d >> 16);
             float pf = W.pf[lane], pb = W.pb[lane];
             corner_hastings_fast(x, cv, B, pf, pb);
-            const int dec = a.trace_on ? -1
-                                       : fast_decision_f(a.beta32, fix48_to_float(dl48), has_fb ? (float)fb : 0.0f, pf, pb,
-                                                         w2, k);
+            int dec = -1;
+            if (!a.trace_on) {
+                if (DL32)
+                    dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, k, dl32_error(am, k));
+                else
+                    dec = fast_decision_f(a.beta32, fix48_to_float(dl48), has_fb ? (float)fb : 0.0f, pf, pb, w2, k);
+            }
             if (dec >= 0) {
                 if (dec) md.bnew[v] = s;
                 count_result(c, dec != 0, false, k);
             } else {
                 double pf64 = 0.0, pb64 = 0.0;
+                __int128 dle = 0;
+                double fbe = 0.0;
                 for (int e = my_est; e < my_est + my_ecnt; ++e) {
                     const int t = (int)((unsigned)W.key[e] & 0x3ffffffu);
                     if (t == r || t == s) continue;
                     const unsigned ec = W.ec[e];
-                    entry_exact(md, x, t, (int)(ec & 0xffu), (int)(ec >> 8), pf64, pb64);
+                    if (DL32)
+                        entry_exact_all(md, x, t, (int)(ec & 0xffu), (int)(ec >> 8), dle, fbe, pf64, pb64);
+                    else
+                        entry_exact(md, x, t, (int)(ec & 0xffu), (int)(ec >> 8), pf64, pb64);
+                }
+                double dL;
+                if (DL32) {
+#pragma unroll 1
+                    for (int jj = 0; jj < 8; ++jj) special_terms(md, x, jj, dle, fbe);
+                    dL = fix_to_double(dle) + fbe;
+                } else {
+                    dL = fix48_to_double(dl48) + (has_fb ? fb : 0.0);
                 }
                 corner_hastings_exact(x, cv, B, pf64, pb64);
-                const Exact ex = exact_decision_d(a.beta, fix48_to_double(dl48) + (has_fb ? fb : 0.0), pf64, pb64, w2);
+                const Exact ex = exact_decision_d(a.beta, dL, pf64, pb64, w2);
                 if (ex.accept) md.bnew[v] = s;
-                count_result(c, ex.accept, ex.margin, k);
+                count_exact(c, ex.accept, ex.margin, k);
                 write_trace(a, v, s, 1 | (ex.accept ? 2 : 0) | (ex.margin ? 4 : 0), ex.dH, ex.logA);
             }
         }
@@ -1127,6 +1347,66 @@ ModelDev model_dev(sbp_model *m) {
     return d;
 }
 
+namespace {
+
+// the evaluation kernels of the three degree groups (after k_propose)
+template <bool DL32>
+int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
+    const sbp_graph *g = m->g;
+    const int B = m->B;
+    // movers with k <= 32: batches of 32 per warp
+    if (g->bin[2] > g->bin[1]) {
+        const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
+        const size_t smem = (size_t)wb * kWarpsPerCta;
+        SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<0, DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_eval_batch<0, DL32><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 0, wb);
+        SBP_LAUNCHED();
+    }
+    auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
+    // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
+    // small, otherwise one warp each with a 256-slot table
+    if (g->bin[3] > g->bin[2]) {
+        if (B <= kDirectMaxB) {
+            const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
+            const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
+            const size_t smem = (size_t)wb * nwarps;
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<1, DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_batch<1, DL32><<<sms * 3, nwarps * 32, smem, m->stream>>>(a, 1, wb);
+            SBP_LAUNCHED();
+        } else {
+            const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp<DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_warp<DL32><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
+            SBP_LAUNCHED();
+        }
+    }
+    // movers with k > 128: per-warp tables sized for min(max degree, B)
+    // distinct blocks while they fit, one CTA per mover beyond that
+    if (g->bin[4] > g->bin[3]) {
+        const int64_t dmax = g->max_deg < B ? g->max_deg : B;
+        const int64_t need = dmax + dmax / 4 + 2;
+        int cap_log2 = 6;
+        while ((int64_t(1) << cap_log2) < need) ++cap_log2;
+        const int cap = 1 << cap_log2;
+        if (cap <= 4096 && g->max_deg < 65536) {
+            const int nwarps = cap <= 2048 ? 8 : 4;
+            const size_t smem = warp_smem(cap, nwarps);
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp<DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_warp<DL32><<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);
+            SBP_LAUNCHED();
+        } else {
+            const size_t smem = (size_t)cap * (8 + 4 + 4);
+            if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
+            SBP_CUDA(cudaFuncSetAttribute(k_eval_cta<DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, m->stream>>>(a, 2, cap, cap_log2);
+            SBP_LAUNCHED();
+        }
+    }
+    return SBP_OK;
+}
+
+}  // namespace
+
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace) {
     const sbp_graph *g = m->g;
     if (!m->movers) {
@@ -1166,55 +1446,7 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
         k_propose<<<(int)blocks, 256, 0, m->stream>>>(a);
         SBP_LAUNCHED();
     }
-    // movers with k <= 32: batches of 32 per warp
-    if (g->bin[2] > g->bin[1]) {
-        const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
-        const size_t smem = (size_t)wb * kWarpsPerCta;
-        SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_eval_batch<0><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 0, wb);
-        SBP_LAUNCHED();
-    }
-    auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
-    // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
-    // small, otherwise one warp each with a 256-slot table
-    if (g->bin[3] > g->bin[2]) {
-        if (B <= kDirectMaxB) {
-            const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
-            const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
-            const size_t smem = (size_t)wb * nwarps;
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_eval_batch<1><<<sms * 3, nwarps * 32, smem, m->stream>>>(a, 1, wb);
-            SBP_LAUNCHED();
-        } else {
-            const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_eval_warp<<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
-            SBP_LAUNCHED();
-        }
-    }
-    // movers with k > 128: per-warp tables sized for min(max degree, B)
-    // distinct blocks while they fit, one CTA per mover beyond that
-    if (g->bin[4] > g->bin[3]) {
-        const int64_t dmax = g->max_deg < B ? g->max_deg : B;
-        const int64_t need = dmax + dmax / 4 + 2;
-        int cap_log2 = 6;
-        while ((int64_t(1) << cap_log2) < need) ++cap_log2;
-        const int cap = 1 << cap_log2;
-        if (cap <= 4096 && g->max_deg < 65536) {
-            const int nwarps = cap <= 2048 ? 8 : 4;
-            const size_t smem = warp_smem(cap, nwarps);
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_eval_warp<<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);
-            SBP_LAUNCHED();
-        } else {
-            const size_t smem = (size_t)cap * (8 + 4 + 4);
-            if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_eval_cta<<<sms * 4, kBigThreads, smem, m->stream>>>(a, 2, cap, cap_log2);
-            SBP_LAUNCHED();
-        }
-    }
-    return SBP_OK;
+    return m->p.dl_fp32 ? launch_evals<true>(m, a, sms) : launch_evals<false>(m, a, sms);
 }
 
 }  // namespace sbp

@@ -213,6 +213,45 @@ def test_nodal_sweeps_scaled_dcsbm():
     assert margin <= 5
 
 
+def _hub_graph():
+    rng = np.random.default_rng(21)
+    n = 6000
+    src = rng.integers(0, n, 40000)
+    dst = rng.integers(0, n, 40000)
+    for hub, deg in [(7, 2600), (8, 3100), (9, 5000)]:
+        src = np.concatenate([src, np.full(deg, hub), rng.integers(0, n, deg // 2), [hub, hub]])
+        dst = np.concatenate([dst, rng.integers(0, n, deg), np.full(deg // 2, hub), [hub, hub]])
+    return _G(n, src, dst)
+
+
+@pytest.mark.parametrize("case", ["dcsbm_dense", "dcsbm_sparse", "hubs_B3000", "hubs_B64"])
+def test_fp32_delta_dl_decides_as_exact(case):
+    # the precision form (FP32 x ln x terms, exact recheck inside the error
+    # band) must take exactly the decisions of the exact evaluation, with no
+    # per-vertex trace (a trace forces the exact path)
+    if case.startswith("dcsbm"):
+        g = make_config("dcsbm_1m", scale=0.05)
+        B, b = 316, perturb(g.planted, 316, 0.3, seed=0)
+        dmax = 4096 if case.endswith("dense") else 1
+    else:
+        g = _hub_graph()
+        B = 3000 if case == "hubs_B3000" else 64
+        b, dmax = random_labels(g.n, B, seed=2), 4096
+    pg = P.Graph(g.n, g.src, g.dst)
+    fast = P.Model(pg, B, b, P.Params.default(seed=11, dense_max_B=dmax, dl_fp32=1))
+    exact = P.Model(pg, B, b, P.Params.default(seed=11, dense_max_B=dmax, dl_fp32=0))
+    rechecks = moves = 0
+    for sw in range(5):
+        sf = fast.sweep(sw)
+        se = exact.sweep(sw)
+        assert sf.n_accepted == se.n_accepted and sf.n_moves == se.n_moves
+        assert np.array_equal(fast.assignment(), exact.assignment())
+        assert fast.dl() == exact.dl()
+        rechecks += sf.n_recheck
+        moves += sf.n_moves
+    assert rechecks < moves
+
+
 def test_shards_then_commit_equal_one_sweep():
     g = make_config("plain_1k")
     b = random_labels(g.n, 16, seed=4)
