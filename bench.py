@@ -122,6 +122,27 @@ def algorithmic_bytes(n, m, B, move_edges):
     return decide, rebuild
 
 
+def dl_vs_fp64(P, torch, model, g, B, dev):
+    """DL of the final state as the library holds it (exact fixed-point
+    sums) against an FP64 evaluation of Eq. 2 from the same counts (the
+    library's allocation-free FP64 reduction), as a relative difference."""
+    if B > 4096:
+        return None
+    keys, cnt = model.coo()
+    M = np.zeros(B * B, np.int32)
+    M[keys] = cnt
+    dout, din = model.degrees()
+    Md = torch.from_numpy(M).to(dev)
+    od = torch.from_numpy(dout).to(dev)
+    idg = torch.from_numpy(din).to(dev)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    P.sbp_dense_dl_noalloc(Md, B, od, idg, g.m, g.n, out, torch.cuda.current_stream(dev).cuda_stream)
+    torch.cuda.synchronize(dev)
+    dl64 = float(out.item())
+    dl = model.dl()
+    return {"dl": dl, "dl_fp64": dl64, "rel_error": abs(dl - dl64) / abs(dl64)}
+
+
 def dense_max_b(args) -> int:
     """dense: M held dense while B <= 4096; sparse: per-row hashed sparse
     rows at every B (dense_max_B = 1)."""
@@ -208,6 +229,7 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     st = P.sbp_nodal_sweep(model.h, sweep_id, 0, g.n, stats=True)
+    precision = dl_vs_fp64(P, torch, model, g, B, dev)
 
     res = None
     if rank == 0:
@@ -241,6 +263,7 @@ def run_ours(args, rank, world, local_rank):
             "breakdown_ms": {"decide": dec_avg, "commit": statistics.mean(commit_ms),
                              "decide_min": min(decide_ms), "commit_bytes": reb_b},
             "last_sweep": st.as_dict(),
+            "precision": precision,
             "clocks": ck,
         }
     return res

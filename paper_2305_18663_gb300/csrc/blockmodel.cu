@@ -216,13 +216,10 @@ __global__ void k_zero_if(int32_t *__restrict__ M, int64_t n, const int32_t *__r
 // old (block, block) cell and enters the new one.  An edge is visited once:
 // through the out-row of its moved source, or through the in-row of its
 // moved target when the source stayed.  Lanes take the edges of one row,
-// four loads in flight per lane; lanes that hit the same cell add once.
+// four loads in flight per lane.
 // (a dense M has B <= 16384, so a cell index fits 32 bits)
 __device__ __forceinline__ void delta_add(int32_t *__restrict__ M, bool valid, int key, int d) {
-    const unsigned act = __ballot_sync(0xffffffffu, valid);
-    if (!act) return;
-    const unsigned peers = __match_any_sync(0xffffffffu, valid ? key : -1);
-    if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&M[key], d * __popc(peers));
+    if (valid) atomicAdd(&M[key], d);
 }
 
 // out-row [a, z) of a vertex moved r -> s
