@@ -230,6 +230,27 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = float(t.item())
     st = P.sbp_nodal_sweep(model.h, sweep_id, 0, g.n, stats=True)
     precision = dl_vs_fp64(P, torch, model, g, B, dev)
+    dense_comparison = None
+    if args.m_form == "sparse" and B <= 4096:
+        # the same sweeps with M held dense (the comparison form)
+        model.close()
+        dm = P.Model(graph, B, b0, P.Params.default(seed=args.seed, dense_max_B=4096, dl_fp32=params.dl_fp32), stream)
+        for k in range(args.warmup):
+            P.sbp_nodal_decide(dm.h, k, 0, g.n)
+            P.sbp_commit(dm.h, stats=False)
+        t0e = torch.cuda.Event(enable_timing=True)
+        t1e = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        t0e.record(stream)
+        for k in range(args.warmup, args.warmup + args.steps):
+            P.sbp_nodal_decide(dm.h, k, 0, g.n)
+            P.sbp_commit(dm.h, stats=False)
+        t1e.record(stream)
+        torch.cuda.synchronize(dev)
+        dms = t0e.elapsed_time(t1e)
+        dense_comparison = {"m_form": "dense", "value": g.n * args.steps / (dms * 1e-3), "unit": UNIT,
+                            "ms_per_step": dms / args.steps}
+        dm.close()
 
     res = None
     if rank == 0:
@@ -264,6 +285,7 @@ def run_ours(args, rank, world, local_rank):
                              "decide_min": min(decide_ms), "commit_bytes": reb_b},
             "last_sweep": st.as_dict(),
             "precision": precision,
+            "dense_comparison": dense_comparison,
             "clocks": ck,
         }
     return res
@@ -338,6 +360,73 @@ def run_partition(args):
     print(json.dumps(res))
 
 
+def _gen(spec):
+    from synth.dcsbm import dcsbm
+
+    g = dcsbm(**spec)
+    return g.n, g.src, g.dst
+
+
+def gen_graphs(specs, procs=None):
+    """Draws the graphs of specs (a process pool, spawned: no CUDA in it)."""
+    import multiprocessing as mp
+
+    procs = procs or min(16, os.cpu_count() or 1)
+    if procs <= 1 or len(specs) < 4:
+        return [_gen(s) for s in specs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_gen, specs, chunksize=max(1, len(specs) // (4 * procs)))
+
+
+def run_batch(args):
+    """The batching form: many small uneven graphs partitioned (full
+    golden-ratio runs) by one batch call against one sbp_partition call per
+    graph, on the same graphs, with every result compared."""
+    import torch
+
+    import paper_2305_18663_gb300 as P
+    from synth.dcsbm import batch_specs
+
+    torch.cuda.set_device(0)
+    P.load()
+    specs = batch_specs(args.batch_total, seed=args.seed)
+    stride = max(1, args.batch_total // args.batch_count)
+    chosen = specs[::stride][: args.batch_count]
+    t0 = time.perf_counter()
+    raw = gen_graphs(chosen)
+    t_gen = time.perf_counter() - t0
+    graphs = [P.Graph(n, src, dst) for n, src, dst in raw]
+    opts = P.BatchOptions.default(workers=args.batch_workers)
+    params = P.Params.default(seed=args.seed, dense_max_B=opts.dense_max_B)
+    torch.cuda.synchronize()
+    bstats = P.BatchStats()
+    t0 = time.perf_counter()
+    out = P.partition_batch(graphs, params, opts, bstats)
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plain = [g.partition(params) for g in graphs]
+    t_plain = time.perf_counter() - t0
+    mismatch = sum(1 for (b, B, dl, ns, _, _), (pb, pB, pdl, pns) in zip(out, plain)
+                   if not (B == pB and dl == pdl and ns == pns and np.array_equal(b, pb)))
+    done = np.array([o[5] for o in out])
+    nv = sum(g.n for g in graphs)
+    ne = sum(g.m for g in graphs)
+    res = {"metric": "graphs/s, batched vs plain (full partition runs)", "value": len(graphs) / t_batch,
+           "unit": "graphs/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
+           "plain": {"value": len(graphs) / t_plain, "unit": "graphs/s", "seconds": t_plain},
+           "batched_seconds": t_batch, "speedup_vs_plain": t_plain / t_batch, "batch_stats": bstats.as_dict(),
+           "results_equal": mismatch == 0, "mismatches": mismatch,
+           "completion_s": {"p50": float(np.percentile(done, 50)), "p99": float(np.percentile(done, 99))},
+           "dtype": "f32 terms, exact recheck", "data": "synthetic",
+           "config": {"workload": f"{len(graphs)} of {args.batch_total} directed DCSBM graphs (every {stride}th), "
+                                  "N log-uniform [500, 50000], mean out-degree uniform [8, 32], "
+                                  "planted B = round(sqrt(N)/2), degree exponent 2.5 on [1, 100], intra:inter 4:1",
+                      "graphs": len(graphs), "vertices": nv, "edges": ne, "workers": args.batch_workers,
+                      "max_B": opts.max_B, "max_n": opts.max_n, "dense_max_B": opts.dense_max_B,
+                      "generation_s": t_gen}}
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,14 +438,22 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--oracle-sample", type=int, default=50_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "partition"])
-    ap.add_argument("--m-form", default="dense", choices=["dense", "sparse"])
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "partition", "batch"])
+    ap.add_argument("--batch-total", type=int, default=4096, help="graphs of the batching workload")
+    ap.add_argument("--batch-count", type=int, default=256, help="graphs actually run (an evenly strided subset)")
+    ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--m-form", default="sparse", choices=["dense", "sparse"],
+                    help="sparse: hashed sparse rows at every B (the M form of the 1M-vertex precision "
+                         "configuration; a dense run of the same sweeps is reported beside it); dense: M dense")
     ap.add_argument("--dl", default="fp32", choices=["fp32", "exact"],
                     help="fp32: x ln x terms in FP32 with the exact recheck inside the error band; "
                          "exact: fixed-point/FP64 terms for every proposal")
     args = ap.parse_args()
     if args.mode == "partition":
         run_partition(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
         return
 
     rank = int(os.environ.get("RANK", 0))

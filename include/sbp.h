@@ -241,6 +241,74 @@ int sbp_dense_dl_noalloc(const int32_t *M, int32_t B, const int32_t *dout, const
 int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1, int32_t count,
                      uint64_t *out);
 
+/* ---------------------------------------------------------------------
+ * Batching form: many graphs partitioned together.
+ *
+ * Every graph runs the same golden-ratio search as sbp_partition (Section
+ * II-B; Alg. 1, 2) and ends with the same assignment, B, DL and sweep count.
+ * MCMC phases at B <= max_B run in persistent launches over all waiting
+ * graphs (a CTA per graph phase, sweeps and the convergence test on the
+ * device), overlapped with the per-graph work (merge phases, larger-B
+ * phases) that `workers` host threads drive on their graphs' streams.  Graphs are admitted in input order while their
+ * estimated device memory fits mem_fraction of the free memory, and each
+ * model is freed when its graph finishes.
+ *
+ * workers: host threads (1..256); max_B: largest B of a batched MCMC phase
+ * (1..1024); max_n: largest graph (vertices) whose phases are batched (a CTA
+ * takes a whole phase, so big graphs are better served by the per-graph
+ * kernels); dense_max_B: dense/sparse switch of the batch's models
+ * (max_B..16384); ctas_per_sm: persistent CTAs per SM (1..8); mem_fraction:
+ * (0, 0.95]. */
+typedef struct sbp_batch_options {
+    int32_t workers;
+    int32_t max_B;
+    int32_t dense_max_B;
+    int32_t ctas_per_sm;
+    int32_t max_n;
+    int32_t reserved;
+    double mem_fraction;
+} sbp_batch_options;
+
+/* Per-graph result: B, DL and sweeps as sbp_partition returns them; t_admit
+ * and t_done: seconds from the call's start to the graph's admission and to
+ * its result. */
+typedef struct sbp_batch_result {
+    int32_t B;
+    int32_t reserved;
+    double dl;
+    int64_t n_sweeps;
+    double t_admit;
+    double t_done;
+} sbp_batch_result;
+
+/* Where a batch call spent its time: rounds: persistent launches;
+ * s_per_graph: worker-seconds of per-graph work (summed over the workers),
+ * of which s_merge in set-up, merge phases and compaction and s_sweeps in
+ * per-graph MCMC sweeps; s_batched: wall seconds of the persistent launches;
+ * MCMC phases run batched and per graph. */
+typedef struct sbp_batch_stats {
+    int64_t rounds;
+    double s_per_graph;
+    double s_batched;
+    int64_t phases_batched;
+    int64_t phases_per_graph;
+    double s_merge;
+    double s_sweeps;
+} sbp_batch_stats;
+
+/* Fills o with the defaults: 16 workers, max_B 512, max_n 4096, dense_max_B
+ * 4096, 2 CTAs per SM, mem_fraction 0.5. */
+int sbp_default_batch_options(sbp_batch_options *o);
+
+/* Partitions graphs[0..count).  p: NULL for the defaults (shared by every
+ * graph); o: NULL for the defaults.  b_out: NULL, or count pointers (host or
+ * device) to n_i labels each; res: count results (host); stats: NULL or
+ * the call's time split.  Fails with the first error of any graph; partial
+ * results are then undefined. */
+int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
+                        const sbp_batch_options *o, int32_t *const *b_out, sbp_batch_result *res,
+                        sbp_batch_stats *stats);
+
 /* Number of kernel launches the library has issued in this process, over
  * all handles and devices (a host-side counter, incremented as each launch
  * is enqueued, whether or not the kernel then finds work to do).  For

@@ -26,7 +26,8 @@ __all__ = [
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
-    "sbp_dense_dl_noalloc", "sbp_kernel_launches",
+    "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_default_batch_options", "sbp_partition_batch",
+    "BatchOptions", "BatchResult", "BatchStats", "partition_batch",
     "Graph", "Model", "deal_vertices",
 ]
 
@@ -72,6 +73,52 @@ class SweepStats(C.Structure):
         ("dl_before", C.c_double),
         ("dl_after", C.c_double),
         ("n_recheck", C.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [
+        ("workers", C.c_int32),
+        ("max_B", C.c_int32),
+        ("dense_max_B", C.c_int32),
+        ("ctas_per_sm", C.c_int32),
+        ("max_n", C.c_int32),
+        ("reserved", C.c_int32),
+        ("mem_fraction", C.c_double),
+    ]
+
+    @classmethod
+    def default(cls, **kw) -> "BatchOptions":
+        o = cls()
+        _check(lib().sbp_default_batch_options(C.byref(o)))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+
+class BatchResult(C.Structure):
+    _fields_ = [
+        ("B", C.c_int32),
+        ("reserved", C.c_int32),
+        ("dl", C.c_double),
+        ("n_sweeps", C.c_int64),
+        ("t_admit", C.c_double),
+        ("t_done", C.c_double),
+    ]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [
+        ("rounds", C.c_int64),
+        ("s_per_graph", C.c_double),
+        ("s_batched", C.c_double),
+        ("phases_batched", C.c_int64),
+        ("phases_per_graph", C.c_int64),
+        ("s_merge", C.c_double),
+        ("s_sweeps", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -124,6 +171,8 @@ def load(path: str | None = None):
         "sbp_philox_check": (C.c_int, [u64, u64, u64, u64, u64, u64, i32, vp]),
         "sbp_dense_dl_noalloc": (C.c_int, [vp, i32, vp, vp, i64, i64, vp, vp]),
         "sbp_kernel_launches": (C.c_int, [P(u64)]),
+        "sbp_default_batch_options": (C.c_int, [P(BatchOptions)]),
+        "sbp_partition_batch": (C.c_int, [vp, i32, P(Params), P(BatchOptions), vp, P(BatchResult), P(BatchStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -252,6 +301,26 @@ def sbp_partition(g: int, b_out, params: Params | None = None, stream=None) -> t
     return B.value, dl.value, ns.value
 
 
+def sbp_default_batch_options() -> BatchOptions:
+    return BatchOptions.default()
+
+
+def sbp_partition_batch(graphs: list[int], b_outs, params: Params | None = None,
+                        options: BatchOptions | None = None, stats: BatchStats | None = None) -> list[BatchResult]:
+    """graphs: handles; b_outs: None or one int32 buffer per graph."""
+    n = len(graphs)
+    ga = (C.c_void_p * max(n, 1))(*graphs)
+    res = (BatchResult * max(n, 1))()
+    if b_outs is None:
+        bp = None
+    else:
+        bp = (C.c_void_p * max(n, 1))(*[_ptr(b, np.int32) for b in b_outs])
+    _check(lib().sbp_partition_batch(ga, n, C.byref(params) if params else None,
+                                     C.byref(options) if options else None, bp, res,
+                                     C.byref(stats) if stats is not None else None))
+    return [res[i] for i in range(n)]
+
+
 def sbp_get_assignment(m: int, b_out) -> None:
     _check(lib().sbp_get_assignment(m, _ptr(b_out, np.int32)))
 
@@ -339,6 +408,15 @@ class Graph:
         b = np.zeros(self.n, np.int32)
         B, dl, ns = sbp_partition(self.h, b, params, stream)
         return b, B, dl, ns
+
+
+def partition_batch(graphs: list["Graph"], params: Params | None = None, options: BatchOptions | None = None,
+                    stats: BatchStats | None = None):
+    """Partitions every graph (the batching form); returns per graph
+    (b, B, dl, n_sweeps, t_admit, t_done)."""
+    outs = [np.zeros(g.n, np.int32) for g in graphs]
+    res = sbp_partition_batch([g.h for g in graphs], outs, params, options, stats)
+    return [(outs[i], r.B, r.dl, r.n_sweeps, r.t_admit, r.t_done) for i, r in enumerate(res)]
 
 
 class Model:

@@ -3,11 +3,14 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
+#include "driver.h"
 
 namespace sbp {
 
@@ -15,6 +18,56 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t model_alloc(void **p, size_t bytes, cudaStream_t st) {
+    return cudaMallocAsync(p, bytes > 0 ? bytes : 1, st);
+}
+
+void model_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+namespace {
+std::mutex g_pinned_mu;
+std::vector<void *> g_pinned_free;
+}  // namespace
+
+// 4 KB pinned buffers, never returned to the driver (cudaFreeHost would
+// synchronise the device)
+void *pinned_get() {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+        void *p = g_pinned_free.back();
+        g_pinned_free.pop_back();
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pinned_put(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
+
+int ensure_dyn_smem(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> set;
+    int dev = 0;
+    SBP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = set[std::make_pair(dev, func)];
+    if (bytes > cur) {
+        SBP_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        cur = bytes;
+    }
+    return SBP_OK;
+}
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -197,27 +250,15 @@ extern "C" int sbp_default_params(sbp_params *p) {
 
 extern "C" void sbp_free_model(sbp_model_t *m) {
     if (!m) return;
-    if (m->stream) cudaStreamSynchronize(m->stream);
-    cudaFree(m->b);
-    cudaFree(m->bnew);
-    cudaFree(m->M);
-    cudaFree(m->P);
-    cudaFree(m->Pc);
-    cudaFree(m->dout);
-    cudaFree(m->din);
-    cudaFree(m->rcp);
-    cudaFree(m->dl);
-    cudaFree(m->partials);
-    cudaFree(m->counters);
-    cudaFree(m->status);
-    cudaFree(m->best_s);
-    cudaFree(m->best_d);
-    cudaFree(m->map);
-    cudaFree(m->vcount);
-    cudaFree(m->movers);
-    cudaFree(m->mcount);
+    cudaStream_t st = m->stream;
+    if (st) cudaStreamSynchronize(st);
+    void *ps[] = {m->b,        m->bnew,   m->M,        m->P,       m->Pc,     m->dout,  m->din,
+                  m->rcp,      m->rcp32,  m->dsum,     m->dl,      m->partials, m->counters, m->status,
+                  m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount};
+    for (void *p : ps) model_free(p, st);
     free_sparse(m);
-    cudaFreeHost(m->pinned);
+    pinned_put(m->pinned);
+    if (st) cudaStreamSynchronize(st);
     delete m;
 }
 
@@ -237,10 +278,13 @@ extern "C" int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32
     m->stream = static_cast<cudaStream_t>(stream);
     m->npartials = 1024;
     const size_t n = (size_t)g->n;
-    if (cudaMalloc(&m->b, n * 4) != cudaSuccess || cudaMalloc(&m->bnew, n * 4) != cudaSuccess ||
-        cudaMalloc(&m->dl, 16) != cudaSuccess || cudaMalloc(&m->partials, (size_t)m->npartials * 32) != cudaSuccess ||
-        cudaMalloc(&m->counters, sizeof(DevCounters)) != cudaSuccess || cudaMalloc(&m->status, 8) != cudaSuccess ||
-        cudaMallocHost(&m->pinned, 4096) != cudaSuccess) {
+    cudaStream_t st = m->stream;
+    m->pinned = pinned_get();
+    if (model_alloc((void **)&m->b, n * 4, st) != cudaSuccess || model_alloc((void **)&m->bnew, n * 4, st) != cudaSuccess ||
+        model_alloc((void **)&m->dl, 16, st) != cudaSuccess ||
+        model_alloc((void **)&m->partials, (size_t)m->npartials * 32, st) != cudaSuccess ||
+        model_alloc((void **)&m->counters, sizeof(DevCounters), st) != cudaSuccess ||
+        model_alloc((void **)&m->status, 8, st) != cudaSuccess || !m->pinned) {
         cudaGetLastError();
         sbp_free_model(m);
         return fail(SBP_ENOMEM, "sbp_build_blockmodel: allocation failed");
@@ -349,50 +393,6 @@ extern "C" int sbp_compact(sbp_model_t *m, int32_t *B_out) {
 namespace sbp {
 namespace {
 
-struct State {
-    int32_t B = 0;
-    double dl = 0;
-    std::vector<int32_t> b;
-};
-
-struct Bracket {
-    State s[3];  // 0 hi, 1 mid, 2 lo (B == 0: empty)
-    void insert(State &&x) {
-        if (s[1].B == 0) {
-            s[1] = std::move(x);
-            return;
-        }
-        if (x.dl < s[1].dl) {
-            if (s[1].B > x.B) s[0] = std::move(s[1]);
-            else s[2] = std::move(s[1]);
-            s[1] = std::move(x);
-        } else {
-            if (x.B > s[1].B) s[0] = std::move(x);
-            else s[2] = std::move(x);
-        }
-    }
-    bool next(double reduction, int &start, int32_t &target) const {
-        if (s[2].B == 0) {
-            int64_t nm = (int64_t)std::floor((double)s[1].B * reduction);
-            if (nm > s[1].B - 1) nm = s[1].B - 1;
-            if (nm < 1) return false;
-            start = 1;
-            target = (int32_t)(s[1].B - nm);
-            return true;
-        }
-        if (s[0].B - s[2].B <= 2) return false;
-        const int32_t up = s[0].B - s[1].B, low = s[1].B - s[2].B;
-        int32_t upper, lower;
-        if (up >= low) { start = 0; upper = s[0].B; lower = s[1].B; }
-        else { start = 1; upper = s[1].B; lower = s[2].B; }
-        int32_t t = upper - (int32_t)std::llround(0.618 * (double)(upper - lower));
-        if (t >= upper) t = upper - 1;
-        if (t <= lower) t = lower + 1;
-        target = t;
-        return true;
-    }
-};
-
 int read_assignment(sbp_model *m, std::vector<int32_t> &b) {
     b.resize((size_t)m->g->n);
     SBP_CUDA(cudaMemcpyAsync(b.data(), m->b, b.size() * 4, cudaMemcpyDeviceToHost, m->stream));
@@ -407,50 +407,97 @@ int read_dl(sbp_model *m, double &dl) {
     return SBP_OK;
 }
 
-int run_partition(sbp_model *m, int32_t *b_out, int32_t *B_out, double *dl_out, int64_t *n_sweeps) {
-    const sbp_params &p = m->p;
-    const int64_t n = m->g->n;
-    uint64_t sweep_id = 0, round_id = 0;
-    int64_t total = 0;
-    Bracket br;
+}  // namespace
+
+int PartitionRun::begin(sbp_model *model) {
+    m = model;
+    hist.assign((size_t)m->p.max_sweeps + 1, 0.0);
     State init;
     init.B = m->B;
+    init.id = ++last_id;
     SBP_TRY(read_dl(m, init.dl));
     SBP_TRY(read_assignment(m, init.b));
+    model_holds = init.id;
     br.insert(std::move(init));
+    return next_phase();
+}
+
+int PartitionRun::next_phase() {
     int start;
     int32_t target;
-    std::vector<double> hist((size_t)p.max_sweeps + 1);
-    while (br.next(p.reduction, start, target)) {
-        const State &from = br.s[start];
-        SBP_TRY(upload_assignment(m, from.B, from.b.data()));
-        int32_t Bm = m->B, rounds = 0;
-        SBP_TRY(sbp_merge_blocks(m, round_id, from.B - target, &Bm, &rounds));
-        round_id += (uint64_t)rounds;
-        const double t = br.s[2].B == 0 ? p.t_pre : p.t_post;
-        SBP_TRY(read_dl(m, hist[0]));
-        int k;
-        for (k = 1; k <= p.max_sweeps; ++k) {
-            sbp_sweep_stats st;
-            SBP_TRY(sbp_nodal_sweep(m, sweep_id++, 0, n, &st));
-            hist[(size_t)k] = st.dl_after;
-            if (k >= 3 && std::fabs(hist[(size_t)k - 3] - hist[(size_t)k]) < t * hist[(size_t)k]) break;
-        }
-        total += k > p.max_sweeps ? p.max_sweeps : k;
-        int32_t Bc = m->B;
-        SBP_TRY(sbp_compact(m, &Bc));
-        State x;
-        x.B = m->B;
-        SBP_TRY(read_dl(m, x.dl));
-        SBP_TRY(read_assignment(m, x.b));
-        br.insert(std::move(x));
+    if (!br.next(m->p.reduction, start, target)) {
+        done = true;
+        return SBP_OK;
     }
+    const State &from = br.s[start];
+    // the model already holds that state (labels, counts, DL) when it is the
+    // one the last phase ended in; uploading it again would rebuild the same
+    if (from.id != model_holds) SBP_TRY(upload_assignment(m, from.B, from.b.data()));
+    model_holds = 0;
+    int32_t Bm = m->B, rounds = 0;
+    SBP_TRY(sbp_merge_blocks(m, round_id, from.B - target, &Bm, &rounds));
+    round_id += (uint64_t)rounds;
+    t = br.s[2].B == 0 ? m->p.t_pre : m->p.t_post;
+    SBP_TRY(read_dl(m, hist[0]));
+    k = 0;
+    return SBP_OK;
+}
+
+bool PartitionRun::phase_over() const {
+    if (k >= m->p.max_sweeps) return true;
+    return k >= 3 && std::fabs(hist[(size_t)k - 3] - hist[(size_t)k]) < t * hist[(size_t)k];
+}
+
+int PartitionRun::sweep() {
+    sbp_sweep_stats st;
+    SBP_TRY(sbp_nodal_sweep(m, sweep_id++, 0, m->g->n, &st));
+    ++k;
+    hist[(size_t)k] = st.dl_after;
+    return SBP_OK;
+}
+
+int PartitionRun::after_sweeps(int k_done, double dl_last) {
+    sweep_id += (uint64_t)k_done;
+    k = k_done;
+    if (k > 0) hist[(size_t)k] = dl_last;
+    return SBP_OK;
+}
+
+int PartitionRun::end_phase() {
+    total += k;
+    int32_t Bc = m->B;
+    SBP_TRY(sbp_compact(m, &Bc));
+    State x;
+    x.B = m->B;
+    x.id = ++last_id;
+    SBP_TRY(read_dl(m, x.dl));
+    SBP_TRY(read_assignment(m, x.b));
+    model_holds = x.id;
+    br.insert(std::move(x));
+    return next_phase();
+}
+
+int PartitionRun::finish(int32_t *b_out, int32_t *B_out, double *dl_out, int64_t *n_sweeps) const {
     const State &best = br.s[1];
-    SBP_CUDA(cudaMemcpy(b_out, best.b.data(), (size_t)n * 4, is_device_ptr(b_out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    if (b_out)
+        SBP_CUDA(cudaMemcpy(b_out, best.b.data(), (size_t)m->g->n * 4,
+                            is_device_ptr(b_out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
     if (B_out) *B_out = best.B;
     if (dl_out) *dl_out = best.dl;
     if (n_sweeps) *n_sweeps = total;
     return SBP_OK;
+}
+
+namespace {
+
+int run_partition(sbp_model *m, int32_t *b_out, int32_t *B_out, double *dl_out, int64_t *n_sweeps) {
+    PartitionRun r;
+    SBP_TRY(r.begin(m));
+    while (!r.done) {
+        while (!r.phase_over()) SBP_TRY(r.sweep());
+        SBP_TRY(r.end_phase());
+    }
+    return r.finish(b_out, B_out, dl_out, n_sweeps);
 }
 
 }  // namespace

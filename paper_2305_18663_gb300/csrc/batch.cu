@@ -1,0 +1,746 @@
+// batch.cu -- many graphs' MCMC phases in one persistent launch.
+//
+// The batching form of the nodal sweep: thousands of small, uneven graphs
+// each need a few tens of sweeps per MCMC phase (Alg. 2) at a few hundred
+// blocks.  Launched one graph at a time, each sweep is a dozen small kernels
+// plus a host round trip for the convergence test.  Here one persistent
+// launch takes a table of jobs (one MCMC phase of one graph each, every graph
+// in its own dense model); a CTA pulls a job from a device queue, runs the
+// whole phase for it and pulls the next, largest jobs first.  Per sweep,
+// inside the CTA:
+//   1. proposals, one thread per vertex (the same proposal as the per-graph
+//      pass), movers (s != r) appended to the graph's mover list;
+//   2. evaluation, one warp per mover: the row is aggregated into
+//      direct-mapped per-warp counts in shared memory (B entries), then the
+//      same Delta DL, Hastings and test code as the per-graph pass;
+//   3. the apply step from the moved vertices' rows.  Each cell update is an
+//      atomic whose returned old count gives T[new] - T[old] (x ln x in
+//      128-bit fixed point), so sum M ln M is carried exactly from sweep to
+//      sweep without a pass over the B x B cells;
+//   4. prefix rows, degrees and DL (Eq. 2, the same integer L as a recount,
+//      hence the same bits), and the convergence test of Alg. 2 on the device.
+// The decisions are the exact ones (the precision form's band guarantees it),
+// the counts are integers and L is an exact integer, so a graph's phase ends
+// with the same assignment, M, DL and sweep count as the per-graph path.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "apply.cuh"
+#include "batch.h"
+#include "driver.h"
+#include "nodal_dev.cuh"
+
+namespace sbp {
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWarps = kBatchThreads / 32;
+
+// the blockmodel arrays the apply step writes (the decision pass sees them
+// read-only through DecideArgs)
+struct ModelOut {
+    int32_t *b, *M, *dout, *din, *dsum;
+    uint32_t *P, *Pc;
+    double *rcp;
+    float *rcp32;
+};
+
+struct BatchJob {
+    DecideArgs a;        // graph, model, seed, beta (trace off)
+    ModelOut w;
+    uint64_t sweep0;     // sweep id of the phase's first sweep
+    double t;            // convergence threshold of the phase
+    int max_sweeps;
+    int dl32;
+    double *hist;        // [max_sweeps + 1]; hist[0] = DL after the merge (set by the host)
+    int *k_res;          // sweeps done (host-mapped)
+    double *dl_res;      // DL after the last sweep (host-mapped)
+    double *dl;          // the model's dl[0] (after) and dl[1] (before the last sweep)
+};
+
+// one cell update of the incremental apply with the exact change of sum x ln x
+__device__ __forceinline__ void cell_add(int32_t *__restrict__ M, const __int128 *__restrict__ T, bool valid, int key,
+                                         int d, __int128 &acc) {
+    if (!valid) return;
+    const int old = atomicAdd(&M[key], d);
+    acc += T[old + d] - T[old];
+}
+
+// (labels and M through plain loads and atomics: this kernel writes all of
+// them between sweeps, so no read-only-cache path may be used)
+__device__ void apply_rows(const GraphDev &g, const int32_t *bold, const int32_t *bnew, int32_t *M, int B,
+                           const __int128 *__restrict__ T, int v, __int128 &acc) {
+    const int lane = threadIdx.x & 31;
+    const int r = bold[v], s = bnew[v];
+    const int o0 = g.op[v], o1 = g.op[v + 1], i0 = g.ip[v], i1 = g.ip[v + 1];
+    for (int e0 = o0; e0 < o1; e0 += 32) {
+        const int e = e0 + lane;
+        const bool ok = e < o1;
+        const int w = ok ? g.oc[e] : 0;
+        const int tw = ok ? bold[w] : 0, uw = ok ? bnew[w] : 0;
+        cell_add(M, T, ok, r * B + tw, -1, acc);
+        cell_add(M, T, ok, s * B + uw, 1, acc);
+    }
+    for (int e0 = i0; e0 < i1; e0 += 32) {
+        const int e = e0 + lane;
+        bool ok = e < i1;
+        const int w = ok ? g.ic[e] : 0;
+        const int t = ok ? bold[w] : 0;
+        ok = ok && bnew[w] == t;
+        cell_add(M, T, ok, t * B + r, -1, acc);
+        cell_add(M, T, ok, t * B + s, 1, acc);
+    }
+}
+
+// the CTA's sum of one int128 per thread (every thread gets it)
+__device__ __int128 cta_sum_128(__int128 v, __int128 *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum_128(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    __int128 s = 0;
+    for (int q = 0; q < kBatchWarps; ++q) s += sh[q];
+    __syncthreads();
+    return s;
+}
+
+template <bool DL32>
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob *__restrict__ jobs, int njobs,
+                                                                  unsigned *__restrict__ queue, int warp_words) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ DecideArgs sa;
+    __shared__ ModelOut sw;
+    __shared__ __int128 red[kBatchWarps];
+    __shared__ unsigned s_job, s_nmov;
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    unsigned *cnt = reinterpret_cast<unsigned *>(bsm) + (size_t)wid * warp_words;
+    for (;;) {
+        if (tid == 0) s_job = atomicAdd(queue, 1u);
+        __syncthreads();
+        const unsigned j = s_job;
+        if (j >= (unsigned)njobs) return;
+        if (tid == 0) {
+            sa = jobs[j].a;
+            sw = jobs[j].w;
+        }
+        __syncthreads();
+        const BatchJob &J = jobs[j];
+        const GraphDev &g = sa.g;
+        const ModelDev &md = sa.md;
+        const int B = md.B, n = g.n;
+        int *list = reinterpret_cast<int *>(cnt + B);
+        for (int i = lane; i < B; i += 32) cnt[i] = 0u;
+        // sum over the cells of T[M] at the phase start (exact)
+        __int128 c = 0;
+        for (int64_t i = tid; i < (int64_t)B * B; i += kBatchThreads) c += md.T[md.M[i]];
+        __int128 C = cta_sum_128(c, red);
+        double prev = J.hist[0];
+        int k = 0;
+        for (;;) {
+            ++k;
+            const uint64_t sweep_id = J.sweep0 + (uint64_t)(k - 1);
+            if (tid == 0) s_nmov = 0;
+            __syncthreads();
+            // 1. proposals
+            for (int base = 0; base < n; base += kBatchThreads) {
+                const int v = base + tid;
+                bool mv = false;
+                Proposal p;
+                if (v < n) {
+                    p = propose_vertex(g, md, sa.seed, sweep_id, v);
+                    mv = p.k > 0 && p.s != p.r;
+                }
+                const unsigned msk = __ballot_sync(0xffffffffu, mv);
+                unsigned pos0 = 0;
+                if (msk) {
+                    if (lane == __ffs(msk) - 1) pos0 = atomicAdd(&s_nmov, (unsigned)__popc(msk));
+                    pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(msk) - 1);
+                }
+                if (mv) {
+                    Mover m;
+                    m.v = v;
+                    m.s = p.s;
+                    m.w2 = p.w2;
+                    sa.movers[pos0 + __popc(msk & ((1u << lane) - 1u))] = m;
+                }
+            }
+            __syncthreads();
+            // 2. evaluation, one warp per mover
+            const int nmov = (int)s_nmov;
+            Counts cts;
+            for (int q = wid; q < nmov; q += kBatchWarps) {
+                const Mover mv = sa.movers[q];
+                const int v = mv.v;
+                const int o0 = g.op[v], kout = g.op[v + 1] - o0;
+                const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
+                const int kk = kout + kin;
+                int nl = 0, self = 0;
+                for (int base = 0; base < kk; base += 32) {
+                    const int idx = base + lane;
+                    const bool valid = idx < kk, is_out = idx < kout;
+                    const int nb = valid ? (is_out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
+                    const bool is_self = valid && nb == v;
+                    self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
+                    bool fresh = false;
+                    int t = 0;
+                    if (valid && !is_self) {
+                        t = md.b[nb];
+                        fresh = atomicAdd(&cnt[t], is_out ? 1u : 0x10000u) == 0u;
+                    }
+                    const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+                    if (fresh) list[nl + __popc(fm & ((1u << lane) - 1u))] = t;
+                    nl += __popc(fm);
+                }
+                __syncwarp();
+                VertexCtx x;
+                x.v = v;
+                x.r = md.b[v];
+                x.s = mv.s;
+                x.Kout = kout;
+                x.Kin = kin;
+                x.self = self;
+                x.k = kk;
+                evaluate_warp<DL32>(sa, md, x, mv.w2, [&](auto &&f) {
+                    for (int e = lane; e < nl; e += 32) {
+                        const int t = list[e];
+                        const unsigned cc = cnt[t];
+                        f(t, (int)(cc & 0xffffu), (int)(cc >> 16));
+                    }
+                }, cts);
+                __syncwarp();
+                for (int e = lane; e < nl; e += 32) cnt[list[e]] = 0u;
+                __syncwarp();
+            }
+            __syncthreads();
+            // 3. apply: warp per 32 vertex ids, rows of the moved ones
+            __int128 dc = 0;
+            for (int base = wid * 32; base < n; base += kBatchThreads) {
+                const int vv = base + lane;
+                const bool moved = vv < n && md.bnew[vv] != md.b[vv];
+                unsigned mm = __ballot_sync(0xffffffffu, moved);
+                while (mm) {
+                    const int qq = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    apply_rows(g, md.b, md.bnew, sw.M, B, md.T, base + qq, dc);
+                }
+            }
+            C += cta_sum_128(dc, red);  // includes the barrier before the label copy
+            for (int v = tid; v < n; v += kBatchThreads) sw.b[v] = md.bnew[v];
+            __syncthreads();
+            // 4. prefix rows, degrees, DL, the stopping rule
+            __int128 dd = 0;
+            for (int u = wid; u < B; u += kBatchWarps) {
+                prefix_block(sw.M, B, u, sw.P, sw.dout, sw.din, sw.rcp, sw.rcp32, sw.dsum, sw.Pc, md.pstep);
+                if (lane == 0) {
+                    dd += md.T[sw.dout[u]];
+                    dd += md.T[sw.din[u]];
+                }
+            }
+            const __int128 D = cta_sum_128(dd, red);
+            if (tid == 0) {
+                const double dlk = dl_eq2(g.m, g.n, B, fix_to_double(C - D));
+                J.hist[k] = dlk;
+                const bool stop = k >= J.max_sweeps ||
+                                  (k >= 3 && fabs(J.hist[k - 3] - dlk) < J.t * dlk);
+                s_stop = stop ? 1 : 0;
+                J.dl[1] = prev;
+                J.dl[0] = dlk;
+                prev = dlk;
+                if (stop) {
+                    *J.k_res = k;
+                    *J.dl_res = dlk;
+                }
+            }
+            __syncthreads();
+            if (s_stop) break;
+        }
+        __syncthreads();
+    }
+}
+
+int sm_count_b() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace
+
+bool batch_eligible(const sbp_model *m, int max_B, int64_t max_n) {
+    return m->dense && m->B <= max_B && m->B <= kBatchMaxB && m->g->n <= max_n && m->g->m < (int64_t(1) << 22) &&
+           m->g->max_deg < 65536 && m->g->n < (int64_t(1) << 30);
+}
+
+// Enqueues one MCMC phase for each model on stream st (all eligible and
+// idle; hist0[i] = DL after the merge), starting at sweep id sweep0[i] with
+// threshold t[i].  When the stream reaches the end of the launch, k_res[i]
+// holds the sweeps done and dl_res[i] the last DL (device-visible pointers,
+// typically into host-mapped memory), and each model is in the state the
+// per-graph sweeps would leave.  The launch's scratch is freed in stream
+// order.
+int batch_enqueue(const std::vector<sbp_model *> &models, const std::vector<uint64_t> &sweep0,
+                  const std::vector<double> &t, const std::vector<double> &hist0, const std::vector<int *> &k_res,
+                  const std::vector<double *> &dl_res, const BatchTuning &tune, cudaStream_t st) {
+    const int nj = (int)models.size();
+    if (nj == 0) return SBP_OK;
+    int maxB = 1, max_sweeps = 1, dl32 = models[0]->p.dl_fp32;
+    for (const sbp_model *m : models) {
+        maxB = std::max(maxB, (int)m->B);
+        max_sweeps = std::max(max_sweeps, m->p.max_sweeps);
+        if (m->p.dl_fp32 != dl32) return fail(SBP_EINVAL, "batch: all models must share dl_fp32");
+        if (!batch_eligible(m, kBatchMaxB, INT32_MAX)) return fail(SBP_EINVAL, "batch: model not eligible");
+    }
+    // device scratch: jobs, hist rows, queue
+    const size_t hist_stride = (size_t)max_sweeps + 1;
+    const size_t bytes = (size_t)nj * sizeof(BatchJob) + (size_t)nj * hist_stride * 8 + 16;
+    unsigned char *buf = nullptr;
+    SBP_CUDA(cudaMallocAsync(&buf, bytes, st));
+    BatchJob *d_jobs = reinterpret_cast<BatchJob *>(buf);
+    double *d_hist = reinterpret_cast<double *>(buf + (size_t)nj * sizeof(BatchJob));
+    unsigned *d_queue = reinterpret_cast<unsigned *>(d_hist + (size_t)nj * hist_stride);
+    // largest graphs first
+    std::vector<int> order((size_t)nj);
+    for (int i = 0; i < nj; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return models[(size_t)x]->g->m + models[(size_t)x]->g->n > models[(size_t)y]->g->m + models[(size_t)y]->g->n;
+    });
+    std::vector<BatchJob> jobs((size_t)nj);
+    std::vector<double> h0((size_t)nj * hist_stride, 0.0);
+    for (int q = 0; q < nj; ++q) {
+        const int i = order[(size_t)q];
+        sbp_model *m = models[(size_t)i];
+        if (!m->movers) {
+            // on this stream, which runs the kernel that first uses them
+            if (model_alloc(&m->movers, (size_t)(m->g->n > 0 ? m->g->n : 1) * sizeof(Mover), st) != cudaSuccess ||
+                model_alloc((void **)&m->mcount, 4 * sizeof(unsigned), st) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFreeAsync(buf, st);
+                return fail(SBP_ENOMEM, "device allocation failed for the mover lists");
+            }
+        }
+        BatchJob &J = jobs[(size_t)q];
+        J.a = DecideArgs();
+        J.a.g = m->g->dev();
+        J.a.md = model_dev(m);
+        J.a.v_begin = 0;
+        J.a.v_end = m->g->n;
+        J.a.movers = static_cast<Mover *>(m->movers);
+        J.a.mcount = m->mcount;
+        J.a.seed = m->p.seed;
+        J.a.sweep_id = sweep0[(size_t)i];
+        J.a.beta = m->p.beta;
+        J.a.beta32 = (float)m->p.beta;
+        J.a.trace_on = 0;
+        J.a.tr = sbp_vertex_trace{nullptr, nullptr, nullptr, nullptr};
+        J.w.b = m->b;
+        J.w.M = m->M;
+        J.w.dout = m->dout;
+        J.w.din = m->din;
+        J.w.dsum = m->dsum;
+        J.w.P = m->P;
+        J.w.Pc = m->Pc;
+        J.w.rcp = m->rcp;
+        J.w.rcp32 = m->rcp32;
+        J.sweep0 = sweep0[(size_t)i];
+        J.t = t[(size_t)i];
+        J.max_sweeps = m->p.max_sweeps;
+        J.dl32 = dl32;
+        J.hist = d_hist + (size_t)q * hist_stride;
+        J.k_res = k_res[(size_t)i];
+        J.dl_res = dl_res[(size_t)i];
+        J.dl = m->dl;
+        h0[(size_t)q * hist_stride] = hist0[(size_t)i];
+    }
+    // the host copies are pageable: these copies complete before returning
+    SBP_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)nj * sizeof(BatchJob), cudaMemcpyHostToDevice, st));
+    SBP_CUDA(cudaMemcpyAsync(d_hist, h0.data(), h0.size() * 8, cudaMemcpyHostToDevice, st));
+    SBP_CUDA(cudaMemsetAsync(d_queue, 0, 4, st));
+    // per warp: B counts and a list of up to B blocks
+    const int warp_words = 2 * maxB + 4;
+    const size_t smem = (size_t)kBatchWarps * warp_words * 4;
+    const int per_sm = tune.ctas_per_sm > 0 ? tune.ctas_per_sm : 2;
+    const int grid = std::min(nj, sm_count_b() * per_sm);
+    if (dl32) {
+        SBP_TRY(ensure_dyn_smem((const void *)k_batch_mcmc<true>, smem));
+        k_batch_mcmc<true><<<grid, kBatchThreads, smem, st>>>(d_jobs, nj, d_queue, warp_words);
+    } else {
+        SBP_TRY(ensure_dyn_smem((const void *)k_batch_mcmc<false>, smem));
+        k_batch_mcmc<false><<<grid, kBatchThreads, smem, st>>>(d_jobs, nj, d_queue, warp_words);
+    }
+    SBP_LAUNCHED();
+    SBP_CUDA(cudaFreeAsync(buf, st));
+    return SBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The batch driver.  Every graph runs its own golden-ratio search
+// (PartitionRun).  Two kinds of work overlap:
+//   - per-graph work on host worker threads: model set-up, merge phases,
+//     compaction, and the MCMC phases the persistent kernel does not take (B
+//     above the batch limit, or sparse rows).  Workers take graphs from a
+//     shared queue, largest first; a graph's work goes to its model's stream;
+//   - the persistent launch, driven by a launcher thread: it takes every graph
+//     whose next MCMC phase is batchable once enough are ready (a GPU's worth
+//     of CTAs) or once nothing else can make progress, runs their phases,
+//     and hands the graphs back to the workers.
+// Graphs are admitted in input order while their estimated device memory
+// fits the budget, and their models are freed as soon as they finish, so a
+// later graph takes the place of a finished one.
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// device bytes of a graph's model at its largest (sparse rows at B = N)
+size_t model_bytes(const sbp_graph *g, int dense_max_B) {
+    const size_t n = (size_t)g->n, m = (size_t)std::max<int64_t>(g->m, 1);
+    return 144 * m + 128 * n + 12 * (size_t)dense_max_B * (size_t)dense_max_B + (1u << 20);
+}
+
+struct Item {
+    const sbp_graph *g = nullptr;
+    sbp_model *m = nullptr;
+    PartitionRun run;
+    bool started = false, after_batch = false, finished = false;
+    size_t bytes = 0;
+    double t_admit = 0, t_done = 0;
+};
+
+}  // namespace
+
+int partition_batch(const sbp_graph *const *graphs, int count, const sbp_params &p, const BatchOptions &opt,
+                    int32_t *const *b_out, sbp_batch_result *res, sbp_batch_stats *stats) {
+    const int W = std::max(1, opt.workers);
+    const int nstreams = W;
+    std::vector<cudaStream_t> streams((size_t)nstreams, nullptr);
+    auto destroy_streams = [&]() {
+        for (auto &s : streams)
+            if (s) cudaStreamDestroy(s);
+    };
+    for (auto &s : streams)
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            destroy_streams();
+            return cuda_fail(cudaGetLastError(), "sbp_partition_batch: cudaStreamCreate");
+        }
+    size_t free_b = 0, total_b = 0;
+    SBP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = (size_t)((double)free_b * opt.mem_fraction);
+    sbp_params prm = p;
+    prm.dense_max_B = opt.tune.dense_max_B;
+    int dev = 0;
+    SBP_CUDA(cudaGetDevice(&dev));
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t full_batch = (size_t)sms * (size_t)std::max(1, opt.tune.ctas_per_sm);
+
+    std::vector<Item> items((size_t)count);
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<int> cpu_q;   // graphs needing per-graph work
+    std::vector<int> ready;   // graphs waiting for a batched MCMC phase
+    int next = 0, done = 0, busy = 0, in_batch = 0;
+    size_t used = 0;
+    int err = SBP_OK;
+    std::string err_msg;
+    sbp_batch_stats st{};
+    std::atomic<int64_t> per_graph_phases{0};
+    double busy_s = 0.0;
+    const double t_start = now_s();
+
+    // under mu: admit graphs while their memory fits (always one when idle)
+    auto admit = [&]() {
+        while (next < count) {
+            Item &it = items[(size_t)next];
+            it.g = graphs[next];
+            it.bytes = model_bytes(it.g, prm.dense_max_B);
+            const bool idle = (done == next);
+            if (!idle && used + it.bytes > budget) break;
+            used += it.bytes;
+            it.t_admit = now_s() - t_start;
+            cpu_q.push_back(next);
+            ++next;
+        }
+    };
+    auto fail_all = [&](int rc, const std::string &msg) {
+        if (err == SBP_OK) {
+            err = rc;
+            err_msg = msg;
+        }
+        cv.notify_all();
+    };
+    // one graph's per-graph work, until it waits for a batched phase or ends
+    auto work = [&](int idx) -> int {
+        Item &it = items[(size_t)idx];
+        int r = SBP_OK;
+        double tm = now_s();
+        if (!it.started) {
+            std::vector<int32_t> ident((size_t)it.g->n);
+            std::iota(ident.begin(), ident.end(), 0);
+            r = sbp_build_blockmodel(it.g, (int32_t)it.g->n, ident.data(), &prm, streams[(size_t)idx % nstreams], &it.m);
+            if (r == SBP_OK) r = it.run.begin(it.m);
+            it.started = true;
+        } else if (it.after_batch) {
+            r = it.run.end_phase();
+            it.after_batch = false;
+        }
+        double t_merge = now_s() - tm, t_sweeps = 0.0;
+        while (r == SBP_OK && !it.run.done && !batch_eligible(it.m, opt.tune.max_B, opt.tune.max_n)) {
+            tm = now_s();
+            while (r == SBP_OK && !it.run.phase_over()) r = it.run.sweep();
+            const double t1 = now_s();
+            t_sweeps += t1 - tm;
+            if (r == SBP_OK) r = it.run.end_phase();
+            t_merge += now_s() - t1;
+            per_graph_phases.fetch_add(1, std::memory_order_relaxed);
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            st.s_merge += t_merge;
+            st.s_sweeps += t_sweeps;
+        }
+        if (r == SBP_OK && it.run.done) {
+            sbp_batch_result &o = res[idx];
+            r = it.run.finish(b_out ? b_out[idx] : nullptr, &o.B, &o.dl, &o.n_sweeps);
+            it.t_done = now_s() - t_start;
+            o.t_admit = it.t_admit;
+            o.t_done = it.t_done;
+            sbp_free_model(it.m);
+            it.m = nullptr;
+            it.finished = true;
+        }
+        return r;
+    };
+    auto worker = [&]() {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&]() { return err != SBP_OK || done == count || !cpu_q.empty(); });
+            if (err != SBP_OK || done == count) return;
+            // largest graph first
+            size_t pick = 0;
+            for (size_t q = 1; q < cpu_q.size(); ++q)
+                if (items[(size_t)cpu_q[q]].g->m > items[(size_t)cpu_q[pick]].g->m) pick = q;
+            const int idx = cpu_q[pick];
+            cpu_q.erase(cpu_q.begin() + (long)pick);
+            ++busy;
+            lk.unlock();
+            const double t0 = now_s();
+            const int r = work(idx);
+            std::string msg;
+            if (r != SBP_OK) {
+                char buf[1024];
+                sbp_last_error(buf, sizeof buf);
+                msg = "graph " + std::to_string(idx) + ": " + buf;
+            }
+            lk.lock();
+            busy_s += now_s() - t0;
+            --busy;
+            if (r != SBP_OK) {
+                fail_all(r, msg);
+                return;
+            }
+            Item &it = items[(size_t)idx];
+            if (it.finished) {
+                ++done;
+                used -= it.bytes;
+                admit();
+            } else {
+                ready.push_back(idx);
+            }
+            cv.notify_all();
+        }
+    };
+
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        admit();
+    }
+    std::vector<std::thread> th;
+    for (int w = 0; w < W; ++w) th.emplace_back(worker);
+    // the launcher (this thread): persistent launches in flight on their own
+    // streams, results in host-mapped memory, completion by event
+    struct Launch {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        std::vector<int> take;
+        double t0 = 0;
+    };
+    const int kMaxInflight = 4;
+    std::vector<Launch> pool((size_t)kMaxInflight);
+    std::vector<int> free_slots;
+    for (int q = 0; q < kMaxInflight; ++q) {
+        free_slots.push_back(q);
+        if (cudaStreamCreateWithFlags(&pool[(size_t)q].st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pool[(size_t)q].ev, cudaEventDisableTiming) != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            fail_all(cuda_fail(cudaGetLastError(), "sbp_partition_batch: stream or event"), "stream or event creation");
+        }
+    }
+    int *h_k = nullptr;
+    double *h_dl = nullptr;
+    int *d_k = nullptr;
+    double *d_dl = nullptr;
+    const size_t cnt1 = (size_t)std::max(count, 1);
+    if (cudaHostAlloc((void **)&h_k, cnt1 * 4, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc((void **)&h_dl, cnt1 * 8, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&d_k, h_k, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&d_dl, h_dl, 0) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        fail_all(cuda_fail(cudaGetLastError(), "sbp_partition_batch: mapped memory"), "mapped host memory");
+    }
+    std::vector<int> inflight;
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait_for(lk, std::chrono::microseconds(500), [&]() {
+                return err != SBP_OK || done == count || ready.size() >= full_batch ||
+                       (!ready.empty() && cpu_q.empty() && busy < W && !free_slots.empty());
+            });
+            // completed launches hand their graphs back to the workers
+            for (size_t q = 0; q < inflight.size();) {
+                Launch &L = pool[(size_t)inflight[q]];
+                const cudaError_t e = cudaEventQuery(L.ev);
+                if (e == cudaErrorNotReady) {
+                    ++q;
+                    continue;
+                }
+                if (e != cudaSuccess) {
+                    fail_all(cuda_fail(e, "persistent launch"), std::string("batched phase: ") + cudaGetErrorString(e));
+                    break;
+                }
+                st.s_batched += now_s() - L.t0;
+                for (int idx : L.take) {
+                    Item &it = items[(size_t)idx];
+                    it.run.after_sweeps(h_k[idx], h_dl[idx]);
+                    it.after_batch = true;
+                    cpu_q.push_back(idx);
+                }
+                L.take.clear();
+                free_slots.push_back(inflight[q]);
+                inflight.erase(inflight.begin() + (long)q);
+                cv.notify_all();
+            }
+            if (err != SBP_OK) break;
+            if (done == count && inflight.empty()) break;
+            // a new launch once a GPU's worth is ready, or when the workers
+            // have nothing else to do
+            const bool starving = cpu_q.empty() && busy < W;
+            if (ready.empty() || free_slots.empty() || (ready.size() < full_batch && !starving)) continue;
+            const int slot = free_slots.back();
+            free_slots.pop_back();
+            Launch &L = pool[(size_t)slot];
+            L.take.swap(ready);
+            ready.clear();
+            inflight.push_back(slot);
+            std::vector<sbp_model *> ms;
+            std::vector<uint64_t> s0;
+            std::vector<double> tt, h0;
+            std::vector<int *> kr;
+            std::vector<double *> dr;
+            for (int idx : L.take) {
+                Item &it = items[(size_t)idx];
+                ms.push_back(it.m);
+                s0.push_back(it.run.sweep_id);
+                tt.push_back(it.run.t);
+                h0.push_back(it.run.hist[0]);
+                kr.push_back(d_k + idx);
+                dr.push_back(d_dl + idx);
+            }
+            lk.unlock();
+            L.t0 = now_s();
+            int r = batch_enqueue(ms, s0, tt, h0, kr, dr, opt.tune, L.st);
+            if (r == SBP_OK && cudaEventRecord(L.ev, L.st) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+            std::string msg;
+            if (r != SBP_OK) {
+                char buf[1024];
+                sbp_last_error(buf, sizeof buf);
+                msg = std::string("batched phase: ") + buf;
+            }
+            lk.lock();
+            ++st.rounds;
+            st.phases_batched += (int64_t)L.take.size();
+            if (r != SBP_OK) {
+                fail_all(r, msg);
+                break;
+            }
+        }
+    }
+    for (int q : inflight) cudaEventSynchronize(pool[(size_t)q].ev);
+    for (Launch &L : pool) {
+        if (L.ev) cudaEventDestroy(L.ev);
+        if (L.st) cudaStreamDestroy(L.st);
+    }
+    if (h_k) cudaFreeHost(h_k);
+    if (h_dl) cudaFreeHost(h_dl);
+    cv.notify_all();
+    for (auto &t : th) t.join();
+    for (Item &it : items)
+        if (it.m) sbp_free_model(it.m);
+    destroy_streams();
+    if (err != SBP_OK) return fail(err, err_msg);
+    st.s_per_graph = busy_s;
+    st.phases_per_graph = per_graph_phases.load();
+    if (stats) *stats = st;
+    return SBP_OK;
+}
+
+}  // namespace sbp
+
+extern "C" int sbp_default_batch_options(sbp_batch_options *o) {
+    if (!o) return sbp::fail(SBP_EINVAL, "sbp_default_batch_options: NULL");
+    o->workers = 16;
+    o->max_B = 512;
+    o->dense_max_B = 4096;
+    o->ctas_per_sm = 2;
+    o->max_n = 4096;
+    o->reserved = 0;
+    o->mem_fraction = 0.5;
+    return SBP_OK;
+}
+
+extern "C" int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
+                                   const sbp_batch_options *o, int32_t *const *b_out, sbp_batch_result *res,
+                                   sbp_batch_stats *stats) {
+    using namespace sbp;
+    if (count < 0 || (count > 0 && (!graphs || !res))) return fail(SBP_EINVAL, "sbp_partition_batch: NULL argument");
+    for (int i = 0; i < count; ++i)
+        if (!graphs[i]) return fail(SBP_EINVAL, "sbp_partition_batch: NULL graph " + std::to_string(i));
+    sbp_params prm;
+    if (p) prm = *p;
+    else sbp_default_params(&prm);
+    sbp_batch_options bo;
+    if (o) bo = *o;
+    else sbp_default_batch_options(&bo);
+    if (bo.workers < 1 || bo.workers > 256) return fail(SBP_EINVAL, "sbp_partition_batch: workers must be in [1, 256]");
+    if (bo.max_B < 1 || bo.max_B > kBatchMaxB)
+        return fail(SBP_EINVAL, "sbp_partition_batch: max_B must be in [1, " + std::to_string(kBatchMaxB) + "]");
+    if (bo.dense_max_B < bo.max_B || bo.dense_max_B > 16384)
+        return fail(SBP_EINVAL, "sbp_partition_batch: dense_max_B must be in [max_B, 16384]");
+    if (bo.ctas_per_sm < 1 || bo.ctas_per_sm > 8) return fail(SBP_EINVAL, "sbp_partition_batch: ctas_per_sm must be in [1, 8]");
+    if (bo.max_n < 0) return fail(SBP_EINVAL, "sbp_partition_batch: max_n must be >= 0");
+    if (!(bo.mem_fraction > 0.0 && bo.mem_fraction <= 0.95))
+        return fail(SBP_EINVAL, "sbp_partition_batch: mem_fraction must be in (0, 0.95]");
+    BatchOptions opt;
+    opt.workers = bo.workers;
+    opt.mem_fraction = bo.mem_fraction;
+    opt.tune.max_B = bo.max_B;
+    opt.tune.dense_max_B = bo.dense_max_B;
+    opt.tune.ctas_per_sm = bo.ctas_per_sm;
+    opt.tune.max_n = bo.max_n;
+    return partition_batch(graphs, count, prm, opt, b_out, res, stats);
+}

@@ -12,7 +12,7 @@
 // is reduced in a fixed order so it is reproducible bit for bit.
 #include <cmath>
 
-#include "common.cuh"
+#include "apply.cuh"
 
 namespace sbp {
 namespace {
@@ -69,16 +69,6 @@ __global__ void __launch_bounds__(kThreads) k_hist_dense(GraphDev g, const int32
         if (diag[i]) atomicAdd(&M[(size_t)i * B + i], diag[i]);
 }
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += x;
-    }
-    return v;
-}
-
 // one warp per block u
 __global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__restrict__ M, int B,
                                                            uint32_t *__restrict__ P, int32_t *__restrict__ dout,
@@ -86,49 +76,8 @@ __global__ void __launch_bounds__(kThreads) k_prefix_dense(const int32_t *__rest
                                                            float *__restrict__ rcp32, int32_t *__restrict__ dsum,
                                                            uint32_t *__restrict__ Pc, int pstep) {
     const int u = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
     if (u >= B) return;
-    uint32_t *row = P + (size_t)u * 2 * B;
-    uint32_t carry = 0;
-    for (int c0 = 0; c0 < B; c0 += 32) {
-        const int c = c0 + lane;
-        uint32_t v = c < B ? (uint32_t)M[(size_t)u * B + c] : 0u;
-        v = warp_incl_scan(v) + carry;
-        if (c < B) row[c] = v;
-        carry = __shfl_sync(0xffffffffu, v, 31);
-    }
-    const uint32_t du_out = carry;
-    for (int c0 = 0; c0 < B; c0 += 32) {
-        const int c = c0 + lane;
-        uint32_t v = c < B ? (uint32_t)M[(size_t)c * B + u] : 0u;
-        v = warp_incl_scan(v) + carry;
-        if (c < B) row[B + c] = v;
-        carry = __shfl_sync(0xffffffffu, v, 31);
-    }
-    __syncwarp();
-    const int pi = (lane + 1) * pstep - 1 < 2 * B - 1 ? (lane + 1) * pstep - 1 : 2 * B - 1;
-    Pc[(size_t)u * 32 + lane] = row[pi];
-    if (lane == 0) {
-        const uint32_t du_in = carry - du_out;
-        dout[u] = (int32_t)du_out;
-        din[u] = (int32_t)du_in;
-        rcp[u] = 1.0 / ((double)du_out + (double)du_in + (double)B);
-        rcp32[u] = 1.0f / ((float)du_out + (float)du_in + (float)B);
-        dsum[u] = (int32_t)(du_out + du_in);
-    }
-}
-
-struct DlPartial {
-    __int128 fix;  // sum of x ln x * 2^64 over counts inside the table
-    double fb;     // FP64 sum over counts beyond it
-    double pad;
-};
-
-__device__ __forceinline__ void add_xlogx(const __int128 *__restrict__ T, int64_t XT, int64_t x, int sign, __int128 &fix,
-                                          double &fb) {
-    if (x < 2) return;
-    if (x < XT) fix += sign > 0 ? T[x] : -T[x];
-    else fb += sign * ((double)x * log((double)x));
+    prefix_block(M, B, u, P, dout, din, rcp, rcp32, dsum, Pc, pstep);
 }
 
 // Eq. 1 split form: sum over M of x ln x minus the degree terms, one
@@ -192,13 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_dl_final(const DlPartial *__restri
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double L = fix_to_double(sfix[0]) + sfb[0];
-        double model = 0.0;
-        if (E > 0) {
-            const double x = (double)B * (double)B / (double)E;
-            model = (double)E * ((1.0 + x) * log1p(x) - x * log(x));
-        }
-        dl[0] = model + (double)N * log((double)B) - L;
+        dl[0] = dl_eq2(E, N, B, fix_to_double(sfix[0]) + sfb[0]);
     }
 }
 
@@ -217,65 +160,6 @@ __global__ void k_zero_if(int32_t *__restrict__ M, int64_t n, const int32_t *__r
 // through the out-row of its moved source, or through the in-row of its
 // moved target when the source stayed.  Lanes take the edges of one row,
 // four loads in flight per lane.
-// (a dense M has B <= 16384, so a cell index fits 32 bits)
-__device__ __forceinline__ void delta_add(int32_t *__restrict__ M, bool valid, int key, int d) {
-    if (valid) atomicAdd(&M[key], d);
-}
-
-// out-row [a, z) of a vertex moved r -> s
-__device__ __forceinline__ void delta_out_row(const int32_t *__restrict__ oc, int a, int z, int r, int s,
-                                              const int32_t *__restrict__ bnew, const int32_t *__restrict__ bold,
-                                              int32_t *__restrict__ M, int B) {
-    const int lane = threadIdx.x & 31;
-    for (int e0 = a; e0 < z; e0 += 128) {
-        int w[4], t[4], u[4];
-        bool ok[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int e = e0 + 32 * j + lane;
-            ok[j] = e < z;
-            w[j] = ok[j] ? oc[e] : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            t[j] = ok[j] ? bold[w[j]] : 0;
-            u[j] = ok[j] ? bnew[w[j]] : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            delta_add(M, ok[j], r * B + t[j], -1);
-            delta_add(M, ok[j], s * B + u[j], 1);
-        }
-    }
-}
-
-// in-row [a, z) of a vertex moved r -> s; only sources that stayed
-__device__ __forceinline__ void delta_in_row(const int32_t *__restrict__ ic, int a, int z, int r, int s,
-                                             const int32_t *__restrict__ bnew, const int32_t *__restrict__ bold,
-                                             int32_t *__restrict__ M, int B) {
-    const int lane = threadIdx.x & 31;
-    for (int e0 = a; e0 < z; e0 += 128) {
-        int w[4], t[4];
-        bool ok[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int e = e0 + 32 * j + lane;
-            ok[j] = e < z;
-            w[j] = ok[j] ? ic[e] : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            t[j] = ok[j] ? bold[w[j]] : 0;
-            ok[j] = ok[j] && bnew[w[j]] == t[j];
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            delta_add(M, ok[j], t[j] * B + r, -1);
-            delta_add(M, ok[j], t[j] * B + s, 1);
-        }
-    }
-}
-
 // Warps [0, n_big) take one vertex each of the largest-degree group (in
 // descending degree, so the longest rows start first); the remaining warps
 // take 32 consecutive vertex ids each and skip the ones of that group.
@@ -348,40 +232,33 @@ int ensure_capacity(sbp_model *m, int32_t B) {
     if (!m->dense) SBP_TRY(ensure_sparse_capacity(m, B));
     const bool need_dense = m->dense && B > m->Bdense;
     if (B <= m->Bcap && !need_dense) return SBP_OK;
+    cudaStream_t st = m->stream;
+    auto alloc = [&](auto **p, size_t bytes) { return model_alloc((void **)p, bytes, st) == cudaSuccess; };
     if (need_dense) {
-        cudaFree(m->M);
-        cudaFree(m->P);
-        cudaFree(m->Pc);
+        model_free(m->M, st);
+        model_free(m->P, st);
+        model_free(m->Pc, st);
         m->M = nullptr; m->P = nullptr; m->Pc = nullptr;
         m->Bdense = 0;
         const size_t BB = (size_t)B * B;
-        if (cudaMalloc(&m->M, BB * 4) != cudaSuccess || cudaMalloc(&m->P, BB * 8) != cudaSuccess ||
-            cudaMalloc(&m->Pc, (size_t)B * 32 * 4) != cudaSuccess) {
+        if (!alloc(&m->M, BB * 4) || !alloc(&m->P, BB * 8) || !alloc(&m->Pc, (size_t)B * 32 * 4)) {
             cudaGetLastError();
-            return fail(SBP_ENOMEM, "cudaMalloc failed for a dense blockmodel of B = " + std::to_string(B));
+            return fail(SBP_ENOMEM, "device allocation failed for a dense blockmodel of B = " + std::to_string(B));
         }
         m->Bdense = B;
     }
     if (B > m->Bcap) {
-        cudaFree(m->dout);
-        cudaFree(m->din);
-        cudaFree(m->rcp);
-        cudaFree(m->rcp32);
-        cudaFree(m->dsum);
-        cudaFree(m->best_s);
-        cudaFree(m->best_d);
-        cudaFree(m->map);
-        cudaFree(m->vcount);
+        void *old[] = {m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->best_s, m->best_d, m->map, m->vcount};
+        for (void *p : old) model_free(p, st);
         m->dout = m->din = nullptr; m->rcp = nullptr; m->rcp32 = nullptr; m->dsum = nullptr;
         m->best_s = m->map = m->vcount = nullptr; m->best_d = nullptr;
         m->Bcap = 0;
-        if (cudaMalloc(&m->dout, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->din, (size_t)B * 4) != cudaSuccess ||
-            cudaMalloc(&m->rcp, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->rcp32, (size_t)B * 4) != cudaSuccess ||
-            cudaMalloc(&m->dsum, (size_t)B * 4) != cudaSuccess || cudaMalloc(&m->best_s, (size_t)B * 4) != cudaSuccess ||
-            cudaMalloc(&m->best_d, (size_t)B * 8) != cudaSuccess || cudaMalloc(&m->map, (size_t)B * 4) != cudaSuccess ||
-            cudaMalloc(&m->vcount, (size_t)B * 4) != cudaSuccess) {
+        const size_t b = (size_t)B;
+        if (!alloc(&m->dout, b * 4) || !alloc(&m->din, b * 4) || !alloc(&m->rcp, b * 8) || !alloc(&m->rcp32, b * 4) ||
+            !alloc(&m->dsum, b * 4) || !alloc(&m->best_s, b * 4) || !alloc(&m->best_d, b * 8) ||
+            !alloc(&m->map, b * 4) || !alloc(&m->vcount, b * 4)) {
             cudaGetLastError();
-            return fail(SBP_ENOMEM, "cudaMalloc failed for the block arrays of B = " + std::to_string(B));
+            return fail(SBP_ENOMEM, "device allocation failed for the block arrays of B = " + std::to_string(B));
         }
         m->Bcap = B;
     }
@@ -397,7 +274,7 @@ int count_cells(sbp_model *m, int32_t *cells) {
     if (g->m > 0) {
         const size_t smem = (size_t)B * 4;
         if (smem > 48 * 1024)
-            SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SBP_TRY(ensure_dyn_smem((const void *)k_hist_dense, smem));
         k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, num_sms() * 8), kThreads, smem, m->stream>>>(g->dev(), m->b,
                                                                                                         cells, B, nullptr);
         SBP_LAUNCHED();
@@ -422,7 +299,7 @@ int update_cells(sbp_model *m, int32_t *cells) {
     if (g->m > 0) {
         const size_t smem = (size_t)B * 4;
         if (smem > 48 * 1024)
-            SBP_CUDA(cudaFuncSetAttribute(k_hist_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SBP_TRY(ensure_dyn_smem((const void *)k_hist_dense, smem));
         k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, cells, B,
                                                                                                   flag);
         SBP_LAUNCHED();

@@ -31,6 +31,19 @@ void count_launch();
         SBP_CUDA(cudaGetLastError());            \
     } while (0)
 
+// Device memory of a model: stream-ordered allocation on the model's stream
+// (no device-wide synchronisation, so threads driving other models are not
+// stalled), and a pool of small pinned host buffers for read-backs.
+cudaError_t model_alloc(void **p, size_t bytes, cudaStream_t st);
+void model_free(void *p, cudaStream_t st);
+void *pinned_get();
+void pinned_put(void *p);
+
+// Raises the dynamic shared memory limit of kernel `func` on the current
+// device to at least `bytes`; never lowers it, so threads launching the same
+// kernel with different sizes cannot undercut one another's launch.
+int ensure_dyn_smem(const void *func, size_t bytes);
+
 #define SBP_TRY(call)                \
     do {                             \
         int _rc = (call);            \

@@ -1,35 +1,16 @@
-// nodal.cu -- the asynchronous-Gibbs nodal decision pass.
+// nodal.cu -- the asynchronous-Gibbs nodal decision pass of one graph.
 //
-// For every vertex v (block r) against the frozen (b, M):
-//   1. proposal (Alg. 2 "propose new community"): a uniformly chosen
-//      incident edge (out-list then in-list) gives the neighbour block u;
-//      s is drawn with probability (1 + M[u][s] + M[s][u]) / (d_u + B) by an
-//      integer inverse CDF over the prefix array P[u];
-//   2. neighbour-block counts kout[t], kin[t] (Section III-A (c): the sparse
-//      vector of changes) aggregated with warp match/ballot and, for longer
-//      rows, a shared-memory hash table;
-//   3. Delta DL over the changed entries of rows r,s and columns r,s only
-//      (Section II-C), block degrees included (Eq. 1-2).  Every term is
-//      f(x+k) - f(x) with f(x) = x ln x at integer counts, summed exactly in
-//      128-bit fixed point from a table (FP64 for counts beyond the table);
-//   4. Hastings-corrected Metropolis test (Alg. 2): logA = -beta dDL +
-//      ln(p_bwd / p_fwd), accept iff ln(u) < logA.  The Hastings sums and
-//      the logarithms are first evaluated in FP32 with a rigorous error
-//      bound; when ln(u) falls inside that band (or a trace is requested)
-//      the sums and the test are redone in FP64, so every decision equals
-//      the FP64 one.
-// The decision goes to the pending assignment; M is untouched until commit.
-//
-// GB300 executes one FP64 warp instruction per ~20 SM cycles, so the FP64
-// work is kept off the common path and spread across lanes when it runs.
 // Kernels: k_propose (one lane per vertex) draws every proposal and sends
 // those with s != r to three lists by degree; k_eval_batch (32 movers per
-// warp, k <= 32), k_eval_warp (one warp per mover with a shared-memory
-// table) and k_eval_cta (one CTA per mover, very large tables) aggregate
-// the rows of the movers only and run the test.
+// warp, k <= 32, and k <= 128 with direct-mapped counts while B is small),
+// k_eval_warp (one warp per mover with a shared-memory table) and k_eval_cta
+// (one CTA per mover, very large tables) aggregate the rows of the movers
+// only and run the test.  The decision goes to the pending assignment; M is
+// untouched until commit.  The steps and their numerics are described in
+// nodal_dev.cuh.
 #include <cmath>
 
-#include "common.cuh"
+#include "nodal_dev.cuh"
 
 // CTAs per SM the warp kernel is compiled for (register budget)
 #ifndef SBP_DECIDE_MIN_BLOCKS
@@ -39,394 +20,12 @@
 namespace sbp {
 namespace {
 
-// A proposal with s != b[v] that still needs its Delta DL and test.
-struct Mover {
-    int v, s;
-    unsigned long long w2;  // the Philox word of the acceptance draw
-};
-
-struct DecideArgs {
-    GraphDev g;
-    ModelDev md;
-    int64_t v_begin, v_end;
-    Mover *movers;           // three lists: k <= 32, 33..128, > 128
-    unsigned *mcount;        // their lengths (device counters)
-    int64_t mbase[3];        // their offsets in movers
-    uint64_t seed, sweep_id;
-    double beta;
-    float beta32;
-    int trace_on;
-    sbp_vertex_trace tr;
-};
-
-struct Counts {
-    unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0, recheck = 0;
-};
-
-__device__ __forceinline__ void write_trace(const DecideArgs &a, int v, int s, int flags, double dH, double logA) {
-    if (a.tr.s) a.tr.s[v] = s;
-    if (a.tr.flags) a.tr.flags[v] = flags;
-    if (a.tr.dH) a.tr.dH[v] = dH;
-    if (a.tr.logA) a.tr.logA[v] = logA;
-}
-
-
-// Per-vertex scalars shared by the evaluation steps.
-struct VertexCtx {
-    int v, r, s;
-    int Kout, Kin, self;  // out / in degree of v (self-loops included), self-loops
-    int ko_r, ki_r, ko_s, ki_s;
-    int k;  // total degree, an upper bound on the number of entries
-};
-
-// one neighbour block t not in {r, s}: exact Delta L terms, FP32 Hastings terms
-__device__ __forceinline__ void entry_fast(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, __int128 &dl,
-                                           double &fb, float &pf, float &pb) {
-    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
-    // a zero count gives T[x] - T[x] = 0, so no branch is needed
-    dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
-    dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
-    const float rc = md.rcp32[t];
-    const float c = (float)(ko + ki);
-    pf += c * (float)(Mts + Mst + 1) * rc;
-    pb += c * (float)((Mtr - ki) + (Mrt - ko) + 1) * rc;
-}
-
-// the same Hastings terms in FP64 (the expression the FP64 test uses)
-__device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, double &pf,
-                                            double &pb) {
-    const int64_t Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
-    const double den = (double)((int64_t)md.dsum[t] + md.B);
-    const double c = (double)(ko + ki);
-    pf += c * (double)(Mts + Mst + 1) / den;
-    pb += c * (double)((Mtr - ki) + (Mrt - ko) + 1) / den;
-}
-
-// ---------------------------------------------------------------------------
-// FP32 Delta L (the precision form).  f(x+k) - f(x), f(x) = x ln x, for
-// integer counts x >= 0 and x + k >= 0, from logf / log1pf (at most 2 ulp
-// each): k ln(x+k) + x log1p(k/x) when x + k >= x/2 (k/x > -1/2, so the
-// log1p argument's rounding is not amplified), else (x+k) ln(x+k) - x ln x
-// (no cancellation left to avoid).  Either way the result is within
-// 14 * 2^-24 of the sum of the magnitudes of its two parts, which is added
-// to am.  Summed over n terms in FP32 with at most d additions between any
-// term and the total, the error of Delta L stays below
-// 2^-24 (14 + d) sum(am): kDl32Base + k/32 bounds d + 14 for every kernel
-// (entries per lane or per chunk, the warp tree, the eight corner and degree
-// terms, the final additions).
-constexpr float kDl32Base = 40.0f;
-
-__device__ __forceinline__ float dxlogx32(int x, int k, float &am) {
-    if (k == 0) return 0.0f;
-    const int y = x + k;
-    const float xf = (float)x, yf = (float)y;
-    if (x == 0 || 2 * y < x) {
-        const float fy = y > 1 ? yf * logf(yf) : 0.0f;
-        const float fx = x > 1 ? xf * logf(xf) : 0.0f;
-        am += fabsf(fy) + fabsf(fx);
-        return fy - fx;
-    }
-    const float kf = (float)k;
-    const float t1 = kf * logf(yf);
-    const float t2 = xf * log1pf(kf / xf);
-    am += fabsf(t1) + fabsf(t2);
-    return t1 + t2;
-}
-
-// bound on |Delta L (FP32) - Delta L| for a move of a degree-k vertex
-__device__ __forceinline__ float dl32_error(float am, int k) {
-    return 0x1p-24f * (kDl32Base + (float)k * (1.0f / 32.0f)) * am * 1.01f + 1e-30f;
-}
-
-// entry_fast with the FP32 Delta L terms
-__device__ __forceinline__ void entry_fast32(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, float &dl,
-                                             float &am, float &pf, float &pb) {
-    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
-    dl += dxlogx32(Mrt, -ko, am) + dxlogx32(Mst, ko, am);
-    dl += dxlogx32(Mtr, -ki, am) + dxlogx32(Mts, ki, am);
-    const float rc = md.rcp32[t];
-    const float c = (float)(ko + ki);
-    pf += c * (float)(Mts + Mst + 1) * rc;
-    pb += c * (float)((Mtr - ki) + (Mrt - ko) + 1) * rc;
-}
-
-// the exact Delta L terms and the FP64 Hastings terms of one entry (the
-// recheck of the precision form)
-__device__ __forceinline__ void entry_exact_all(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki,
-                                                __int128 &dl, double &fb, double &pf, double &pb) {
-    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
-    dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
-    dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
-    const double den = (double)((int64_t)md.dsum[t] + md.B);
-    const double c = (double)(ko + ki);
-    pf += c * (double)((int64_t)Mts + Mst + 1) / den;
-    pb += c * (double)(((int64_t)Mtr - ki) + ((int64_t)Mrt - ko) + 1) / den;
-}
-
-// Delta L terms of the 2x2 corner (j = 0..3: (r,r) (s,s) (r,s) (s,r)) and of
-// the block degrees (j = 4..7: dout_r dout_s din_r din_s, subtracted), one
-// per lane, selected without divergence.  Returns the count it read (lanes
-// 0..3 read the four corner entries of M).
-__device__ __forceinline__ int special_terms(const ModelDev &md, const VertexCtx &x, int j, __int128 &dl, double &fb) {
-    if (j >= 8) return 0;
-    const int r = x.r, s = x.s, B = md.B;
-    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s;
-    const int rowi = (j == 0 || j == 2) ? r : s;
-    const int coli = (j == 0 || j == 3) ? r : s;
-    const int blk = (j == 4 || j == 6) ? r : s;
-    (void)B;
-    const int kk = j == 0   ? -(cr + x.self)
-                   : j == 1 ? cs + x.self
-                   : j == 2 ? x.ki_r - x.ko_s
-                   : j == 3 ? x.ko_r - x.ki_s
-                   : j == 4 ? -x.Kout
-                   : j == 5 ? x.Kout
-                   : j == 6 ? -x.Kin
-                            : x.Kin;
-    // the corner entries through the blockmodel accessor (dense or sparse)
-    const int val = j < 4 ? Mat(md, rowi, coli) : (j < 6 ? md.dout[blk] : md.din[blk]);
-    double f2 = 0.0;
-    const __int128 d = dT(md.T, md.XT, val, kk, f2);
-    dl += j < 4 ? d : -d;
-    fb += j < 4 ? f2 : -f2;
-    return val;
-}
-
-// special_terms with the FP32 Delta L terms
-__device__ __forceinline__ int special_terms32(const ModelDev &md, const VertexCtx &x, int j, float &dl, float &am) {
-    if (j >= 8) return 0;
-    const int r = x.r, s = x.s;
-    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s;
-    const int rowi = (j == 0 || j == 2) ? r : s;
-    const int coli = (j == 0 || j == 3) ? r : s;
-    const int blk = (j == 4 || j == 6) ? r : s;
-    const int kk = j == 0   ? -(cr + x.self)
-                   : j == 1 ? cs + x.self
-                   : j == 2 ? x.ki_r - x.ko_s
-                   : j == 3 ? x.ko_r - x.ki_s
-                   : j == 4 ? -x.Kout
-                   : j == 5 ? x.Kout
-                   : j == 6 ? -x.Kin
-                            : x.Kin;
-    const int val = j < 4 ? Mat(md, rowi, coli) : (j < 6 ? md.dout[blk] : md.din[blk]);
-    const float d = dxlogx32(val, kk, am);
-    dl += j < 4 ? d : -d;
-    return val;
-}
-
-// Hastings terms of v's neighbours in r and in s (forward and backward),
-// from the corner entries and the block degrees; FP32 and FP64 versions.
-struct CornerVals {
-    int Mrr, Mss, Mrs, Msr, dr, ds;
-};
-
-__device__ __forceinline__ void corner_hastings_fast(const VertexCtx &x, const CornerVals &c, int B, float &pf,
-                                                     float &pb) {
-    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin;
-    pf += (float)(cr + 2 * x.self) * (float)(c.Mrs + c.Msr + 1) / (float)(c.dr + B);
-    pf += (float)cs * (float)(2 * c.Mss + 1) / (float)(c.ds + B);
-    pb += (float)cr * (float)(2 * (c.Mrr - cr - x.self) + 1) / (float)(c.dr - K + B);
-    pb += (float)(cs + 2 * x.self) * (float)((c.Msr + x.ko_r - x.ki_s) + (c.Mrs + x.ki_r - x.ko_s) + 1) /
-          (float)(c.ds + K + B);
-}
-
-__device__ __forceinline__ void corner_hastings_exact(const VertexCtx &x, const CornerVals &c, int B, double &pf,
-                                                      double &pb) {
-    const int64_t cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s, K = x.Kout + x.Kin, self = x.self;
-    pf += (double)(cr + 2 * self) * (double)((int64_t)c.Mrs + c.Msr + 1) / (double)((int64_t)c.dr + B);
-    pf += (double)cs * (double)(2 * (int64_t)c.Mss + 1) / (double)((int64_t)c.ds + B);
-    pb += (double)cr * (double)(2 * ((int64_t)c.Mrr - cr - self) + 1) / (double)((int64_t)c.dr - K + B);
-    pb += (double)(cs + 2 * self) *
-          (double)(((int64_t)c.Msr + x.ko_r - x.ki_s) + ((int64_t)c.Mrs + x.ki_r - x.ko_s) + 1) /
-          (double)((int64_t)c.ds + K + B);
-}
-
-// FP32 decision with its error band.  Returns 1 accept, 0 reject, -1 when
-// the band does not settle it (FP64 needed).
-__device__ __forceinline__ int fast_decision_f(float b32, float dl32, float fb32, float pf, float pb, uint64_t w2,
-                                               int k, float eps_dl = 0.0f) {
-    const uint64_t um = w2 >> 11;
-    if (um == 0) return 1;  // u = 0: ln u = -inf
-    const float lnpf = logf(pf), lnpb = logf(pb);
-    const float logA = b32 * (dl32 + fb32) + (lnpb - lnpf);
-    const float u32 = fmaf((float)(unsigned)(um >> 21), 0x1p-32f, (float)(unsigned)(um & 0x1fffffu) * 0x1p-53f);
-    const float lnu = logf(u32);
-    const float diff = logA - lnu;
-    const float e = b32 * (eps_dl + 3.0f * 0x1p-24f * (fabsf(dl32) + fabsf(fb32) + 1.0f)) + 2.0f * (float)(k + 9) * 0x1p-24f +
-                    0x1p-23f * (fabsf(lnpf) + fabsf(lnpb) + 2.0f * fabsf(lnu) + fabsf(logA) + 1.0f);
-    const float band = 4.0f * e + 1e-6f;
-    if (!(fabsf(diff) > band)) return -1;  // also catches NaN / inf
-    return diff > 0.0f ? 1 : 0;
-}
-
-__device__ __forceinline__ int fast_decision(float b32, __int128 dl, bool has_fb, double fb, float pf, float pb,
-                                             uint64_t w2, int k) {
-    return fast_decision_f(b32, fix_to_float(dl), has_fb ? (float)fb : 0.0f, pf, pb, w2, k);
-}
-
-struct Exact {
-    double dH, logA;
-    bool accept, margin;
-};
-
-// the FP64 test: logA = -beta dDL + ln p_bwd - ln p_fwd, accept iff ln u < logA
-__device__ __noinline__ Exact exact_decision_d(double beta, double dL, double pf, double pb, uint64_t w2) {
-    Exact e;
-    e.dH = -dL;
-    e.logA = -beta * e.dH + log(pb) - log(pf);
-    const double lnu = log((double)(w2 >> 11) * 0x1p-53);
-    e.accept = lnu < e.logA;
-    e.margin = fabs(lnu - e.logA) <= 1e-9 * fmax(fabs(e.logA), 1.0);
-    return e;
-}
-
-__device__ __forceinline__ Exact exact_decision(double beta, __int128 dl, double fb, double pf, double pb, uint64_t w2) {
-    return exact_decision_d(beta, fix_to_double(dl) + fb, pf, pb, w2);
-}
-
-__device__ __forceinline__ unsigned hash_slot(int key, int cap_log2) {
-    return ((unsigned)key * 0x9E3779B1u) >> (32 - cap_log2);
-}
-
-// insert (key, inc) into an open-addressing table; false when full
-__device__ __forceinline__ bool table_add(int *keys, unsigned long long *cnt, int *list, int *nlist, int cap,
-                                          int cap_log2, int key, unsigned long long inc) {
-    unsigned h = hash_slot(key, cap_log2);
-    for (int p = 0; p < cap; ++p) {
-        const int prev = atomicCAS(&keys[h], -1, key);
-        if (prev == -1) {
-            list[atomicAdd(nlist, 1)] = (int)h;
-            atomicAdd(&cnt[h], inc);
-            return true;
-        }
-        if (prev == key) {
-            atomicAdd(&cnt[h], inc);
-            return true;
-        }
-        h = (h + 1) & (unsigned)(cap - 1);
-    }
-    return false;
-}
-
-// the same with 32-bit counts (ko | ki << 16) and 16-bit list entries
-__device__ __forceinline__ bool table_add32(int *keys, unsigned *cnt, unsigned short *list, int *nlist, int cap,
-                                            int cap_log2, int key, unsigned inc) {
-    unsigned h = hash_slot(key, cap_log2);
-    for (int p = 0; p < cap; ++p) {
-        const int prev = atomicCAS(&keys[h], -1, key);
-        if (prev == -1) {
-            list[atomicAdd(nlist, 1)] = (unsigned short)h;
-            atomicAdd(&cnt[h], inc);
-            return true;
-        }
-        if (prev == key) {
-            atomicAdd(&cnt[h], inc);
-            return true;
-        }
-        h = (h + 1) & (unsigned)(cap - 1);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin, int k) {
-    c.proposed++;
-    c.moves++;
-    c.accepted += accept;
-    c.margin += margin;
-    c.acc_edges += accept ? (unsigned long long)k : 0ull;
-}
-
-// a move decided by the exact evaluation
-__device__ __forceinline__ void count_exact(Counts &c, bool accept, bool margin, int k) {
-    count_result(c, accept, margin, k);
-    c.recheck++;
-}
-
-// ---------------------------------------------------------------------------
-// proposals: one lane per vertex, all vertices of the range
-
-__device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c) {
-    if (c.proposed | c.moves) {
-        atomicAdd(&md.counters->proposed, c.proposed);
-        atomicAdd(&md.counters->moves, c.moves);
-        atomicAdd(&md.counters->accepted, c.accepted);
-        atomicAdd(&md.counters->margin, c.margin);
-        if (c.acc_edges) atomicAdd(&md.counters->acc_edges, c.acc_edges);
-        if (c.recheck) atomicAdd(&md.counters->recheck, c.recheck);
-    }
-}
-
-__device__ __forceinline__ void flush_counts_warp(const ModelDev &md, Counts c, unsigned long long extra_edges) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c.proposed += __shfl_xor_sync(0xffffffffu, c.proposed, o);
-        c.moves += __shfl_xor_sync(0xffffffffu, c.moves, o);
-        c.accepted += __shfl_xor_sync(0xffffffffu, c.accepted, o);
-        c.margin += __shfl_xor_sync(0xffffffffu, c.margin, o);
-        c.acc_edges += __shfl_xor_sync(0xffffffffu, c.acc_edges, o);
-        c.recheck += __shfl_xor_sync(0xffffffffu, c.recheck, o);
-        extra_edges += __shfl_xor_sync(0xffffffffu, extra_edges, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        flush_counts(md, c);
-        if (extra_edges) atomicAdd(&md.counters->move_edges, extra_edges);
-    }
-}
-
-// first index i in Pu[0, len) with Pu[i] > t, searched by one lane: the 32
-// pivots with vector loads, then the segment eight entries at a time
-__device__ __forceinline__ int lane_cdf_search(const uint32_t *__restrict__ Pu, const uint32_t *__restrict__ Pcu, int len,
-                                               int step, uint32_t t) {
-    int lo = 0, seg = len;
-    if (len > 32) {
-        uint4 pv[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) pv[i] = reinterpret_cast<const uint4 *>(Pcu)[i];
-        int fp = 31;
-#pragma unroll
-        for (int i = 7; i >= 0; --i) {
-            if (pv[i].w > t) fp = 4 * i + 3;
-            if (pv[i].z > t) fp = 4 * i + 2;
-            if (pv[i].y > t) fp = 4 * i + 1;
-            if (pv[i].x > t) fp = 4 * i;
-        }
-        lo = fp * step;
-        seg = step < len - lo ? step : len - lo;
-    }
-    if (seg <= 32) {
-        for (int g0 = 0; g0 < seg; g0 += 8) {
-            uint32_t x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = g0 + i < seg ? Pu[lo + g0 + i] : 0xffffffffu;
-            int idx = -1;
-#pragma unroll
-            for (int i = 7; i >= 0; --i)
-                if (x[i] > t) idx = i;
-            if (idx >= 0) return lo + g0 + idx;
-        }
-        return lo + seg - 1;
-    }
-    int n = seg;
-    while (n > 0) {
-        const int half = n >> 1;
-        if (Pu[lo + half] <= t) {
-            lo += half + 1;
-            n -= half + 1;
-        } else {
-            n = half;
-        }
-    }
-    return lo;
-}
-
-// Proposal of every vertex in [v_begin, v_end) (Alg. 2 "propose new
-// community"): the j-th incident edge gives u, then s by the inverse CDF of
-// (1 + M[u][s] + M[s][u]) / (d_u + B).  Proposals with s = r end here; the
-// others are appended to the list of their degree group.
+// Proposal of every vertex in [v_begin, v_end).  Proposals with s = r end
+// here; the others are appended to the list of their degree group.
 __global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
     const ModelDev &md = a.md;
     const GraphDev &g = a.g;
-    const int lane = threadIdx.x & 31, B = md.B;
+    const int lane = threadIdx.x & 31;
     Counts c;
     unsigned long long medges = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -435,36 +34,17 @@ __global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
         int bin = -1, s = 0, v = (int)vv;
         uint64_t w2 = 0;
         if (vv < a.v_end) {
-            const int r = md.b[v];
-            const int o0 = g.op[v], kout = g.op[v + 1] - o0;
-            const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
-            const int k = kout + kin;
-            if (k == 0) {
-                write_trace(a, v, r, 0, 0.0, 0.0);
+            const Proposal p = propose_vertex(g, md, a.seed, a.sweep_id, v);
+            s = p.s;
+            if (p.k == 0) {
+                write_trace(a, v, p.r, 0, 0.0, 0.0);
+            } else if (p.s == p.r) {
+                c.proposed++;
+                write_trace(a, v, p.r, 1, 0.0, 0.0);
             } else {
-                const U64x4 w = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
-                const int j = (int)draw_below(w.x, (uint64_t)k);
-                const int nb = j < kout ? g.oc[o0 + j] : g.ic[i0 + j - kout];
-                const int u = md.b[nb];
-                const int64_t du = md.dsum[u];
-                const int64_t y = draw_below(w.y, (uint64_t)(du + B));
-                if (y < B) {
-                    s = (int)y;
-                } else if (md.sparse) {
-                    s = sparse_cdf_block(md, u, (uint32_t)(y - B), (uint32_t)md.dout[u]);
-                } else {
-                    const int idx = lane_cdf_search(md.P + (size_t)u * 2 * B, md.Pc + (size_t)u * 32, 2 * B, md.pstep,
-                                                    (uint32_t)(y - B));
-                    s = idx < B ? idx : idx - B;
-                }
-                if (s == r) {
-                    c.proposed++;
-                    write_trace(a, v, r, 1, 0.0, 0.0);
-                } else {
-                    bin = k <= kSmallDeg ? 0 : k <= kWarpDeg ? 1 : 2;
-                    w2 = w.z;
-                    medges += (unsigned long long)k;
-                }
+                bin = p.k <= kSmallDeg ? 0 : p.k <= kWarpDeg ? 1 : 2;
+                w2 = p.w2;
+                medges += (unsigned long long)p.k;
             }
         }
 #pragma unroll
@@ -485,114 +65,6 @@ __global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
         }
     }
     flush_counts_warp(md, c, medges);
-}
-
-// ---------------------------------------------------------------------------
-// moves of vertices with 33 <= k (one warp per vertex)
-
-// Evaluates the move v: r -> s once the entries are aggregated.
-// each_entry(f) calls f(t, ko, ki) for each entry the calling lane holds.
-// All 32 lanes call this; the result is written by lane 0.
-template <bool DL32, class EachEntry>
-__device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
-                                              EachEntry each_entry, Counts &c) {
-    const int lane = threadIdx.x & 31;
-    // neighbours in r and in s (one lane holds each); 16-bit fields when
-    // the degree allows it
-    if (x.k < 65536) {
-        int pr = 0, ps = 0;
-        each_entry([&](int t, int ko, int ki) {
-            if (t == x.r) pr += ko | (ki << 16);
-            else if (t == x.s) ps += ko | (ki << 16);
-        });
-        pr = warp_sum_i(pr);
-        ps = warp_sum_i(ps);
-        x.ko_r = pr & 0xffff;
-        x.ki_r = pr >> 16;
-        x.ko_s = ps & 0xffff;
-        x.ki_s = ps >> 16;
-    } else {
-        int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        each_entry([&](int t, int ko, int ki) {
-            if (t == x.r) { a0 += ko; a1 += ki; }
-            else if (t == x.s) { a2 += ko; a3 += ki; }
-        });
-        x.ko_r = warp_sum_i(a0);
-        x.ki_r = warp_sum_i(a1);
-        x.ko_s = warp_sum_i(a2);
-        x.ki_s = warp_sum_i(a3);
-    }
-
-    __int128 dl = 0;
-    double fb = 0.0;
-    float pf = 0.0f, pb = 0.0f;
-    float dlf = 0.0f, am = 0.0f;
-    int val;
-    if (DL32) {
-        each_entry([&](int t, int ko, int ki) {
-            if (t != x.r && t != x.s) entry_fast32(md, x, t, ko, ki, dlf, am, pf, pb);
-        });
-        val = special_terms32(md, x, lane, dlf, am);
-    } else {
-        each_entry([&](int t, int ko, int ki) {
-            if (t != x.r && t != x.s) entry_fast(md, x, t, ko, ki, dl, fb, pf, pb);
-        });
-        val = special_terms(md, x, lane, dl, fb);
-    }
-    CornerVals cv;
-    cv.Mrr = __shfl_sync(0xffffffffu, val, 0);
-    cv.Mss = __shfl_sync(0xffffffffu, val, 1);
-    cv.Mrs = __shfl_sync(0xffffffffu, val, 2);
-    cv.Msr = __shfl_sync(0xffffffffu, val, 3);
-    cv.dr = md.dsum[x.r];
-    cv.ds = md.dsum[x.s];
-    pf = warp_sum_f(pf);
-    pb = warp_sum_f(pb);
-    corner_hastings_fast(x, cv, md.B, pf, pb);
-    int dec = -1;
-    bool has_fb = false;
-    if (DL32) {
-        dlf = warp_sum_f(dlf);
-        am = warp_sum_f(am);
-        if (!a.trace_on) dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, x.k, dl32_error(am, x.k));
-    } else {
-        dl = warp_sum_128(dl);
-        has_fb = __any_sync(0xffffffffu, __double_as_longlong(fb) != 0);
-        if (has_fb) fb = warp_sum(fb);
-        if (!a.trace_on) dec = fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
-    }
-    if (dec >= 0) {
-        if (lane == 0) {
-            if (dec) md.bnew[x.v] = x.s;
-            count_result(c, dec != 0, false, x.k);
-        }
-        return;
-    }
-    double pf64 = 0.0, pb64 = 0.0;
-    if (DL32) {
-        // the exact Delta L as well
-        dl = 0;
-        fb = 0.0;
-        each_entry([&](int t, int ko, int ki) {
-            if (t != x.r && t != x.s) entry_exact_all(md, x, t, ko, ki, dl, fb, pf64, pb64);
-        });
-        special_terms(md, x, lane, dl, fb);
-        dl = warp_sum_128(dl);
-        if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
-    } else {
-        each_entry([&](int t, int ko, int ki) {
-            if (t != x.r && t != x.s) entry_exact(md, x, t, ko, ki, pf64, pb64);
-        });
-    }
-    pf64 = warp_sum(pf64);
-    pb64 = warp_sum(pb64);
-    corner_hastings_exact(x, cv, md.B, pf64, pb64);
-    if (lane == 0) {
-        const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
-        if (e.accept) md.bnew[x.v] = x.s;
-        count_exact(c, e.accept, e.margin, x.k);
-        write_trace(a, x.v, x.s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
-    }
 }
 
 // One warp per mover of list `bin` (k >= 33).  Dynamic shared memory per
@@ -1358,7 +830,7 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
     if (g->bin[2] > g->bin[1]) {
         const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
         const size_t smem = (size_t)wb * kWarpsPerCta;
-        SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<0, DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<0, DL32>, smem));
         k_eval_batch<0, DL32><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 0, wb);
         SBP_LAUNCHED();
     }
@@ -1370,12 +842,12 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
             const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
             const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
             const size_t smem = (size_t)wb * nwarps;
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_batch<1, DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32>, smem));
             k_eval_batch<1, DL32><<<sms * 3, nwarps * 32, smem, m->stream>>>(a, 1, wb);
             SBP_LAUNCHED();
         } else {
             const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp<DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp<DL32>, smem));
             k_eval_warp<DL32><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
             SBP_LAUNCHED();
         }
@@ -1391,13 +863,13 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
         if (cap <= 4096 && g->max_deg < 65536) {
             const int nwarps = cap <= 2048 ? 8 : 4;
             const size_t smem = warp_smem(cap, nwarps);
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_warp<DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp<DL32>, smem));
             k_eval_warp<DL32><<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);
             SBP_LAUNCHED();
         } else {
             const size_t smem = (size_t)cap * (8 + 4 + 4);
             if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
-            SBP_CUDA(cudaFuncSetAttribute(k_eval_cta<DL32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_cta<DL32>, smem));
             k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, m->stream>>>(a, 2, cap, cap_log2);
             SBP_LAUNCHED();
         }
@@ -1410,8 +882,8 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace) {
     const sbp_graph *g = m->g;
     if (!m->movers) {
-        if (cudaMalloc(&m->movers, (size_t)(g->n > 0 ? g->n : 1) * sizeof(Mover)) != cudaSuccess ||
-            cudaMalloc(&m->mcount, 4 * sizeof(unsigned)) != cudaSuccess) {
+        if (model_alloc(&m->movers, (size_t)(g->n > 0 ? g->n : 1) * sizeof(Mover), m->stream) != cudaSuccess ||
+            model_alloc((void **)&m->mcount, 4 * sizeof(unsigned), m->stream) != cudaSuccess) {
             cudaGetLastError();
             return fail(SBP_ENOMEM, "cudaMalloc failed for the mover lists");
         }

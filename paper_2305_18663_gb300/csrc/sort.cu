@@ -356,7 +356,7 @@ int rs_pass(const K *ks, const V *vs, const EdgeKeys &ek, K *kmade, int64_t n, i
     SBP_TRY(exclusive_scan_u32(hist, hist, (int64_t)nbins * G, nullptr, sscr, st));
     const size_t smem = rs_stage_bytes<K, V>(vs != nullptr);
     // the staging area plus the static tables pass the default 48 KB limit
-    SBP_CUDA(cudaFuncSetAttribute(k_rs_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SBP_TRY(ensure_dyn_smem((const void *)k_rs_scatter<K, V>, smem));
     k_rs_scatter<K, V><<<G, kRsThreads, smem, st>>>(ks, vs, n, chunk, shift, nbins, G, hist, kd, vd);
     SBP_LAUNCHED();
     return SBP_OK;

@@ -289,10 +289,10 @@ int bits_for(uint64_t maxval) {
 }
 
 template <class T>
-int alloc(T **p, int64_t count) {
-    cudaFree(*p);
+int alloc(sbp_model *m, T **p, int64_t count) {
+    model_free(*p, m->stream);
     *p = nullptr;
-    if (cudaMalloc((void **)p, (size_t)(count > 0 ? count : 1) * sizeof(T)) != cudaSuccess) {
+    if (model_alloc((void **)p, (size_t)(count > 0 ? count : 1) * sizeof(T), m->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(SBP_ENOMEM, "cudaMalloc failed for the sparse blockmodel");
     }
@@ -313,36 +313,36 @@ int ensure_sparse_capacity(sbp_model *m, int32_t B) {
     sbp_model::Sparse &S = m->sp;
     const int64_t E = m->g->m > 0 ? m->g->m : 1;
     if (S.cap_e < E) {
-        SBP_TRY(alloc(&S.key0, E));
-        SBP_TRY(alloc(&S.key1, E));
-        SBP_TRY(alloc(&S.start, E));
-        SBP_TRY(alloc(&S.rc, E));
-        SBP_TRY(alloc(&S.rv, E));
-        SBP_TRY(alloc(&S.rowof, E));
-        SBP_TRY(alloc(&S.rpre, E));
-        SBP_TRY(alloc(&S.cr, E));
-        SBP_TRY(alloc(&S.cv, E));
-        SBP_TRY(alloc(&S.cpre, E));
-        SBP_TRY(alloc(&S.ckey0, E));
-        SBP_TRY(alloc(&S.ckey1, E));
-        SBP_TRY(alloc(&S.cval0, E));
-        SBP_TRY(alloc(&S.cval1, E));
-        SBP_TRY(alloc(&S.hk, 4 * E + 2 * (int64_t)m->g->n));
-        SBP_TRY(alloc(&S.hv, 4 * E + 2 * (int64_t)m->g->n));
+        SBP_TRY(alloc(m, &S.key0, E));
+        SBP_TRY(alloc(m, &S.key1, E));
+        SBP_TRY(alloc(m, &S.start, E));
+        SBP_TRY(alloc(m, &S.rc, E));
+        SBP_TRY(alloc(m, &S.rv, E));
+        SBP_TRY(alloc(m, &S.rowof, E));
+        SBP_TRY(alloc(m, &S.rpre, E));
+        SBP_TRY(alloc(m, &S.cr, E));
+        SBP_TRY(alloc(m, &S.cv, E));
+        SBP_TRY(alloc(m, &S.cpre, E));
+        SBP_TRY(alloc(m, &S.ckey0, E));
+        SBP_TRY(alloc(m, &S.ckey1, E));
+        SBP_TRY(alloc(m, &S.cval0, E));
+        SBP_TRY(alloc(m, &S.cval1, E));
+        SBP_TRY(alloc(m, &S.hk, 4 * E + 2 * (int64_t)m->g->n));
+        SBP_TRY(alloc(m, &S.hv, 4 * E + 2 * (int64_t)m->g->n));
         const int64_t w = std::max(std::max(sort_scratch_words(E), scan_scratch_words(E) + 4),
                                    scan_scratch_words((int64_t)m->g->n + 1) + 4);
-        SBP_TRY(alloc(&S.scratch, w + 1024));
+        SBP_TRY(alloc(m, &S.scratch, w + 1024));
         S.cap_e = E;
     }
     if (sparse_by_count(B, m->g->m) && S.cap_cells < (int64_t)B * B) {
-        SBP_TRY(alloc(&S.cells, (int64_t)B * B));
+        SBP_TRY(alloc(m, &S.cells, (int64_t)B * B));
         S.cap_cells = (int64_t)B * B;
     }
     if (S.cap_b < B) {
-        SBP_TRY(alloc(&S.rp, (int64_t)B + 1));
-        SBP_TRY(alloc(&S.cp, (int64_t)B + 1));
-        SBP_TRY(alloc(&S.hoff, (int64_t)B + 1));
-        SBP_TRY(alloc(&S.cnt, (int64_t)B + 1));
+        SBP_TRY(alloc(m, &S.rp, (int64_t)B + 1));
+        SBP_TRY(alloc(m, &S.cp, (int64_t)B + 1));
+        SBP_TRY(alloc(m, &S.hoff, (int64_t)B + 1));
+        SBP_TRY(alloc(m, &S.cnt, (int64_t)B + 1));
         S.cap_b = B;
     }
     return SBP_OK;
@@ -471,7 +471,7 @@ void free_sparse(sbp_model *m) {
     sbp_model::Sparse &S = m->sp;
     void *ps[] = {S.key0, S.key1, S.start, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv, S.cpre, S.ckey0,
                   S.ckey1, S.cval0, S.cval1, S.hk, S.hv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells};
-    for (void *p : ps) cudaFree(p);
+    for (void *p : ps) model_free(p, m->stream);
     S = sbp_model::Sparse();
 }
 

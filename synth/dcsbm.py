@@ -29,7 +29,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Graph", "dcsbm", "perturb", "block_sizes", "CONFIGS", "make_config"]
+__all__ = ["Graph", "dcsbm", "perturb", "block_sizes", "CONFIGS", "make_config", "batch_specs", "serving_specs"]
 
 
 @dataclass
@@ -193,3 +193,36 @@ def make_config(name: str, seed: int = 0, scale: float = 1.0) -> Graph:
         c["n"] = max(int(c["n"] * scale), c["n_blocks"])
         c["e"] = max(int(c["e"] * scale), 1)
     return dcsbm(seed=seed, **c)
+
+
+def batch_specs(count: int = 4096, seed: int = 0, n_lo: int = 500, n_hi: int = 50_000) -> list[dict]:
+    """The many-small-graphs workload: N log-uniform in [n_lo, n_hi], mean
+    out-degree uniform in [8, 32], planted B = round(sqrt(N) / 2), degree
+    exponent 2.5 clipped to [1, 100], intra:inter 4:1, equal planted blocks.
+    Returns the keyword arguments of ``dcsbm`` for each graph (graph i uses
+    seed ``seed * 1_000_003 + i``)."""
+    rng = _rng(seed)
+    n = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64)
+    deg = rng.uniform(8.0, 32.0, count)
+    out = []
+    for i in range(count):
+        ni = int(n[i])
+        out.append(dict(n=ni, e=int(round(ni * deg[i])), n_blocks=max(1, int(round(np.sqrt(ni) / 2))), gamma=2.5,
+                        kmin=1, kmax=100, ratio=4.0, sizes="equal", seed=seed * 1_000_003 + i))
+    return out
+
+
+def serving_specs(count: int, seed: int = 0, n_lo: int = 1_000, n_hi: int = 2_000_000) -> list[dict]:
+    """Requests of the serving workload: N log-uniform in [n_lo, n_hi], mean
+    out-degree 16, planted B = round(sqrt(N) / 2), degree exponent 2.3 clipped
+    to [1, 1000], intra:inter 3:1 (the ratio is not stated for this workload),
+    log-normal planted sizes."""
+    rng = _rng(seed + 7)
+    n = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int64)
+    out = []
+    for i in range(count):
+        ni = int(n[i])
+        out.append(dict(n=ni, e=16 * ni, n_blocks=max(1, int(round(np.sqrt(ni) / 2))), gamma=2.3, kmin=1, kmax=1000,
+                        ratio=3.0, sizes="lognormal", seed=seed * 1_000_003 + 500_000 + i))
+    return out
+

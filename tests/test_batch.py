@@ -1,0 +1,65 @@
+"""The batching form: every graph of a batch ends with exactly the result of
+its own sbp_partition run (assignment, B, DL, sweep count), whatever the
+batch's schedule (workers, batch limit, admission waves).  Needs a GPU."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2305_18663_gb300 as P  # noqa: E402
+from synth.dcsbm import batch_specs, dcsbm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load()
+
+
+def _graphs(count, n_hi, seed=3):
+    specs = batch_specs(count, seed=seed, n_lo=300, n_hi=n_hi)
+    gs = [dcsbm(**s) for s in specs]
+    return gs, [P.Graph(g.n, g.src, g.dst) for g in gs]
+
+
+def _plain(pg, params):
+    return pg.partition(params)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(),                                            # defaults
+    dict(workers=3, max_B=64, dense_max_B=128),        # more per-graph phases, sparse rows above 128
+    dict(workers=2, max_B=1024, mem_fraction=1e-9),    # one graph admitted at a time
+])
+def test_batch_equals_plain(opts):
+    gs, pgs = _graphs(10, 4000)
+    params = P.Params.default(seed=4, dense_max_B=opts.get("dense_max_B", 1024))
+    out = P.partition_batch(pgs, params, P.BatchOptions.default(**opts))
+    for g, pg, (b, B, dl, ns, ta, td) in zip(gs, pgs, out):
+        pb, pB, pdl, pns = _plain(pg, params)
+        assert B == pB and ns == pns
+        assert dl == pdl
+        assert np.array_equal(b, pb)
+        assert 0.0 <= ta <= td
+
+
+def test_batch_dense_switch_does_not_change_results():
+    # the batch's dense/sparse switch is a schedule choice: the same graph
+    # partitioned with dense rows up to 4096 or sparse rows above 64 agrees
+    gs, pgs = _graphs(4, 2500, seed=9)
+    a = P.partition_batch(pgs, P.Params.default(seed=1), P.BatchOptions.default(dense_max_B=4096))
+    b = P.partition_batch(pgs, P.Params.default(seed=1), P.BatchOptions.default(max_B=64, dense_max_B=64))
+    for x, y in zip(a, b):
+        assert x[1] == y[1] and x[2] == y[2] and x[3] == y[3] and np.array_equal(x[0], y[0])
+
+
+def test_batch_bad_options_raise():
+    gs, pgs = _graphs(1, 600)
+    with pytest.raises(P.SbpError):
+        P.partition_batch(pgs, None, P.BatchOptions.default(max_B=5000))
+    with pytest.raises(P.SbpError):
+        P.partition_batch(pgs, None, P.BatchOptions.default(workers=0))
+    assert P.partition_batch([], None, None) == []
