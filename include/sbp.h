@@ -269,14 +269,15 @@ typedef struct sbp_batch_options {
     double mem_fraction;
 } sbp_batch_options;
 
-/* Per-graph result: B, DL and sweeps as sbp_partition returns them; t_admit
- * and t_done: seconds from the call's start to the graph's admission and to
- * its result. */
+/* Per-graph result: B, DL and sweeps as sbp_partition returns them;
+ * t_submit, t_admit, t_done: seconds from the start of the call (or of the
+ * server) to the graph's submission, admission and result. */
 typedef struct sbp_batch_result {
     int32_t B;
     int32_t reserved;
     double dl;
     int64_t n_sweeps;
+    double t_submit;
     double t_admit;
     double t_done;
 } sbp_batch_result;
@@ -308,6 +309,27 @@ int sbp_default_batch_options(sbp_batch_options *o);
 int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
                         const sbp_batch_options *o, int32_t *const *b_out, sbp_batch_result *res,
                         sbp_batch_stats *stats);
+
+/* ---------------------------------------------------------------------
+ * Serving form: the batch engine fed while it runs (continuous batching).
+ * sbp_server_create starts the engine (host worker threads and a launcher
+ * thread); requests submitted while others run are admitted as their
+ * memory fits (memory freed by finished requests admits the next), and
+ * their work overlaps on the device with the others'.  Every request's
+ * result equals sbp_partition of its graph alone.  A graph and its b_out
+ * buffer (host or device, n labels, or NULL) must stay valid until the
+ * request is done.  sbp_server_wait blocks until the request is done and
+ * returns its result (the request's own failure, if it failed);
+ * sbp_server_poll sets *done without blocking; sbp_server_destroy finishes
+ * every submitted request, then stops the threads and frees the engine. */
+typedef struct sbp_server sbp_server_t;
+
+int sbp_server_create(const sbp_params *p, const sbp_batch_options *o, sbp_server_t **out);
+int sbp_server_submit(sbp_server_t *s, const sbp_graph_t *g, int32_t *b_out, int64_t *request);
+int sbp_server_poll(sbp_server_t *s, int64_t request, int32_t *done);
+int sbp_server_wait(sbp_server_t *s, int64_t request, sbp_batch_result *res);
+int sbp_server_stats(sbp_server_t *s, sbp_batch_stats *stats);
+void sbp_server_destroy(sbp_server_t *s);
 
 /* Number of kernel launches the library has issued in this process, over
  * all handles and devices (a host-side counter, incremented as each launch

@@ -27,7 +27,9 @@ __all__ = [
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
     "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_default_batch_options", "sbp_partition_batch",
-    "BatchOptions", "BatchResult", "BatchStats", "partition_batch",
+    "BatchOptions", "BatchResult", "BatchStats", "partition_batch", "Server",
+    "sbp_server_create", "sbp_server_submit", "sbp_server_poll", "sbp_server_wait", "sbp_server_stats",
+    "sbp_server_destroy",
     "Graph", "Model", "deal_vertices",
 ]
 
@@ -105,6 +107,7 @@ class BatchResult(C.Structure):
         ("reserved", C.c_int32),
         ("dl", C.c_double),
         ("n_sweeps", C.c_int64),
+        ("t_submit", C.c_double),
         ("t_admit", C.c_double),
         ("t_done", C.c_double),
     ]
@@ -173,6 +176,12 @@ def load(path: str | None = None):
         "sbp_kernel_launches": (C.c_int, [P(u64)]),
         "sbp_default_batch_options": (C.c_int, [P(BatchOptions)]),
         "sbp_partition_batch": (C.c_int, [vp, i32, P(Params), P(BatchOptions), vp, P(BatchResult), P(BatchStats)]),
+        "sbp_server_create": (C.c_int, [P(Params), P(BatchOptions), P(vp)]),
+        "sbp_server_submit": (C.c_int, [vp, vp, vp, P(i64)]),
+        "sbp_server_poll": (C.c_int, [vp, i64, P(i32)]),
+        "sbp_server_wait": (C.c_int, [vp, i64, P(BatchResult)]),
+        "sbp_server_stats": (C.c_int, [vp, P(BatchStats)]),
+        "sbp_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -417,6 +426,77 @@ def partition_batch(graphs: list["Graph"], params: Params | None = None, options
     outs = [np.zeros(g.n, np.int32) for g in graphs]
     res = sbp_partition_batch([g.h for g in graphs], outs, params, options, stats)
     return [(outs[i], r.B, r.dl, r.n_sweeps, r.t_admit, r.t_done) for i, r in enumerate(res)]
+
+
+def sbp_server_create(params: Params | None = None, options: BatchOptions | None = None) -> int:
+    h = C.c_void_p()
+    _check(lib().sbp_server_create(C.byref(params) if params else None, C.byref(options) if options else None,
+                                   C.byref(h)))
+    return h.value
+
+
+def sbp_server_submit(s: int, g: int, b_out) -> int:
+    rid = C.c_int64()
+    _check(lib().sbp_server_submit(s, g, _ptr(b_out, np.int32) if b_out is not None else None, C.byref(rid)))
+    return rid.value
+
+
+def sbp_server_poll(s: int, request: int) -> bool:
+    d = C.c_int32()
+    _check(lib().sbp_server_poll(s, request, C.byref(d)))
+    return bool(d.value)
+
+
+def sbp_server_wait(s: int, request: int) -> BatchResult:
+    r = BatchResult()
+    _check(lib().sbp_server_wait(s, request, C.byref(r)))
+    return r
+
+
+def sbp_server_stats(s: int) -> BatchStats:
+    st = BatchStats()
+    _check(lib().sbp_server_stats(s, C.byref(st)))
+    return st
+
+
+def sbp_server_destroy(s: int) -> None:
+    lib().sbp_server_destroy(s)
+
+
+class Server:
+    """The serving form: submit graphs at any time, wait for their results.
+    Keeps each submitted graph and its label buffer alive until done."""
+
+    def __init__(self, params: Params | None = None, options: BatchOptions | None = None):
+        self.h = sbp_server_create(params, options)
+        self._keep: dict[int, tuple] = {}
+
+    def submit(self, g: "Graph") -> int:
+        b = np.zeros(g.n, np.int32)
+        rid = sbp_server_submit(self.h, g.h, b)
+        self._keep[rid] = (g, b)
+        return rid
+
+    def done(self, rid: int) -> bool:
+        return sbp_server_poll(self.h, rid)
+
+    def wait(self, rid: int):
+        """(b, B, dl, n_sweeps, t_submit, t_admit, t_done)"""
+        r = sbp_server_wait(self.h, rid)
+        g, b = self._keep.pop(rid)
+        return b, r.B, r.dl, r.n_sweeps, r.t_submit, r.t_admit, r.t_done
+
+    def stats(self) -> BatchStats:
+        return sbp_server_stats(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            sbp_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
 
 
 class Model:

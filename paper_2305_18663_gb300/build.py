@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsbp.so")
 SOURCES = ["api.cu", "graph.cu", "blockmodel.cu", "nodal.cu", "merge.cu", "xlogx_table.cu", "sort.cu", "sparse.cu",
-           "noalloc.cu", "batch.cu"]
+           "noalloc.cu", "batch.cu", "engine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

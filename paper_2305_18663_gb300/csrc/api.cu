@@ -218,6 +218,9 @@ int relabel_and_rebuild(sbp_model *m, const std::vector<int32_t> &map, int32_t B
 }
 
 }  // namespace
+
+int params_valid(const sbp_params &p) { return validate_params(p); }
+
 }  // namespace sbp
 
 using namespace sbp;

@@ -386,319 +386,6 @@ int batch_enqueue(const std::vector<sbp_model *> &models, const std::vector<uint
     return SBP_OK;
 }
 
-// ---------------------------------------------------------------------------
-// The batch driver.  Every graph runs its own golden-ratio search
-// (PartitionRun).  Two kinds of work overlap:
-//   - per-graph work on host worker threads: model set-up, merge phases,
-//     compaction, and the MCMC phases the persistent kernel does not take (B
-//     above the batch limit, or sparse rows).  Workers take graphs from a
-//     shared queue, largest first; a graph's work goes to its model's stream;
-//   - the persistent launch, driven by a launcher thread: it takes every graph
-//     whose next MCMC phase is batchable once enough are ready (a GPU's worth
-//     of CTAs) or once nothing else can make progress, runs their phases,
-//     and hands the graphs back to the workers.
-// Graphs are admitted in input order while their estimated device memory
-// fits the budget, and their models are freed as soon as they finish, so a
-// later graph takes the place of a finished one.
-
-namespace {
-
-double now_s() {
-    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-// device bytes of a graph's model at its largest (sparse rows at B = N)
-size_t model_bytes(const sbp_graph *g, int dense_max_B) {
-    const size_t n = (size_t)g->n, m = (size_t)std::max<int64_t>(g->m, 1);
-    return 144 * m + 128 * n + 12 * (size_t)dense_max_B * (size_t)dense_max_B + (1u << 20);
-}
-
-struct Item {
-    const sbp_graph *g = nullptr;
-    sbp_model *m = nullptr;
-    PartitionRun run;
-    bool started = false, after_batch = false, finished = false;
-    size_t bytes = 0;
-    double t_admit = 0, t_done = 0;
-};
-
-}  // namespace
-
-int partition_batch(const sbp_graph *const *graphs, int count, const sbp_params &p, const BatchOptions &opt,
-                    int32_t *const *b_out, sbp_batch_result *res, sbp_batch_stats *stats) {
-    const int W = std::max(1, opt.workers);
-    const int nstreams = W;
-    std::vector<cudaStream_t> streams((size_t)nstreams, nullptr);
-    auto destroy_streams = [&]() {
-        for (auto &s : streams)
-            if (s) cudaStreamDestroy(s);
-    };
-    for (auto &s : streams)
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            destroy_streams();
-            return cuda_fail(cudaGetLastError(), "sbp_partition_batch: cudaStreamCreate");
-        }
-    size_t free_b = 0, total_b = 0;
-    SBP_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const size_t budget = (size_t)((double)free_b * opt.mem_fraction);
-    sbp_params prm = p;
-    prm.dense_max_B = opt.tune.dense_max_B;
-    int dev = 0;
-    SBP_CUDA(cudaGetDevice(&dev));
-    int sms = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t full_batch = (size_t)sms * (size_t)std::max(1, opt.tune.ctas_per_sm);
-
-    std::vector<Item> items((size_t)count);
-    std::mutex mu;
-    std::condition_variable cv;
-    std::vector<int> cpu_q;   // graphs needing per-graph work
-    std::vector<int> ready;   // graphs waiting for a batched MCMC phase
-    int next = 0, done = 0, busy = 0, in_batch = 0;
-    size_t used = 0;
-    int err = SBP_OK;
-    std::string err_msg;
-    sbp_batch_stats st{};
-    std::atomic<int64_t> per_graph_phases{0};
-    double busy_s = 0.0;
-    const double t_start = now_s();
-
-    // under mu: admit graphs while their memory fits (always one when idle)
-    auto admit = [&]() {
-        while (next < count) {
-            Item &it = items[(size_t)next];
-            it.g = graphs[next];
-            it.bytes = model_bytes(it.g, prm.dense_max_B);
-            const bool idle = (done == next);
-            if (!idle && used + it.bytes > budget) break;
-            used += it.bytes;
-            it.t_admit = now_s() - t_start;
-            cpu_q.push_back(next);
-            ++next;
-        }
-    };
-    auto fail_all = [&](int rc, const std::string &msg) {
-        if (err == SBP_OK) {
-            err = rc;
-            err_msg = msg;
-        }
-        cv.notify_all();
-    };
-    // one graph's per-graph work, until it waits for a batched phase or ends
-    auto work = [&](int idx) -> int {
-        Item &it = items[(size_t)idx];
-        int r = SBP_OK;
-        double tm = now_s();
-        if (!it.started) {
-            std::vector<int32_t> ident((size_t)it.g->n);
-            std::iota(ident.begin(), ident.end(), 0);
-            r = sbp_build_blockmodel(it.g, (int32_t)it.g->n, ident.data(), &prm, streams[(size_t)idx % nstreams], &it.m);
-            if (r == SBP_OK) r = it.run.begin(it.m);
-            it.started = true;
-        } else if (it.after_batch) {
-            r = it.run.end_phase();
-            it.after_batch = false;
-        }
-        double t_merge = now_s() - tm, t_sweeps = 0.0;
-        while (r == SBP_OK && !it.run.done && !batch_eligible(it.m, opt.tune.max_B, opt.tune.max_n)) {
-            tm = now_s();
-            while (r == SBP_OK && !it.run.phase_over()) r = it.run.sweep();
-            const double t1 = now_s();
-            t_sweeps += t1 - tm;
-            if (r == SBP_OK) r = it.run.end_phase();
-            t_merge += now_s() - t1;
-            per_graph_phases.fetch_add(1, std::memory_order_relaxed);
-        }
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            st.s_merge += t_merge;
-            st.s_sweeps += t_sweeps;
-        }
-        if (r == SBP_OK && it.run.done) {
-            sbp_batch_result &o = res[idx];
-            r = it.run.finish(b_out ? b_out[idx] : nullptr, &o.B, &o.dl, &o.n_sweeps);
-            it.t_done = now_s() - t_start;
-            o.t_admit = it.t_admit;
-            o.t_done = it.t_done;
-            sbp_free_model(it.m);
-            it.m = nullptr;
-            it.finished = true;
-        }
-        return r;
-    };
-    auto worker = [&]() {
-        std::unique_lock<std::mutex> lk(mu);
-        for (;;) {
-            cv.wait(lk, [&]() { return err != SBP_OK || done == count || !cpu_q.empty(); });
-            if (err != SBP_OK || done == count) return;
-            // largest graph first
-            size_t pick = 0;
-            for (size_t q = 1; q < cpu_q.size(); ++q)
-                if (items[(size_t)cpu_q[q]].g->m > items[(size_t)cpu_q[pick]].g->m) pick = q;
-            const int idx = cpu_q[pick];
-            cpu_q.erase(cpu_q.begin() + (long)pick);
-            ++busy;
-            lk.unlock();
-            const double t0 = now_s();
-            const int r = work(idx);
-            std::string msg;
-            if (r != SBP_OK) {
-                char buf[1024];
-                sbp_last_error(buf, sizeof buf);
-                msg = "graph " + std::to_string(idx) + ": " + buf;
-            }
-            lk.lock();
-            busy_s += now_s() - t0;
-            --busy;
-            if (r != SBP_OK) {
-                fail_all(r, msg);
-                return;
-            }
-            Item &it = items[(size_t)idx];
-            if (it.finished) {
-                ++done;
-                used -= it.bytes;
-                admit();
-            } else {
-                ready.push_back(idx);
-            }
-            cv.notify_all();
-        }
-    };
-
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        admit();
-    }
-    std::vector<std::thread> th;
-    for (int w = 0; w < W; ++w) th.emplace_back(worker);
-    // the launcher (this thread): persistent launches in flight on their own
-    // streams, results in host-mapped memory, completion by event
-    struct Launch {
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
-        std::vector<int> take;
-        double t0 = 0;
-    };
-    const int kMaxInflight = 4;
-    std::vector<Launch> pool((size_t)kMaxInflight);
-    std::vector<int> free_slots;
-    for (int q = 0; q < kMaxInflight; ++q) {
-        free_slots.push_back(q);
-        if (cudaStreamCreateWithFlags(&pool[(size_t)q].st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&pool[(size_t)q].ev, cudaEventDisableTiming) != cudaSuccess) {
-            std::lock_guard<std::mutex> lk(mu);
-            fail_all(cuda_fail(cudaGetLastError(), "sbp_partition_batch: stream or event"), "stream or event creation");
-        }
-    }
-    int *h_k = nullptr;
-    double *h_dl = nullptr;
-    int *d_k = nullptr;
-    double *d_dl = nullptr;
-    const size_t cnt1 = (size_t)std::max(count, 1);
-    if (cudaHostAlloc((void **)&h_k, cnt1 * 4, cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostAlloc((void **)&h_dl, cnt1 * 8, cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void **)&d_k, h_k, 0) != cudaSuccess ||
-        cudaHostGetDevicePointer((void **)&d_dl, h_dl, 0) != cudaSuccess) {
-        std::lock_guard<std::mutex> lk(mu);
-        fail_all(cuda_fail(cudaGetLastError(), "sbp_partition_batch: mapped memory"), "mapped host memory");
-    }
-    std::vector<int> inflight;
-    {
-        std::unique_lock<std::mutex> lk(mu);
-        for (;;) {
-            cv.wait_for(lk, std::chrono::microseconds(500), [&]() {
-                return err != SBP_OK || done == count || ready.size() >= full_batch ||
-                       (!ready.empty() && cpu_q.empty() && busy < W && !free_slots.empty());
-            });
-            // completed launches hand their graphs back to the workers
-            for (size_t q = 0; q < inflight.size();) {
-                Launch &L = pool[(size_t)inflight[q]];
-                const cudaError_t e = cudaEventQuery(L.ev);
-                if (e == cudaErrorNotReady) {
-                    ++q;
-                    continue;
-                }
-                if (e != cudaSuccess) {
-                    fail_all(cuda_fail(e, "persistent launch"), std::string("batched phase: ") + cudaGetErrorString(e));
-                    break;
-                }
-                st.s_batched += now_s() - L.t0;
-                for (int idx : L.take) {
-                    Item &it = items[(size_t)idx];
-                    it.run.after_sweeps(h_k[idx], h_dl[idx]);
-                    it.after_batch = true;
-                    cpu_q.push_back(idx);
-                }
-                L.take.clear();
-                free_slots.push_back(inflight[q]);
-                inflight.erase(inflight.begin() + (long)q);
-                cv.notify_all();
-            }
-            if (err != SBP_OK) break;
-            if (done == count && inflight.empty()) break;
-            // a new launch once a GPU's worth is ready, or when the workers
-            // have nothing else to do
-            const bool starving = cpu_q.empty() && busy < W;
-            if (ready.empty() || free_slots.empty() || (ready.size() < full_batch && !starving)) continue;
-            const int slot = free_slots.back();
-            free_slots.pop_back();
-            Launch &L = pool[(size_t)slot];
-            L.take.swap(ready);
-            ready.clear();
-            inflight.push_back(slot);
-            std::vector<sbp_model *> ms;
-            std::vector<uint64_t> s0;
-            std::vector<double> tt, h0;
-            std::vector<int *> kr;
-            std::vector<double *> dr;
-            for (int idx : L.take) {
-                Item &it = items[(size_t)idx];
-                ms.push_back(it.m);
-                s0.push_back(it.run.sweep_id);
-                tt.push_back(it.run.t);
-                h0.push_back(it.run.hist[0]);
-                kr.push_back(d_k + idx);
-                dr.push_back(d_dl + idx);
-            }
-            lk.unlock();
-            L.t0 = now_s();
-            int r = batch_enqueue(ms, s0, tt, h0, kr, dr, opt.tune, L.st);
-            if (r == SBP_OK && cudaEventRecord(L.ev, L.st) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "cudaEventRecord");
-            std::string msg;
-            if (r != SBP_OK) {
-                char buf[1024];
-                sbp_last_error(buf, sizeof buf);
-                msg = std::string("batched phase: ") + buf;
-            }
-            lk.lock();
-            ++st.rounds;
-            st.phases_batched += (int64_t)L.take.size();
-            if (r != SBP_OK) {
-                fail_all(r, msg);
-                break;
-            }
-        }
-    }
-    for (int q : inflight) cudaEventSynchronize(pool[(size_t)q].ev);
-    for (Launch &L : pool) {
-        if (L.ev) cudaEventDestroy(L.ev);
-        if (L.st) cudaStreamDestroy(L.st);
-    }
-    if (h_k) cudaFreeHost(h_k);
-    if (h_dl) cudaFreeHost(h_dl);
-    cv.notify_all();
-    for (auto &t : th) t.join();
-    for (Item &it : items)
-        if (it.m) sbp_free_model(it.m);
-    destroy_streams();
-    if (err != SBP_OK) return fail(err, err_msg);
-    st.s_per_graph = busy_s;
-    st.phases_per_graph = per_graph_phases.load();
-    if (stats) *stats = st;
-    return SBP_OK;
-}
-
 }  // namespace sbp
 
 extern "C" int sbp_default_batch_options(sbp_batch_options *o) {
@@ -711,36 +398,4 @@ extern "C" int sbp_default_batch_options(sbp_batch_options *o) {
     o->reserved = 0;
     o->mem_fraction = 0.5;
     return SBP_OK;
-}
-
-extern "C" int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
-                                   const sbp_batch_options *o, int32_t *const *b_out, sbp_batch_result *res,
-                                   sbp_batch_stats *stats) {
-    using namespace sbp;
-    if (count < 0 || (count > 0 && (!graphs || !res))) return fail(SBP_EINVAL, "sbp_partition_batch: NULL argument");
-    for (int i = 0; i < count; ++i)
-        if (!graphs[i]) return fail(SBP_EINVAL, "sbp_partition_batch: NULL graph " + std::to_string(i));
-    sbp_params prm;
-    if (p) prm = *p;
-    else sbp_default_params(&prm);
-    sbp_batch_options bo;
-    if (o) bo = *o;
-    else sbp_default_batch_options(&bo);
-    if (bo.workers < 1 || bo.workers > 256) return fail(SBP_EINVAL, "sbp_partition_batch: workers must be in [1, 256]");
-    if (bo.max_B < 1 || bo.max_B > kBatchMaxB)
-        return fail(SBP_EINVAL, "sbp_partition_batch: max_B must be in [1, " + std::to_string(kBatchMaxB) + "]");
-    if (bo.dense_max_B < bo.max_B || bo.dense_max_B > 16384)
-        return fail(SBP_EINVAL, "sbp_partition_batch: dense_max_B must be in [max_B, 16384]");
-    if (bo.ctas_per_sm < 1 || bo.ctas_per_sm > 8) return fail(SBP_EINVAL, "sbp_partition_batch: ctas_per_sm must be in [1, 8]");
-    if (bo.max_n < 0) return fail(SBP_EINVAL, "sbp_partition_batch: max_n must be >= 0");
-    if (!(bo.mem_fraction > 0.0 && bo.mem_fraction <= 0.95))
-        return fail(SBP_EINVAL, "sbp_partition_batch: mem_fraction must be in (0, 0.95]");
-    BatchOptions opt;
-    opt.workers = bo.workers;
-    opt.mem_fraction = bo.mem_fraction;
-    opt.tune.max_B = bo.max_B;
-    opt.tune.dense_max_B = bo.dense_max_B;
-    opt.tune.ctas_per_sm = bo.ctas_per_sm;
-    opt.tune.max_n = bo.max_n;
-    return partition_batch(graphs, count, prm, opt, b_out, res, stats);
 }

@@ -26,9 +26,6 @@ struct BatchOptions {
 
 bool batch_eligible(const sbp_model *m, int max_B, int64_t max_n);
 
-int partition_batch(const sbp_graph *const *graphs, int count, const sbp_params &p, const BatchOptions &opt,
-                    int32_t *const *b_out, sbp_batch_result *res, sbp_batch_stats *stats);
-
 int batch_enqueue(const std::vector<sbp_model *> &models, const std::vector<uint64_t> &sweep0,
                   const std::vector<double> &t, const std::vector<double> &hist0, const std::vector<int *> &k_res,
                   const std::vector<double *> &dl_res, const BatchTuning &tune, cudaStream_t st);

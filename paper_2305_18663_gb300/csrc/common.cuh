@@ -44,6 +44,9 @@ void pinned_put(void *p);
 // kernel with different sizes cannot undercut one another's launch.
 int ensure_dyn_smem(const void *func, size_t bytes);
 
+// SBP_EINVAL with a message when a parameter is out of range
+int params_valid(const sbp_params &p);
+
 #define SBP_TRY(call)                \
     do {                             \
         int _rc = (call);            \

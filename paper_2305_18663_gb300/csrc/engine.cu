@@ -1,0 +1,543 @@
+// engine.cu -- the batch engine behind the batching and serving forms.
+//
+// Every graph runs its own golden-ratio search (PartitionRun, Section II-B;
+// Alg. 1 merge phases, Alg. 2 MCMC phases), with the same result as
+// sbp_partition.  Graphs can be submitted at any time.  Two kinds of work
+// overlap on the device:
+//   - per-graph work, driven by host worker threads: model set-up, merge
+//     phases, compaction, and the MCMC phases the persistent kernel does not
+//     take (B above its limit, big graphs, sparse rows).  Workers take graphs
+//     from a shared queue, largest first; a graph's work goes to its model's
+//     stream;
+//   - persistent launches (batch.cu), driven by the launcher: every graph whose
+//     next MCMC phase is batchable waits until a GPU's worth is ready or the
+//     workers have nothing else to do; up to four launches are in flight on
+//     their own streams, each completing by event, with results in host-mapped
+//     memory; their graphs then go back to the workers.
+// Admission: graphs are admitted in submission order while their estimated
+// device memory fits the budget (one is always admitted when none is
+// running); a finished graph's model is freed at once, so the next request
+// takes its place: continuous batching.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "batch.h"
+#include "driver.h"
+
+namespace sbp {
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// device bytes of a graph's model at its largest (sparse rows at B = N)
+size_t model_bytes(const sbp_graph *g, int dense_max_B) {
+    const size_t n = (size_t)g->n, m = (size_t)std::max<int64_t>(g->m, 1);
+    return 144 * m + 128 * n + 12 * (size_t)dense_max_B * (size_t)dense_max_B + (1u << 20);
+}
+
+}  // namespace
+
+struct Item {
+    const sbp_graph *g = nullptr;
+    int32_t *b_out = nullptr;
+    sbp_model *m = nullptr;
+    PartitionRun run;
+    bool admitted = false, started = false, after_batch = false, finished = false;
+    int rc = SBP_OK;
+    std::string msg;
+    size_t bytes = 0;
+    sbp_batch_result res{};
+};
+
+struct Engine {
+    sbp_params prm{};
+    BatchOptions opt;
+    int W = 1;
+    size_t budget = 0, full_batch = 1;
+    double t0 = 0;
+    std::vector<cudaStream_t> streams;
+
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::unique_ptr<Item>> items;
+    size_t next_admit = 0;          // first graph not yet admitted
+    std::vector<int64_t> cpu_q;     // graphs needing per-graph work
+    std::vector<int64_t> ready;     // graphs waiting for a batched MCMC phase
+    int busy = 0;
+    int64_t running = 0;            // admitted, not finished
+    size_t used = 0;
+    bool closing = false, aborting = false;
+    int fatal = SBP_OK;             // an engine-level failure (streams, launches)
+    std::string fatal_msg;
+    sbp_batch_stats st{};
+    std::atomic<int64_t> per_graph_phases{0};
+    std::vector<std::thread> workers;
+    std::thread launcher;
+
+    int init(const sbp_params &p, const BatchOptions &o, bool background);
+    int64_t submit(const sbp_graph *g, int32_t *b_out);
+    void close_and_join();
+    int loop();  // the launcher
+
+  private:
+    void admit();  // under mu
+    int work(Item &it, cudaStream_t s);
+    void worker();
+};
+
+void Engine::admit() {
+    while (next_admit < items.size()) {
+        Item &it = *items[next_admit];
+        it.bytes = model_bytes(it.g, prm.dense_max_B);
+        if (running > 0 && used + it.bytes > budget) break;
+        used += it.bytes;
+        it.admitted = true;
+        it.res.t_admit = now_s() - t0;
+        ++running;
+        cpu_q.push_back((int64_t)next_admit);
+        ++next_admit;
+    }
+}
+
+int Engine::init(const sbp_params &p, const BatchOptions &o, bool background) {
+    prm = p;
+    opt = o;
+    prm.dense_max_B = opt.tune.dense_max_B;
+    W = std::max(1, opt.workers);
+    t0 = now_s();
+    streams.assign((size_t)W, nullptr);
+    for (auto &s : streams) SBP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    size_t free_b = 0, total_b = 0;
+    SBP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    budget = (size_t)((double)free_b * opt.mem_fraction);
+    int dev = 0, sms = 1;
+    SBP_CUDA(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    full_batch = (size_t)sms * (size_t)std::max(1, opt.tune.ctas_per_sm);
+    for (int w = 0; w < W; ++w)
+        workers.emplace_back([this, dev]() {
+            cudaSetDevice(dev);
+            worker();
+        });
+    if (background)
+        launcher = std::thread([this, dev]() {
+            cudaSetDevice(dev);
+            loop();
+        });
+    return SBP_OK;
+}
+
+int64_t Engine::submit(const sbp_graph *g, int32_t *b_out) {
+    auto it = std::make_unique<Item>();
+    it->g = g;
+    it->b_out = b_out;
+    std::lock_guard<std::mutex> lk(mu);
+    it->res.t_submit = now_s() - t0;
+    items.push_back(std::move(it));
+    admit();
+    cv.notify_all();
+    return (int64_t)items.size() - 1;
+}
+
+// one graph's per-graph work, until it waits for a batched phase or ends
+int Engine::work(Item &it, cudaStream_t s) {
+    int r = SBP_OK;
+    double tm = now_s();
+    if (!it.started) {
+        std::vector<int32_t> ident((size_t)it.g->n);
+        std::iota(ident.begin(), ident.end(), 0);
+        r = sbp_build_blockmodel(it.g, (int32_t)it.g->n, ident.data(), &prm, s, &it.m);
+        if (r == SBP_OK) r = it.run.begin(it.m);
+        it.started = true;
+    } else if (it.after_batch) {
+        r = it.run.end_phase();
+        it.after_batch = false;
+    }
+    double t_merge = now_s() - tm, t_sweeps = 0.0;
+    while (r == SBP_OK && !it.run.done && !batch_eligible(it.m, opt.tune.max_B, opt.tune.max_n)) {
+        tm = now_s();
+        while (r == SBP_OK && !it.run.phase_over()) r = it.run.sweep();
+        const double t1 = now_s();
+        t_sweeps += t1 - tm;
+        if (r == SBP_OK) r = it.run.end_phase();
+        t_merge += now_s() - t1;
+        per_graph_phases.fetch_add(1, std::memory_order_relaxed);
+    }
+    if (r == SBP_OK && it.run.done) r = it.run.finish(it.b_out, &it.res.B, &it.res.dl, &it.res.n_sweeps);
+    if (r != SBP_OK || it.run.done) {
+        if (it.m) sbp_free_model(it.m);
+        it.m = nullptr;
+        it.finished = true;
+        it.res.t_done = now_s() - t0;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        st.s_merge += t_merge;
+        st.s_sweeps += t_sweeps;
+    }
+    return r;
+}
+
+void Engine::worker() {
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        cv.wait(lk, [&]() { return aborting || (closing && running == 0) || !cpu_q.empty(); });
+        if (aborting || (cpu_q.empty() && closing && running == 0)) return;
+        size_t pick = 0;  // the largest graph first
+        for (size_t q = 1; q < cpu_q.size(); ++q)
+            if (items[(size_t)cpu_q[q]]->g->m > items[(size_t)cpu_q[pick]]->g->m) pick = q;
+        const int64_t idx = cpu_q[pick];
+        cpu_q.erase(cpu_q.begin() + (long)pick);
+        Item &it = *items[(size_t)idx];
+        ++busy;
+        lk.unlock();
+        const double ts = now_s();
+        const int r = work(it, streams[(size_t)idx % streams.size()]);
+        std::string msg;
+        if (r != SBP_OK) {
+            char buf[1024];
+            sbp_last_error(buf, sizeof buf);
+            msg = buf;
+        }
+        lk.lock();
+        st.s_per_graph += now_s() - ts;
+        --busy;
+        if (it.finished) {
+            it.rc = r;
+            it.msg = msg;
+            --running;
+            used -= it.bytes;
+            admit();
+        } else {
+            ready.push_back(idx);
+        }
+        cv.notify_all();
+    }
+}
+
+int Engine::loop() {
+    struct Launch {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        std::vector<int64_t> take;
+        double t0 = 0;
+    };
+    const int kMaxInflight = 4;
+    std::vector<Launch> pool((size_t)kMaxInflight);
+    std::vector<int> free_slots, inflight;
+    int *h_k = nullptr;
+    double *h_dl = nullptr;
+    size_t cap = 0;  // entries of the mapped result arrays
+    int rc = SBP_OK;
+    auto engine_fail = [&](int code, const std::string &msg) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (fatal == SBP_OK) {
+            fatal = code;
+            fatal_msg = msg;
+        }
+        aborting = true;
+        cv.notify_all();
+    };
+    for (int q = 0; q < kMaxInflight; ++q) {
+        free_slots.push_back(q);
+        if (cudaStreamCreateWithFlags(&pool[(size_t)q].st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pool[(size_t)q].ev, cudaEventDisableTiming) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "batch engine: stream or event");
+            engine_fail(rc, "batch engine: stream or event creation failed");
+        }
+    }
+    // mapped result slots are indexed by graph; grown (when nothing is in
+    // flight) as graphs are submitted
+    auto ensure_cap = [&](size_t need) -> bool {
+        if (need <= cap) return true;
+        size_t c = std::max<size_t>(need, 2 * cap + 64);
+        int *nk = nullptr;
+        double *nd = nullptr;
+        if (cudaHostAlloc((void **)&nk, c * 4, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void **)&nd, c * 8, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            if (nk) cudaFreeHost(nk);
+            return false;
+        }
+        if (h_k) cudaFreeHost(h_k);
+        if (h_dl) cudaFreeHost(h_dl);
+        h_k = nk;
+        h_dl = nd;
+        cap = c;
+        return true;
+    };
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        while (rc == SBP_OK) {
+            cv.wait_for(lk, std::chrono::microseconds(500), [&]() {
+                return aborting || (closing && running == 0) || ready.size() >= full_batch ||
+                       (!ready.empty() && cpu_q.empty() && busy < W && !free_slots.empty());
+            });
+            for (size_t q = 0; q < inflight.size();) {
+                Launch &L = pool[(size_t)inflight[q]];
+                const cudaError_t e = cudaEventQuery(L.ev);
+                if (e == cudaErrorNotReady) {
+                    ++q;
+                    continue;
+                }
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "persistent launch");
+                    lk.unlock();
+                    engine_fail(rc, std::string("batched phase: ") + cudaGetErrorString(e));
+                    lk.lock();
+                    break;
+                }
+                st.s_batched += now_s() - L.t0;
+                for (int64_t idx : L.take) {
+                    Item &it = *items[(size_t)idx];
+                    it.run.after_sweeps(h_k[idx], h_dl[idx]);
+                    it.after_batch = true;
+                    cpu_q.push_back(idx);
+                }
+                L.take.clear();
+                free_slots.push_back(inflight[q]);
+                inflight.erase(inflight.begin() + (long)q);
+                cv.notify_all();
+            }
+            if (aborting || rc != SBP_OK) break;
+            if (closing && running == 0 && inflight.empty()) break;
+            const bool starving = cpu_q.empty() && busy < W;
+            if (ready.empty() || free_slots.empty() || (ready.size() < full_batch && !starving)) continue;
+            if (!ensure_cap(items.size())) {
+                if (!inflight.empty()) continue;  // grow once nothing reads the old slots
+                rc = SBP_ENOMEM;
+                lk.unlock();
+                engine_fail(rc, "batch engine: mapped host memory");
+                lk.lock();
+                break;
+            }
+            int *d_k = nullptr;
+            double *d_dl = nullptr;
+            if (cudaHostGetDevicePointer((void **)&d_k, h_k, 0) != cudaSuccess ||
+                cudaHostGetDevicePointer((void **)&d_dl, h_dl, 0) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "cudaHostGetDevicePointer");
+                lk.unlock();
+                engine_fail(rc, "batch engine: mapped host memory");
+                lk.lock();
+                break;
+            }
+            const int slot = free_slots.back();
+            free_slots.pop_back();
+            Launch &L = pool[(size_t)slot];
+            L.take.swap(ready);
+            ready.clear();
+            inflight.push_back(slot);
+            std::vector<sbp_model *> ms;
+            std::vector<uint64_t> s0;
+            std::vector<double> tt, h0;
+            std::vector<int *> kr;
+            std::vector<double *> dr;
+            for (int64_t idx : L.take) {
+                Item &it = *items[(size_t)idx];
+                ms.push_back(it.m);
+                s0.push_back(it.run.sweep_id);
+                tt.push_back(it.run.t);
+                h0.push_back(it.run.hist[0]);
+                kr.push_back(d_k + idx);
+                dr.push_back(d_dl + idx);
+            }
+            lk.unlock();
+            L.t0 = now_s();
+            int r = batch_enqueue(ms, s0, tt, h0, kr, dr, opt.tune, L.st);
+            if (r == SBP_OK && cudaEventRecord(L.ev, L.st) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+            std::string msg;
+            if (r != SBP_OK) {
+                char buf[1024];
+                sbp_last_error(buf, sizeof buf);
+                msg = std::string("batched phase: ") + buf;
+            }
+            lk.lock();
+            ++st.rounds;
+            st.phases_batched += (int64_t)L.take.size();
+            if (r != SBP_OK) {
+                rc = r;
+                lk.unlock();
+                engine_fail(r, msg);
+                lk.lock();
+                break;
+            }
+        }
+    }
+    for (int q : inflight) cudaEventSynchronize(pool[(size_t)q].ev);
+    for (Launch &L : pool) {
+        if (L.ev) cudaEventDestroy(L.ev);
+        if (L.st) cudaStreamDestroy(L.st);
+    }
+    if (h_k) cudaFreeHost(h_k);
+    if (h_dl) cudaFreeHost(h_dl);
+    return rc;
+}
+
+void Engine::close_and_join() {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        closing = true;
+        cv.notify_all();
+    }
+    if (launcher.joinable()) launcher.join();
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (fatal != SBP_OK) aborting = true;
+        cv.notify_all();
+    }
+    for (auto &t : workers)
+        if (t.joinable()) t.join();
+    workers.clear();
+    for (auto &p : items)
+        if (p->m) {
+            sbp_free_model(p->m);
+            p->m = nullptr;
+        }
+    for (auto &s : streams)
+        if (s) cudaStreamDestroy(s);
+    streams.clear();
+    st.phases_per_graph = per_graph_phases.load();
+}
+
+// the C ABI's option checks and conversion
+int batch_options(const sbp_batch_options *o, BatchOptions &opt) {
+    sbp_batch_options bo;
+    if (o) bo = *o;
+    else sbp_default_batch_options(&bo);
+    if (bo.workers < 1 || bo.workers > 256) return fail(SBP_EINVAL, "batch options: workers must be in [1, 256]");
+    if (bo.max_B < 1 || bo.max_B > kBatchMaxB)
+        return fail(SBP_EINVAL, "batch options: max_B must be in [1, " + std::to_string(kBatchMaxB) + "]");
+    if (bo.dense_max_B < bo.max_B || bo.dense_max_B > 16384)
+        return fail(SBP_EINVAL, "batch options: dense_max_B must be in [max_B, 16384]");
+    if (bo.ctas_per_sm < 1 || bo.ctas_per_sm > 8) return fail(SBP_EINVAL, "batch options: ctas_per_sm must be in [1, 8]");
+    if (bo.max_n < 0) return fail(SBP_EINVAL, "batch options: max_n must be >= 0");
+    if (!(bo.mem_fraction > 0.0 && bo.mem_fraction <= 0.95))
+        return fail(SBP_EINVAL, "batch options: mem_fraction must be in (0, 0.95]");
+    opt.workers = bo.workers;
+    opt.mem_fraction = bo.mem_fraction;
+    opt.tune.max_B = bo.max_B;
+    opt.tune.dense_max_B = bo.dense_max_B;
+    opt.tune.ctas_per_sm = bo.ctas_per_sm;
+    opt.tune.max_n = bo.max_n;
+    return SBP_OK;
+}
+
+}  // namespace sbp
+
+using sbp::Engine;
+using sbp::fail;
+
+extern "C" int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
+                                   const sbp_batch_options *o, int32_t *const *b_out, sbp_batch_result *res,
+                                   sbp_batch_stats *stats) {
+    if (count < 0 || (count > 0 && (!graphs || !res))) return fail(SBP_EINVAL, "sbp_partition_batch: NULL argument");
+    for (int i = 0; i < count; ++i)
+        if (!graphs[i]) return fail(SBP_EINVAL, "sbp_partition_batch: NULL graph " + std::to_string(i));
+    sbp_params prm;
+    if (p) prm = *p;
+    else sbp_default_params(&prm);
+    SBP_TRY(sbp::params_valid(prm));
+    sbp::BatchOptions opt;
+    SBP_TRY(sbp::batch_options(o, opt));
+    Engine e;
+    SBP_TRY(e.init(prm, opt, false));
+    for (int i = 0; i < count; ++i) e.submit(graphs[i], b_out ? b_out[i] : nullptr);
+    {
+        std::lock_guard<std::mutex> lk(e.mu);
+        e.closing = true;
+    }
+    const int rc = e.loop();
+    e.close_and_join();
+    if (e.fatal != SBP_OK) return fail(e.fatal, e.fatal_msg);
+    if (rc != SBP_OK) return rc;
+    for (int i = 0; i < count; ++i) {
+        const sbp::Item &it = *e.items[(size_t)i];
+        if (it.rc != SBP_OK) return fail(it.rc, "graph " + std::to_string(i) + ": " + it.msg);
+        res[i] = it.res;
+    }
+    if (stats) *stats = e.st;
+    return SBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// serving: the same engine, fed while it runs
+
+struct sbp_server {
+    Engine e;
+};
+
+extern "C" int sbp_server_create(const sbp_params *p, const sbp_batch_options *o, sbp_server_t **out) {
+    if (!out) return fail(SBP_EINVAL, "sbp_server_create: out is NULL");
+    *out = nullptr;
+    sbp_params prm;
+    if (p) prm = *p;
+    else sbp_default_params(&prm);
+    SBP_TRY(sbp::params_valid(prm));
+    sbp::BatchOptions opt;
+    SBP_TRY(sbp::batch_options(o, opt));
+    auto *s = new sbp_server();
+    const int rc = s->e.init(prm, opt, true);
+    if (rc != SBP_OK) {
+        s->e.close_and_join();
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return SBP_OK;
+}
+
+extern "C" int sbp_server_submit(sbp_server_t *s, const sbp_graph_t *g, int32_t *b_out, int64_t *request) {
+    if (!s || !g || !request) return fail(SBP_EINVAL, "sbp_server_submit: NULL argument");
+    {
+        std::lock_guard<std::mutex> lk(s->e.mu);
+        if (s->e.fatal != SBP_OK) return fail(s->e.fatal, s->e.fatal_msg);
+        if (s->e.closing) return fail(SBP_ESTATE, "sbp_server_submit: server is shutting down");
+    }
+    *request = s->e.submit(g, b_out);
+    return SBP_OK;
+}
+
+extern "C" int sbp_server_poll(sbp_server_t *s, int64_t request, int32_t *done) {
+    if (!s || !done) return fail(SBP_EINVAL, "sbp_server_poll: NULL argument");
+    std::lock_guard<std::mutex> lk(s->e.mu);
+    if (request < 0 || request >= (int64_t)s->e.items.size()) return fail(SBP_EINVAL, "sbp_server_poll: unknown request");
+    *done = s->e.items[(size_t)request]->finished ? 1 : 0;
+    return SBP_OK;
+}
+
+extern "C" int sbp_server_wait(sbp_server_t *s, int64_t request, sbp_batch_result *res) {
+    if (!s) return fail(SBP_EINVAL, "sbp_server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(s->e.mu);
+    if (request < 0 || request >= (int64_t)s->e.items.size()) return fail(SBP_EINVAL, "sbp_server_wait: unknown request");
+    sbp::Item &it = *s->e.items[(size_t)request];
+    s->e.cv.wait(lk, [&]() { return it.finished || s->e.aborting; });
+    if (!it.finished) return fail(s->e.fatal != SBP_OK ? s->e.fatal : SBP_ESTATE, "sbp_server_wait: " + s->e.fatal_msg);
+    if (it.rc != SBP_OK) return fail(it.rc, "request " + std::to_string(request) + ": " + it.msg);
+    if (res) *res = it.res;
+    return SBP_OK;
+}
+
+extern "C" int sbp_server_stats(sbp_server_t *s, sbp_batch_stats *stats) {
+    if (!s || !stats) return fail(SBP_EINVAL, "sbp_server_stats: NULL argument");
+    std::lock_guard<std::mutex> lk(s->e.mu);
+    *stats = s->e.st;
+    stats->phases_per_graph = s->e.per_graph_phases.load();
+    return SBP_OK;
+}
+
+extern "C" void sbp_server_destroy(sbp_server_t *s) {
+    if (!s) return;
+    s->e.close_and_join();
+    delete s;
+}
