@@ -50,6 +50,8 @@ class _Params(C.Structure):
         ("t_pre", C.c_double),
         ("t_post", C.c_double),
         ("max_sweeps", C.c_int64),
+        ("hybrid_h", C.c_int64),
+        ("dense_max_B", C.c_int64),
     ]
 
 
@@ -75,6 +77,7 @@ def lib():
         "og_dl": (f64, [i64, i64, i64, f64]),
         "og_move_delta": (ci, [vp, i64, i64, C.POINTER(f64), C.POINTER(f64), C.POINTER(f64)]),
         "og_nodal_decide": (i64, [vp, u64, u64, f64, i64, i64, i32p, vp, vp, vp, vp, vp, ci]),
+        "og_hybrid_decide": (i64, [vp, u64, u64, f64, i64, i32p, vp, vp, vp, vp, vp, ci]),
         "og_merge_delta": (f64, [vp, i64, i64]),
         "og_merge_key": (i64, [f64]),
         "og_merge_propose": (i64, [vp, u64, u64, i64, i64]),
@@ -227,6 +230,22 @@ class Model:
         acc = lib().og_nodal_decide(self._h, seed, sweep_id, beta, v_begin, v_end, b_new, _ptr(s), _ptr(flags), _ptr(dH), _ptr(logA), _ptr(lnu), nthreads)
         return Decisions(b_new, s, flags, dH, logA, lnu, int(acc))
 
+    def hybrid_decide(self, seed: int, sweep_id: int, beta: float, h: int, nthreads: int = 1) -> Decisions:
+        """Hybrid pass: the h highest-degree vertices sequentially (the model
+        is updated by each accepted move), then the rest by asynchronous
+        Gibbs against the resulting model.  The model keeps the state after
+        the sequential part; commit b_new with set_b."""
+        n = self.g.n
+        b_new = self.assignment()
+        s = np.zeros(n, np.int32)
+        flags = np.zeros(n, np.int32)
+        dH = np.zeros(n, np.float64)
+        logA = np.zeros(n, np.float64)
+        lnu = np.zeros(n, np.float64)
+        acc = lib().og_hybrid_decide(self._h, seed, sweep_id, beta, h, b_new, _ptr(s), _ptr(flags), _ptr(dH), _ptr(logA),
+                                     _ptr(lnu), nthreads)
+        return Decisions(b_new, s, flags, dH, logA, lnu, int(acc))
+
     def merge_delta(self, r: int, s: int) -> float:
         return lib().og_merge_delta(self._h, r, s)
 
@@ -285,10 +304,13 @@ class Params:
     t_pre: float = 5e-4
     t_post: float = 1e-4
     max_sweeps: int = 100
+    hybrid_h: int = 0
+    dense_max_B: int = 4096
 
 
 def partition(g: Graph, p: Params = Params(), nthreads: int = 1):
-    cp = _Params(p.seed, p.beta, p.merge_proposals, p.reduction, p.t_pre, p.t_post, p.max_sweeps)
+    cp = _Params(p.seed, p.beta, p.merge_proposals, p.reduction, p.t_pre, p.t_post, p.max_sweeps, p.hybrid_h,
+                 p.dense_max_B)
     b = np.zeros(g.n, np.int32)
     B, d, ns = C.c_int64(), C.c_double(), C.c_int64()
     if lib().og_partition(g._h, C.byref(cp), b, C.byref(B), C.byref(d), C.byref(ns), nthreads) != 0:

@@ -482,6 +482,88 @@ int64_t og_nodal_decide(const og_model *md, uint64_t seed, uint64_t sweep_id, do
     return accepted;
 }
 
+/* Hybrid pass: the hybrid SBP the paper adopts for the work within a node
+ * (Section II-B; Section III-B, "Hybrid SBP"): informative high-degree
+ * vertices are processed sequentially, the rest by asynchronous Gibbs.  The
+ * h vertices of largest degree k_v (ties: lower id first) are visited in that
+ * order; each draws its proposal and is decided (Metropolis-Hastings, Alg. 2)
+ * against the current model, and an accepted move is applied at once (labels
+ * and M; here by recounting M, the plainest correct update).  Then every
+ * other vertex decides against the model the sequential part left
+ * (asynchronous Gibbs).  b_new receives every vertex's label (the sequential
+ * vertices' current ones); the model holds the state after the sequential
+ * part.  Optional outputs as og_nodal_decide, for all vertices.  Returns the
+ * number of accepted moves. */
+typedef struct { int64_t k, v; } deg_key;
+static int cmp_deg(const void *a, const void *b) {
+    const deg_key *x = (const deg_key *)a, *y = (const deg_key *)b;
+    if (x->k != y->k) return x->k > y->k ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+int64_t og_hybrid_decide(og_model *md, uint64_t seed, uint64_t sweep_id, double beta, int64_t h, int32_t *b_new,
+                         int32_t *s_out, int32_t *flags_out, double *dH_out, double *logA_out, double *lnu_out,
+                         int nthreads) {
+    const og_graph *g = md->g;
+    const int64_t n = g->n;
+    if (h > n) h = n;
+    if (h < 0) h = 0;
+    deg_key *kv = (deg_key *)malloc(sizeof(deg_key) * (size_t)(n > 0 ? n : 1));
+    int64_t maxk = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        kv[v].k = (g->op[v + 1] - g->op[v]) + (g->ip[v + 1] - g->ip[v]);
+        kv[v].v = v;
+        if (kv[v].k > maxk) maxk = kv[v].k;
+    }
+    qsort(kv, (size_t)n, sizeof(deg_key), cmp_deg);
+    unsigned char *seq = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    nb_entry *sc = (nb_entry *)malloc(sizeof(nb_entry) * (size_t)(maxk > 0 ? maxk : 1));
+    int32_t *bt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t accepted = 0;
+    for (int64_t i = 0; i < h; ++i) {
+        const int64_t v = kv[i].v;
+        seq[v] = 1;
+        og_decision d;
+        nodal_decide(md, seed, sweep_id, beta, v, sc, &d);
+        if (s_out) s_out[v] = d.s;
+        if (flags_out) flags_out[v] = d.flags;
+        if (dH_out) dH_out[v] = d.dH;
+        if (logA_out) logA_out[v] = d.logA;
+        if (lnu_out) lnu_out[v] = d.lnu;
+        if (d.flags & 2) {
+            accepted++;
+            memcpy(bt, md->b, sizeof(int32_t) * (size_t)n);
+            bt[v] = d.s;
+            og_model_set_b(md, md->B, bt);
+        }
+    }
+    free(sc);
+    free(bt);
+    memcpy(b_new, md->b, sizeof(int32_t) * (size_t)n);
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads) reduction(+ : accepted)
+    {
+        nb_entry *sc2 = (nb_entry *)malloc(sizeof(nb_entry) * (size_t)(maxk > 0 ? maxk : 1));
+#pragma omp for schedule(dynamic, 512)
+        for (int64_t v = 0; v < n; ++v) {
+            if (seq[v]) continue;
+            og_decision d;
+            nodal_decide(md, seed, sweep_id, beta, v, sc2, &d);
+            b_new[v] = (d.flags & 2) ? d.s : md->b[v];
+            if (d.flags & 2) accepted++;
+            if (s_out) s_out[v] = d.s;
+            if (flags_out) flags_out[v] = d.flags;
+            if (dH_out) dH_out[v] = d.dH;
+            if (logA_out) logA_out[v] = d.logA;
+            if (lnu_out) lnu_out[v] = d.lnu;
+        }
+        free(sc2);
+    }
+    free(seq);
+    free(kv);
+    return accepted;
+}
+
 /* ------------------------------------------------------------------------ */
 /* P7. Block-merge proposal and merge Delta DL (Alg. 1 lines "propose" and
  * "calculate Delta DL"; Alg. 4).  u is the block at the far end of a random
@@ -702,6 +784,8 @@ typedef struct {
     double reduction;
     double t_pre, t_post;
     int64_t max_sweeps;
+    int64_t hybrid_h;     /* > 0: hybrid passes while B <= dense_max_B */
+    int64_t dense_max_B;
 } og_params;
 
 /* Merge phase: from state b with B blocks, reach B - n_merges blocks.  When
@@ -727,7 +811,8 @@ static int64_t merge_phase(og_model *md, const og_params *p, uint64_t *round_id,
     return md->B;
 }
 
-/* MCMC phase (Alg. 2 with the asynchronous-Gibbs pass): sweeps until
+/* MCMC phase (Alg. 2 with the asynchronous-Gibbs pass, or the hybrid pass
+ * while B <= dense_max_B when hybrid_h > 0): sweeps until
  * |DL_{k-3} - DL_k| < t DL_k (k >= 3) or max_sweeps. */
 static int64_t mcmc_phase(og_model *md, const og_params *p, uint64_t *sweep_id, double t, int nthreads) {
     const og_graph *g = md->g;
@@ -737,7 +822,10 @@ static int64_t mcmc_phase(og_model *md, const og_params *p, uint64_t *sweep_id, 
     int64_t k;
     for (k = 1; k <= p->max_sweeps; ++k) {
         memcpy(bn, md->b, sizeof(int32_t) * (size_t)g->n);
-        og_nodal_decide(md, p->seed, (*sweep_id)++, p->beta, 0, g->n, bn, NULL, NULL, NULL, NULL, NULL, nthreads);
+        if (p->hybrid_h > 0 && md->B <= p->dense_max_B)
+            og_hybrid_decide(md, p->seed, (*sweep_id)++, p->beta, p->hybrid_h, bn, NULL, NULL, NULL, NULL, NULL, nthreads);
+        else
+            og_nodal_decide(md, p->seed, (*sweep_id)++, p->beta, 0, g->n, bn, NULL, NULL, NULL, NULL, NULL, nthreads);
         og_model_set_b(md, md->B, bn);
         hist[k] = og_model_dl(md);
         if (k >= 3 && fabs(hist[k - 3] - hist[k]) < t * hist[k]) break;

@@ -503,3 +503,53 @@ def test_dl_without_edges_is_the_limit():
         assert prev is None or term < prev
         prev = term
     assert prev < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Hybrid pass: the h highest-degree vertices are decided one after another
+# against the current state, the others against the state the sequential
+# part left.  Pinned by brute-force Delta DL along that sequence.
+
+@pytest.mark.parametrize("seed", range(4))
+def test_hybrid_pass_sequential_then_frozen(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(6, 13))
+    src, dst = tiny_graph(rng, n, int(rng.integers(2 * n, 5 * n)), self_loops=True)
+    B = int(rng.integers(2, 5))
+    b = rng.integers(0, B, n).astype(np.int32)
+    E = src.size
+    deg = np.bincount(src, minlength=n) + np.bincount(dst, minlength=n)
+    order = sorted(range(n), key=lambda v: (-deg[v], v))
+    h = int(rng.integers(1, n))
+    g = O.Graph(n, src, dst)
+    m = O.Model(g, B, b)
+    d = m.hybrid_decide(seed, 4, 0.5, h)
+    state = b.copy()
+    for v in order[:h]:  # sequential part: each against the current state
+        if (d.flags[v] & 1) and d.s[v] != state[v]:
+            b2 = state.copy()
+            b2[v] = d.s[v]
+            want = brute_DL(brute_M(src, dst, b2, B), E, n) - brute_DL(brute_M(src, dst, state, B), E, n)
+            assert d.dH[v] == pytest.approx(want, rel=1e-10, abs=1e-10)
+            if d.flags[v] & 2:
+                state = b2
+    assert np.array_equal(m.assignment(), state)  # the model keeps the sequential result
+    base = brute_DL(brute_M(src, dst, state, B), E, n)
+    want_new = state.copy()
+    for v in order[h:]:  # the rest: against the frozen state
+        if (d.flags[v] & 1) and d.s[v] != state[v]:
+            b2 = state.copy()
+            b2[v] = d.s[v]
+            assert d.dH[v] == pytest.approx(brute_DL(brute_M(src, dst, b2, B), E, n) - base, rel=1e-10, abs=1e-10)
+            if d.flags[v] & 2:
+                want_new[v] = d.s[v]
+    assert np.array_equal(d.b_new, want_new)
+
+
+def test_hybrid_with_h0_is_the_async_pass():
+    g = make_config("plain_1k")
+    G = O.Graph(g.n, g.src, g.dst)
+    b = random_labels(g.n, 8, seed=2)
+    a = O.Model(G, 8, b).nodal_decide(5, 1, 3.0)
+    h = O.Model(G, 8, b).hybrid_decide(5, 1, 3.0, 0)
+    assert np.array_equal(a.b_new, h.b_new) and np.array_equal(a.dH, h.dH)
