@@ -160,7 +160,8 @@ def run_ours(args, rank, world, local_rank):
     g, B, b0 = workload(args.config, args.scale)
     stream = torch.cuda.current_stream(dev)
     graph = P.Graph(g.n, g.src, g.dst)
-    params = P.Params.default(seed=args.seed, dense_max_B=dense_max_b(args), dl_fp32=1 if args.dl == "fp32" else 0)
+    params = P.Params.default(seed=args.seed, dense_max_B=dense_max_b(args), dl_fp32=1 if args.dl == "fp32" else 0,
+                              hybrid_h=args.hybrid_h)
     model = P.Model(graph, B, b0, params, stream)
 
     def barrier():
@@ -273,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic (seeded directed DCSBM generator; the paper's graphs are not available)",
-            "config": describe(args.config, g, B, args.scale, args.m_form),
+            "config": dict(describe(args.config, g, B, args.scale, args.m_form), hybrid_h=args.hybrid_h),
             "impl": "ours",
             "e2e": {"value": g.n * e2e_steps * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * g.n, "d2h_bytes_per_step": 4 * g.n + 48},
@@ -527,6 +528,8 @@ def main():
     ap.add_argument("--m-form", default="sparse", choices=["dense", "sparse"],
                     help="sparse: hashed sparse rows at every B (the M form of the 1M-vertex precision "
                          "configuration; a dense run of the same sweeps is reported beside it); dense: M dense")
+    ap.add_argument("--hybrid-h", type=int, default=0,
+                    help="hybrid pass: this many highest-degree vertices sequentially (dense M only)")
     ap.add_argument("--dl", default="fp32", choices=["fp32", "exact"],
                     help="fp32: x ln x terms in FP32 with the exact recheck inside the error band; "
                          "exact: fixed-point/FP64 terms for every proposal")
@@ -552,7 +555,7 @@ def main():
         res = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * g.n / cb["value"], "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": describe(args.config, g, B, args.scale, args.m_form), "impl": "reference", "cpu_baseline": cb,
+               "config": dict(describe(args.config, g, B, args.scale, args.m_form), hybrid_h=args.hybrid_h), "impl": "reference", "cpu_baseline": cb,
                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(res))
         return

@@ -67,7 +67,13 @@ typedef struct sbp_model sbp_model_t;
  * error bound and redoes them exactly (fixed point and FP64) only for the
  * proposals whose log(u) falls within the resulting band of logA, so every
  * decision equals the FP64 one (Eq. 1-2; the precision form); 0 evaluates
- * them exactly for every proposal. */
+ * them exactly for every proposal;
+ * hybrid_h: 0 for the asynchronous-Gibbs pass; h > 0 for the hybrid pass of
+ * the hybrid SBP the paper adopts (Section III-B): the h vertices of largest
+ * degree (ties: lower id first) are decided one after another against the
+ * current blockmodel, each accepted move applied at once, then the others by
+ * asynchronous Gibbs against the result.  Full-range passes of a dense model
+ * only (sparse models and vertex ranges use the asynchronous pass). */
 typedef struct sbp_params {
     uint64_t seed;
     double beta;
@@ -79,6 +85,8 @@ typedef struct sbp_params {
     int32_t dense_max_B;
     int32_t full_rebuild;
     int32_t dl_fp32;
+    int32_t hybrid_h;
+    int32_t reserved;
 } sbp_params;
 
 /* Counters of one nodal pass.  n_proposed: vertices with at least one edge
@@ -120,7 +128,7 @@ size_t sbp_last_error(char *buf, size_t len);
 
 /* Fills p with the defaults: seed 0, beta 3, 10 merge proposals, 100
  * sweeps, reduction 0.5, t 5e-4 / 1e-4, dense_max_B 4096, full_rebuild 0,
- * dl_fp32 1. */
+ * dl_fp32 1, hybrid_h 0. */
 int sbp_default_params(sbp_params *p);
 
 /* Loads a directed graph given as COO (src[e] -> dst[e], e < m; host or

@@ -54,6 +54,8 @@ class Params(C.Structure):
         ("dense_max_B", C.c_int32),
         ("full_rebuild", C.c_int32),
         ("dl_fp32", C.c_int32),
+        ("hybrid_h", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
     @classmethod

@@ -120,6 +120,7 @@ int validate_params(const sbp_params &p) {
     if (p.dense_max_B < 1 || p.dense_max_B > 16384) return fail(SBP_EINVAL, "params: dense_max_B must be in [1, 16384]");
     if (p.full_rebuild != 0 && p.full_rebuild != 1) return fail(SBP_EINVAL, "params: full_rebuild must be 0 or 1");
     if (p.dl_fp32 != 0 && p.dl_fp32 != 1) return fail(SBP_EINVAL, "params: dl_fp32 must be 0 or 1");
+    if (p.hybrid_h < 0) return fail(SBP_EINVAL, "params: hybrid_h must be >= 0");
     return SBP_OK;
 }
 
@@ -248,6 +249,7 @@ extern "C" int sbp_default_params(sbp_params *p) {
     p->dense_max_B = 4096;
     p->full_rebuild = 0;
     p->dl_fp32 = 1;
+    p->hybrid_h = 0;
     return SBP_OK;
 }
 
@@ -257,7 +259,7 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     if (st) cudaStreamSynchronize(st);
     void *ps[] = {m->b,        m->bnew,   m->M,        m->P,       m->Pc,     m->dout,  m->din,
                   m->rcp,      m->rcp32,  m->dsum,     m->dl,      m->partials, m->counters, m->status,
-                  m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount};
+                  m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount, m->skip};
     for (void *p : ps) model_free(p, st);
     free_sparse(m);
     pinned_put(m->pinned);

@@ -281,7 +281,8 @@ int sm_count_b() {
 }  // namespace
 
 bool batch_eligible(const sbp_model *m, int max_B, int64_t max_n) {
-    return m->dense && m->B <= max_B && m->B <= kBatchMaxB && m->g->n <= max_n && m->g->m < (int64_t(1) << 22) &&
+    return m->dense && m->p.hybrid_h == 0 && m->B <= max_B && m->B <= kBatchMaxB && m->g->n <= max_n &&
+           m->g->m < (int64_t(1) << 22) &&
            m->g->max_deg < 65536 && m->g->n < (int64_t(1) << 30);
 }
 

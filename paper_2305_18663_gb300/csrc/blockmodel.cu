@@ -353,6 +353,15 @@ int build_blockmodel(sbp_model *m, bool after_pass) {
 
 int rebuild_blockmodel(sbp_model *m) { return build_blockmodel(m, false); }
 
+// P, Pc, degrees and reciprocals of a dense model from its M
+int launch_prefix(sbp_model *m) {
+    const int B = m->B;
+    k_prefix_dense<<<grid_for((int64_t)B * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
+        m->M, B, m->P, m->dout, m->din, m->rcp, m->rcp32, m->dsum, m->Pc, (2 * B + 31) / 32);
+    SBP_LAUNCHED();
+    return SBP_OK;
+}
+
 // After a nodal pass (m->b: new labels, m->bnew: the previous ones).  The
 // counts (dense M, or the cell counts of a sparse model rebuilt by
 // counting) take the incremental update when the plan kernel finds few

@@ -92,6 +92,7 @@ struct sbp_graph {
     int device = 0;
     int32_t *op = nullptr, *ip = nullptr, *oc = nullptr, *ic = nullptr, *esrc = nullptr;
     int32_t *order = nullptr;  // vertices grouped: k=0 | 1..32 | 33..128 | >128
+    int32_t *by_degree = nullptr;  // all vertices by degree, descending (ties: lower id first)
     int64_t bin[5] = {0, 0, 0, 0, 0};
     int32_t max_deg = 0;
     sbp::GraphDev dev() const {
@@ -182,6 +183,8 @@ struct sbp_model {
     // nodal pass: proposals with s != r, in three lists by degree
     void *movers = nullptr;
     unsigned *mcount = nullptr;
+    uint8_t *skip = nullptr;  // the hybrid pass's sequential vertices (n flags)
+    int32_t skip_h = -1;      // the h skip was built for
     // pinned host mirror for small read-backs
     void *pinned = nullptr;
     bool dense = true;
@@ -399,6 +402,7 @@ __device__ __forceinline__ int sparse_cdf_block(const ModelDev &md, int u, uint3
 int rebuild_blockmodel(sbp_model *m);  // M, P, degrees, rcp, DL from m->b
 int count_cells(sbp_model *m, int32_t *cells);  // cells[r * B + t] = edges r -> t
 int update_cells(sbp_model *m, int32_t *cells);  // counts of m->bnew -> counts of m->b
+int launch_prefix(sbp_model *m);                 // P, Pc, degrees, reciprocals from a dense M
 int commit_blockmodel(sbp_model *m);   // the same after a pass: m->b new labels, m->bnew the previous ones
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
 int launch_merge_proposals(sbp_model *m, uint64_t round_id);

@@ -103,6 +103,11 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     auto deg = [&](int32_t v) { return (op[(size_t)v + 1] - op[(size_t)v]) + (ip[(size_t)v + 1] - ip[(size_t)v]); };
     std::stable_sort(order.begin() + g->bin[3], order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
 
+    // every vertex by degree, descending, ties by id (the hybrid pass's order)
+    std::vector<int32_t> by_degree((size_t)n);
+    for (int64_t v = 0; v < n; ++v) by_degree[(size_t)v] = (int32_t)v;
+    std::stable_sort(by_degree.begin(), by_degree.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
+
     g->n = n;
     g->m = m;
     g->max_deg = maxk;
@@ -114,6 +119,7 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     if (rc == SBP_OK) rc = upload(&g->ic, ic.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->esrc, esrc.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->order, order.data(), (size_t)n);
+    if (rc == SBP_OK) rc = upload(&g->by_degree, by_degree.data(), (size_t)n);
     if (rc != SBP_OK) {
         sbp_free_graph(g);
         return rc;
@@ -137,5 +143,6 @@ extern "C" void sbp_free_graph(sbp_graph_t *g) {
     cudaFree(g->ic);
     cudaFree(g->esrc);
     cudaFree(g->order);
+    cudaFree(g->by_degree);
     delete g;
 }

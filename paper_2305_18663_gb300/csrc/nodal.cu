@@ -8,6 +8,7 @@
 // only and run the test.  The decision goes to the pending assignment; M is
 // untouched until commit.  The steps and their numerics are described in
 // nodal_dev.cuh.
+#include <algorithm>
 #include <cmath>
 
 #include "nodal_dev.cuh"
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(256) k_propose(DecideArgs a) {
         const int64_t vv = base + threadIdx.x;
         int bin = -1, s = 0, v = (int)vv;
         uint64_t w2 = 0;
-        if (vv < a.v_end) {
+        if (vv < a.v_end && !(a.skip && a.skip[v])) {
             const Proposal p = propose_vertex(g, md, a.seed, a.sweep_id, v);
             s = p.s;
             if (p.k == 0) {
@@ -771,6 +772,232 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
     flush_counts_warp(md, c, 0ull);
 }
 
+// ---------------------------------------------------------------------------
+// Sequential part of the hybrid pass (one CTA).  The h highest-degree
+// vertices, in order, each decided against the current (b, M) with the exact
+// evaluation (fixed-point Delta L, FP64 Hastings and test) and, when accepted,
+// applied at once: the cells of its edges, the degrees of r and s, the
+// labels.  The prefix rows P are rebuilt after this kernel; here the inverse
+// CDF of the proposal scans row u (then column u) of M directly.
+constexpr int kHybThreads = 256;
+
+__device__ __forceinline__ int cta_first_above(const int32_t *M, int B, int u, bool column, uint32_t t, int *s_out,
+                                               uint32_t *s_carry) {
+    // smallest c with sum_{c' <= c} (row u or column u of M)[c'] > t
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    __shared__ uint32_t wsum[kHybThreads / 32];
+    if (tid == 0) {
+        *s_out = B - 1;
+        *s_carry = 0;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < B; c0 += kHybThreads) {
+        const int c = c0 + tid;
+        const uint32_t x = c < B ? (uint32_t)(column ? M[(size_t)c * B + u] : M[(size_t)u * B + c]) : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        uint32_t before = *s_carry, total = 0;
+        for (int q = 0; q < kHybThreads / 32; ++q) {
+            before += q < w ? wsum[q] : 0u;
+            total += wsum[q];
+        }
+        const uint32_t p = before + incl;
+        const bool found = c < B && p > t && p - x <= t;
+        __syncthreads();
+        if (found) *s_out = c;
+        if (tid == 0) *s_carry += total;
+        const int any = __syncthreads_or(found ? 1 : 0);
+        if (any) break;
+    }
+    __syncthreads();
+    return *s_out;
+}
+
+__global__ void __launch_bounds__(kHybThreads) k_hybrid_seq(DecideArgs a, const int32_t *__restrict__ order, int h,
+                                                            int32_t *M, int32_t *dout, int32_t *din, int32_t *dsum,
+                                                            double *rcp, float *rcp32, int32_t *b, int32_t *bnew) {
+    extern __shared__ unsigned hsm[];
+    const ModelDev &md = a.md;
+    const GraphDev &g = a.g;
+    const int B = md.B, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    unsigned *cnt = hsm;
+    int *list = reinterpret_cast<int *>(hsm + B);
+    __shared__ int s_nl, s_self, s_u, s_mode, s_s, s_dec, s_pick;
+    __shared__ uint32_t s_t, s_carry;
+    __shared__ unsigned long long s_w2;
+    __shared__ __int128 r_dl[kHybThreads / 32];
+    __shared__ double r_fb[kHybThreads / 32], r_pf[kHybThreads / 32], r_pb[kHybThreads / 32];
+    for (int i = tid; i < B; i += kHybThreads) cnt[i] = 0u;
+    if (tid == 0) {
+        s_nl = 0;
+        s_self = 0;
+    }
+    Counts c;
+    __syncthreads();
+    for (int i = 0; i < h; ++i) {
+        const int v = order[i];
+        const int r = b[v];
+        const int o0 = g.op[v], kout = g.op[v + 1] - o0, i0 = g.ip[v], kin = g.ip[v + 1] - i0, k = kout + kin;
+        if (k == 0) {
+            if (tid == 0) write_trace(a, v, r, 0, 0.0, 0.0);
+            continue;
+        }
+        // the proposal, as in propose_vertex, against the current state
+        if (tid == 0) {
+            const U64x4 wd = philox4x64_10(a.sweep_id, (uint64_t)v, 0, 0, a.seed, 0);
+            const int j = (int)draw_below(wd.x, (uint64_t)k);
+            const int nb = j < kout ? g.oc[o0 + j] : g.ic[i0 + j - kout];
+            const int u = b[nb];
+            const int64_t y = draw_below(wd.y, (uint64_t)((int64_t)dsum[u] + B));
+            s_w2 = wd.z;
+            s_u = u;
+            if (y < B) {
+                s_mode = 0;
+                s_s = (int)y;
+            } else if (y - B < dout[u]) {
+                s_mode = 1;
+                s_t = (uint32_t)(y - B);
+            } else {
+                s_mode = 2;
+                s_t = (uint32_t)(y - B - dout[u]);
+            }
+        }
+        __syncthreads();
+        int s = s_s;
+        if (s_mode != 0) s = cta_first_above(M, B, s_u, s_mode == 2, s_t, &s_pick, &s_carry);
+        if (s == r) {
+            if (tid == 0) {
+                write_trace(a, v, r, 1, 0.0, 0.0);
+                c.proposed++;
+            }
+            __syncthreads();
+            continue;
+        }
+        // v's neighbour blocks: direct-mapped counts ko | ki << 16
+        for (int e = tid; e < k; e += kHybThreads) {
+            const bool is_out = e < kout;
+            const int nb = is_out ? g.oc[o0 + e] : g.ic[i0 + e - kout];
+            if (nb == v) {
+                if (is_out) atomicAdd(&s_self, 1);
+                continue;
+            }
+            const int t = b[nb];
+            if (atomicAdd(&cnt[t], is_out ? 1u : 0x10000u) == 0u) list[atomicAdd(&s_nl, 1)] = t;
+        }
+        __syncthreads();
+        VertexCtx x;
+        x.v = v;
+        x.r = r;
+        x.s = s;
+        x.Kout = kout;
+        x.Kin = kin;
+        x.self = s_self;
+        x.k = k;
+        x.ko_r = (int)(cnt[r] & 0xffffu);
+        x.ki_r = (int)(cnt[r] >> 16);
+        x.ko_s = (int)(cnt[s] & 0xffffu);
+        x.ki_s = (int)(cnt[s] >> 16);
+        const int nl = s_nl;
+        __int128 dl = 0;
+        double fb = 0.0, pf = 0.0, pb = 0.0;
+        for (int e = tid; e < nl; e += kHybThreads) {
+            const int t = list[e];
+            if (t == r || t == s) continue;
+            const unsigned cc = cnt[t];
+            entry_exact_all(md, x, t, (int)(cc & 0xffffu), (int)(cc >> 16), dl, fb, pf, pb);
+        }
+        if (tid < 8) special_terms(md, x, tid, dl, fb);
+        dl = warp_sum_128(dl);
+        fb = warp_sum(fb);
+        pf = warp_sum(pf);
+        pb = warp_sum(pb);
+        if (lane == 0) {
+            r_dl[w] = dl;
+            r_fb[w] = fb;
+            r_pf[w] = pf;
+            r_pb[w] = pb;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __int128 dlt = 0;
+            double fbt = 0.0, pft = 0.0, pbt = 0.0;
+            for (int q = 0; q < kHybThreads / 32; ++q) {
+                dlt += r_dl[q];
+                fbt += r_fb[q];
+                pft += r_pf[q];
+                pbt += r_pb[q];
+            }
+            CornerVals cv;
+            cv.Mrr = Mat(md, r, r);
+            cv.Mss = Mat(md, s, s);
+            cv.Mrs = Mat(md, r, s);
+            cv.Msr = Mat(md, s, r);
+            cv.dr = dsum[r];
+            cv.ds = dsum[s];
+            corner_hastings_exact(x, cv, B, pft, pbt);
+            const Exact e = exact_decision(a.beta, dlt, fbt, pft, pbt, s_w2);
+            count_exact(c, e.accept, e.margin, 0);
+            write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
+            s_dec = e.accept ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_dec) {
+            // apply the move: the cells of v's edges, then degrees and labels
+            for (int e = tid; e < kout; e += kHybThreads) {
+                const int wv = g.oc[o0 + e];
+                const int tw = wv == v ? r : b[wv], tn = wv == v ? s : b[wv];
+                atomicAdd(&M[(size_t)r * B + tw], -1);
+                atomicAdd(&M[(size_t)s * B + tn], 1);
+            }
+            for (int e = tid; e < kin; e += kHybThreads) {
+                const int wv = g.ic[i0 + e];
+                if (wv == v) continue;
+                const int tw = b[wv];
+                atomicAdd(&M[(size_t)tw * B + r], -1);
+                atomicAdd(&M[(size_t)tw * B + s], 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                dout[r] -= kout;
+                dout[s] += kout;
+                din[r] -= kin;
+                din[s] += kin;
+                const int qs[2] = {r, s};
+                for (int q = 0; q < 2; ++q) {
+                    const int bq = qs[q];
+                    dsum[bq] = dout[bq] + din[bq];
+                    rcp[bq] = 1.0 / ((double)dout[bq] + (double)din[bq] + (double)B);
+                    rcp32[bq] = 1.0f / ((float)dout[bq] + (float)din[bq] + (float)B);
+                }
+                b[v] = s;
+                bnew[v] = s;
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < nl; e += kHybThreads) cnt[list[e]] = 0u;
+        if (tid == 0) {
+            s_nl = 0;
+            s_self = 0;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) flush_counts(md, c);
+}
+
+__global__ void k_mark_skip(const int32_t *__restrict__ order, int h, int n, uint8_t *__restrict__ skip) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) skip[i] = 0;
+}
+
+__global__ void k_mark_skip2(const int32_t *__restrict__ order, int h, uint8_t *__restrict__ skip) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < h; i += gridDim.x * blockDim.x) skip[order[i]] = 1;
+}
+
 int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -904,11 +1131,41 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.beta = m->p.beta;
     a.beta32 = (float)m->p.beta;
     a.tr = trace ? *trace : sbp_vertex_trace{nullptr, nullptr, nullptr, nullptr};
+    a.skip = nullptr;
     a.trace_on = (a.tr.s || a.tr.flags || a.tr.dH || a.tr.logA) ? 1 : 0;
     const int sms = sm_count();
     const int B = m->B;
     if (B >= (1 << 24)) return fail(SBP_ESTATE, "nodal pass: B must be below 2^24");
     SBP_CUDA(cudaMemsetAsync(m->mcount, 0, 4 * sizeof(unsigned), m->stream));
+
+    // hybrid pass: the sequential part first (full-range passes of a dense model)
+    const int64_t h = std::min<int64_t>(m->p.hybrid_h, g->n);
+    if (h > 0 && m->dense && v_begin == 0 && v_end == g->n) {
+        if (g->max_deg >= 65536) return fail(SBP_ESTATE, "hybrid pass: degrees of 65536 or more are not supported");
+        if (!m->skip) {
+            if (model_alloc((void **)&m->skip, (size_t)g->n, m->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(SBP_ENOMEM, "device allocation failed for the hybrid pass");
+            }
+            m->skip_h = -1;
+        }
+        if (m->skip_h != (int32_t)h) {
+            k_mark_skip<<<(int)std::min<int64_t>((g->n + 255) / 256, 1024), 256, 0, m->stream>>>(g->by_degree, (int)h,
+                                                                                                 (int)g->n, m->skip);
+            SBP_LAUNCHED();
+            k_mark_skip2<<<(int)std::min<int64_t>((h + 255) / 256, 1024), 256, 0, m->stream>>>(g->by_degree, (int)h,
+                                                                                               m->skip);
+            SBP_LAUNCHED();
+            m->skip_h = (int32_t)h;
+        }
+        const size_t smem = (size_t)B * 8;
+        SBP_TRY(ensure_dyn_smem((const void *)k_hybrid_seq, smem));
+        k_hybrid_seq<<<1, kHybThreads, smem, m->stream>>>(a, g->by_degree, (int)h, m->M, m->dout, m->din, m->dsum,
+                                                          m->rcp, m->rcp32, m->b, m->bnew);
+        SBP_LAUNCHED();
+        SBP_TRY(launch_prefix(m));
+        a.skip = m->skip;
+    }
 
     // proposals for every vertex of the range
     {

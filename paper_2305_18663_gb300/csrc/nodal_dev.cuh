@@ -50,6 +50,7 @@ struct DecideArgs {
     float beta32;
     int trace_on;
     sbp_vertex_trace tr;
+    const uint8_t *skip;     // NULL, or vertices this pass leaves alone (the hybrid pass's sequential part)
 };
 
 struct Counts {

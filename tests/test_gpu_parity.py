@@ -252,6 +252,36 @@ def test_fp32_delta_dl_decides_as_exact(case):
     assert rechecks < moves
 
 
+@pytest.mark.parametrize("case", ["plain_1k_B8", "hubs_B64", "dcsbm_B316"])
+def test_hybrid_sweeps_match_oracle(case):
+    # hybrid pass: the h highest-degree vertices one after another against the
+    # current state (one CTA, M updated in place), the rest by asynchronous
+    # Gibbs against the result; compared vertex by vertex with the oracle
+    if case == "plain_1k_B8":
+        g, B, h = make_config("plain_1k"), 8, 40
+        b = random_labels(g.n, B, seed=3)
+    elif case == "hubs_B64":
+        g, B, h = _hub_graph(), 64, 30
+        b = random_labels(g.n, B, seed=4)
+    else:
+        g, B, h = make_config("dcsbm_1m", scale=0.02), 316, 200
+        b = perturb(g.planted, 316, 0.3, seed=0)
+    G = O.Graph(g.n, g.src, g.dst)
+    om = O.Model(G, B, b)
+    pg = P.Graph(g.n, g.src, g.dst)
+    pm = P.Model(pg, B, b, P.Params.default(seed=7, hybrid_h=h))
+    for sw in range(4):
+        bcur = om.assignment()
+        gd = gpu_decide(pm, g.n, sw)
+        od = om.hybrid_decide(7, sw, 3.0, h, nthreads=NT)
+        margin = compare_decisions(od, gd, bcur, np.arange(g.n))
+        assert margin.sum() == 0
+        P.sbp_commit(pm.h)
+        assert np.array_equal(pm.assignment(), od.b_new)
+        om.set_b(B, od.b_new)
+        check_blockmodel(pm, om)
+
+
 def test_shards_then_commit_equal_one_sweep():
     g = make_config("plain_1k")
     b = random_labels(g.n, 16, seed=4)
