@@ -339,6 +339,13 @@ int sbp_server_wait(sbp_server_t *s, int64_t request, sbp_batch_result *res);
 int sbp_server_stats(sbp_server_t *s, sbp_batch_stats *stats);
 void sbp_server_destroy(sbp_server_t *s);
 
+/* The FP32 x ln x term of the precision form, for known-answer tests:
+ * val[i] = f(x[i] + k[i]) - f(x[i]) with f(x) = x ln x as the FP32 Delta DL
+ * evaluation computes it, am[i] the magnitude its error bound is
+ * proportional to (|val - exact| <= 28 * 2^-24 * am); host arrays; x >= 0,
+ * 0 <= x + k < 2^31. */
+int sbp_dxlogx32_check(const int32_t *x, const int32_t *k, int32_t count, float *val, float *am);
+
 /* Number of kernel launches the library has issued in this process, over
  * all handles and devices (a host-side counter, incremented as each launch
  * is enqueued, whether or not the kernel then finds work to do).  For

@@ -26,7 +26,7 @@ __all__ = [
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
-    "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_default_batch_options", "sbp_partition_batch",
+    "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_dxlogx32_check", "sbp_default_batch_options", "sbp_partition_batch",
     "BatchOptions", "BatchResult", "BatchStats", "partition_batch", "Server",
     "sbp_server_create", "sbp_server_submit", "sbp_server_poll", "sbp_server_wait", "sbp_server_stats",
     "sbp_server_destroy",
@@ -177,6 +177,7 @@ def load(path: str | None = None):
         "sbp_dense_dl_noalloc": (C.c_int, [vp, i32, vp, vp, i64, i64, vp, vp]),
         "sbp_kernel_launches": (C.c_int, [P(u64)]),
         "sbp_default_batch_options": (C.c_int, [P(BatchOptions)]),
+        "sbp_dxlogx32_check": (C.c_int, [vp, vp, i32, vp, vp]),
         "sbp_partition_batch": (C.c_int, [vp, i32, P(Params), P(BatchOptions), vp, P(BatchResult), P(BatchStats)]),
         "sbp_server_create": (C.c_int, [P(Params), P(BatchOptions), P(vp)]),
         "sbp_server_submit": (C.c_int, [vp, vp, vp, P(i64)]),
@@ -379,6 +380,17 @@ def sbp_dense_dl_noalloc(M, B: int, dout, din, E: int, N: int, dl_out, stream=No
     allocating device memory (see include/sbp.h)."""
     _check(lib().sbp_dense_dl_noalloc(_ptr(M, np.int32), B, _ptr(dout, np.int32), _ptr(din, np.int32), E, N,
                                       _ptr(dl_out, np.float64), _stream_ptr(stream)))
+
+
+def sbp_dxlogx32_check(x, k):
+    """(val, am): the FP32 term f(x+k) - f(x) of the precision form and its
+    error magnitude, evaluated on the device."""
+    x = np.ascontiguousarray(x, np.int32)
+    k = np.ascontiguousarray(k, np.int32)
+    val = np.zeros(x.size, np.float32)
+    am = np.zeros(x.size, np.float32)
+    _check(lib().sbp_dxlogx32_check(x.ctypes.data, k.ctypes.data, int(x.size), val.ctypes.data, am.ctypes.data))
+    return val, am
 
 
 def sbp_kernel_launches() -> int:

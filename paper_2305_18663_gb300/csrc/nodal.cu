@@ -990,6 +990,15 @@ __global__ void __launch_bounds__(kHybThreads) k_hybrid_seq(DecideArgs a, const 
     if (tid == 0) flush_counts(md, c);
 }
 
+__global__ void k_dxlogx32(const int32_t *__restrict__ x, const int32_t *__restrict__ k, int n, float *__restrict__ val,
+                           float *__restrict__ am) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a = 0.0f;
+    val[i] = dxlogx32(x[i], k[i], a);
+    am[i] = a;
+}
+
 __global__ void k_mark_skip(const int32_t *__restrict__ order, int h, int n, uint8_t *__restrict__ skip) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) skip[i] = 0;
 }
@@ -1179,3 +1188,32 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
 }
 
 }  // namespace sbp
+
+// Known-answer hook for the FP32 term of the precision form: val[i] =
+// f(x[i] + k[i]) - f(x[i]) in FP32 and am[i] the magnitude its error bound
+// is proportional to (host arrays).
+extern "C" int sbp_dxlogx32_check(const int32_t *x, const int32_t *k, int32_t count, float *val, float *am) {
+    using namespace sbp;
+    if (count < 0 || count > (1 << 24) || (count > 0 && (!x || !k || !val || !am)))
+        return fail(SBP_EINVAL, "sbp_dxlogx32_check: bad count or NULL array");
+    for (int32_t i = 0; i < count; ++i)
+        if (x[i] < 0 || (int64_t)x[i] + k[i] < 0 || (int64_t)x[i] + k[i] > INT32_MAX)
+            return fail(SBP_EINVAL, "sbp_dxlogx32_check: need x >= 0 and 0 <= x + k < 2^31");
+    if (count == 0) return SBP_OK;
+    void *d = nullptr;
+    SBP_CUDA(cudaMalloc(&d, (size_t)count * 16));
+    int32_t *dx = static_cast<int32_t *>(d), *dk = dx + count;
+    float *dv = reinterpret_cast<float *>(dk + count), *da = dv + count;
+    cudaError_t e = cudaMemcpy(dx, x, (size_t)count * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, k, (size_t)count * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_dxlogx32<<<(count + 255) / 256, 256>>>(dx, dk, count, dv, da);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(val, dv, (size_t)count * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(am, da, (size_t)count * 4, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "sbp_dxlogx32_check");
+    return SBP_OK;
+}

@@ -98,38 +98,65 @@ __device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx 
 
 // ---------------------------------------------------------------------------
 // FP32 Delta L (the precision form).  f(x+k) - f(x), f(x) = x ln x, for
-// integer counts x >= 0 and x + k >= 0, from logf / log1pf (at most 2 ulp
-// each): k ln(x+k) + x log1p(k/x) when x + k >= x/2 (k/x > -1/2, so the
-// log1p argument's rounding is not amplified), else (x+k) ln(x+k) - x ln x
-// (no cancellation left to avoid).  Either way the result is within
-// 14 * 2^-24 of the sum of the magnitudes of its two parts, which is added
-// to am.  Summed over n terms in FP32 with at most d additions between any
-// term and the total, the error of Delta L stays below
-// 2^-24 (14 + d) sum(am): kDl32Base + k/32 bounds d + 14 for every kernel
-// (entries per lane or per chunk, the warp tree, the eight corner and degree
-// terms, the final additions).
-constexpr float kDl32Base = 40.0f;
+// integer counts x >= 0 and x + k >= 0, written
+//   k ln(x+k) + x ln(1 + k/x)          when x + k >= x/2 (k/x >= -1/2),
+//   (x+k) ln(x+k) - x ln x             otherwise (no cancellation left).
+// Logarithms come from the hardware approximation __logf, whose documented
+// error is at most 2^-21.41 absolute on [1/2, 2] and 3 ulp elsewhere; the
+// divisions from __fdividef (2 ulp).  ln(1 + z) for |z| <= 1/2 is the series
+// 2 atanh(w) = 2 (w + w^3/3 + ... + w^15/15), w = z / (2 + z), |w| <= 1/3,
+// whose truncation is below 2e-9 relative; beyond that it is __logf(1 + z)
+// with 1 + z >= 3/2.  With the conversions of counts above 2^24, the products
+// and the final sum, each result is within kTermErr * 2^-24 of the sum of the
+// magnitudes of its two parts, which is added to am; ln 1 is taken as 0
+// exactly.  Summed over the terms of a move in FP32 with at most d additions
+// between any term and the total, the error of Delta L stays below
+// 2^-24 (kTermErr + d) sum(am), and kDl32Depth + k/32 bounds d in every
+// kernel (entries per lane or per chunk, the warp tree, the eight corner and
+// degree terms, the final additions).  A known-answer hook
+// (sbp_dxlogx32_check) lets the tests check the bound against FP64.
+constexpr float kTermErr = 28.0f;
+constexpr float kDl32Depth = 26.0f;
+
+__device__ __forceinline__ float log1p_atanh(float z) {
+    const float w = __fdividef(z, 2.0f + z);
+    const float w2 = w * w;
+    float p = 1.0f / 15.0f;
+    p = fmaf(p, w2, 1.0f / 13.0f);
+    p = fmaf(p, w2, 1.0f / 11.0f);
+    p = fmaf(p, w2, 1.0f / 9.0f);
+    p = fmaf(p, w2, 1.0f / 7.0f);
+    p = fmaf(p, w2, 1.0f / 5.0f);
+    p = fmaf(p, w2, 1.0f / 3.0f);
+    p = fmaf(p, w2, 1.0f);
+    return 2.0f * w * p;
+}
+
+// ln y for an integer count y >= 1 (exactly 0 at 1)
+__device__ __forceinline__ float ln_count(int y) { return y > 1 ? __logf((float)y) : 0.0f; }
 
 __device__ __forceinline__ float dxlogx32(int x, int k, float &am) {
     if (k == 0) return 0.0f;
     const int y = x + k;
     const float xf = (float)x, yf = (float)y;
     if (x == 0 || 2 * y < x) {
-        const float fy = y > 1 ? yf * logf(yf) : 0.0f;
-        const float fx = x > 1 ? xf * logf(xf) : 0.0f;
+        const float fy = yf * ln_count(y > 0 ? y : 1);
+        const float fx = xf * ln_count(x > 0 ? x : 1);
         am += fabsf(fy) + fabsf(fx);
         return fy - fx;
     }
     const float kf = (float)k;
-    const float t1 = kf * logf(yf);
-    const float t2 = xf * log1pf(kf / xf);
+    const float t1 = kf * ln_count(y);
+    const float z = __fdividef(kf, xf);
+    const float l1 = fabsf(z) <= 0.5f ? log1p_atanh(z) : __logf(1.0f + z);
+    const float t2 = xf * l1;
     am += fabsf(t1) + fabsf(t2);
     return t1 + t2;
 }
 
 // bound on |Delta L (FP32) - Delta L| for a move of a degree-k vertex
 __device__ __forceinline__ float dl32_error(float am, int k) {
-    return 0x1p-24f * (kDl32Base + (float)k * (1.0f / 32.0f)) * am * 1.01f + 1e-30f;
+    return 0x1p-24f * (kTermErr + kDl32Depth + (float)k * (1.0f / 32.0f)) * am * 1.01f + 1e-30f;
 }
 
 // entry_fast with the FP32 Delta L terms

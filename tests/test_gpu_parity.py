@@ -110,6 +110,37 @@ def test_philox_device_matches_oracle():
             assert np.array_equal(got[i], O.philox4x64(c, key))
 
 
+def test_fp32_term_within_its_bound():
+    # the FP32 x ln x term against f(x+k) - f(x) in extended precision, over
+    # small and large counts, k of both signs, the branch boundaries, and
+    # counts beyond 2^24
+    rng = np.random.default_rng(17)
+    xs, ks = [], []
+    for hi in (8, 100, 5000, 1 << 20, 1 << 26, (1 << 31) - 2):
+        x = rng.integers(0, hi, 20000)
+        k = np.where(rng.random(x.size) < 0.5, -rng.integers(0, x + 1), rng.integers(1, 2000, x.size))
+        k = np.minimum(k, (1 << 31) - 1 - x)
+        xs.append(x)
+        ks.append(k)
+    e = np.array([0, 1, 2, 3, 4, 10, 100, 1000], np.int64)
+    for x0 in e:
+        for k0 in (-x0, -(x0 // 2), -(x0 // 2) - 1, 1, 2, x0 // 2, x0):
+            if x0 + k0 >= 0 and k0 != 0:
+                xs.append(np.array([x0]))
+                ks.append(np.array([k0]))
+    x = np.concatenate(xs).astype(np.int64)
+    k = np.concatenate(ks).astype(np.int64)
+    keep = (x + k >= 0) & (k != 0)
+    x, k = x[keep], k[keep]
+    val, am = P.sbp_dxlogx32_check(x, k)
+    xl, yl = x.astype(np.longdouble), (x + k).astype(np.longdouble)
+    f = lambda z: np.where(z > 0, z * np.log(np.maximum(z, 1)), 0)  # noqa: E731
+    exact = (f(yl) - f(xl)).astype(np.float64)
+    err = np.abs(val.astype(np.float64) - exact)
+    bound = 28 * 2.0 ** -24 * am.astype(np.float64) * 1.0001 + 1e-30
+    assert np.all(err <= bound), (x[err > bound][:5], k[err > bound][:5], (err / bound).max())
+
+
 @pytest.mark.parametrize("B,dmax", [(1, 4096), (8, 4096), (64, 4096), (1000, 4096), (8, 4), (64, 16), (1000, 16)])
 def test_blockmodel_rebuild_matches_oracle(B, dmax):
     g = make_config("plain_1k")
