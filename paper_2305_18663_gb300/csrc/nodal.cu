@@ -176,6 +176,77 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
 }
 
 // ---------------------------------------------------------------------------
+// One warp per mover with direct-mapped counts (B <= kDirectMaxB): the row's
+// neighbour blocks go straight into a per-warp array of B counts (ko | ki <<
+// 16) with shared-memory atomics, the first touch of a block (an atomic that
+// returns 0) appends it to the warp's list.  No table probing and no warp
+// match; eight 32-edge chunks in flight per round.  Degrees below 65536.
+constexpr int kDirectChunks = 8;
+
+template <bool DL32>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_warp_direct(DecideArgs a, int bin,
+                                                                                           int warp_words) {
+    extern __shared__ unsigned dmw[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const ModelDev &md = a.md;
+    const GraphDev &g = a.g;
+    const int B = md.B;
+    unsigned *cnt = dmw + (size_t)wid * warp_words;
+    int *list = reinterpret_cast<int *>(cnt + B);
+    for (int i = lane; i < B; i += 32) cnt[i] = 0u;
+    __syncwarp();
+    const Mover *mlist = a.movers + a.mbase[bin];
+    const int64_t count = *(volatile unsigned *)&a.mcount[bin];
+    Counts c;
+    for (int64_t q = (int64_t)blockIdx.x * nwarps + wid; q < count; q += (int64_t)gridDim.x * nwarps) {
+        const Mover mv = mlist[q];
+        const int v = mv.v, s = mv.s;
+        const int r = md.b[v];
+        const int o0 = g.op[v], kout = g.op[v + 1] - o0;
+        const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
+        const int k = kout + kin;
+        int nl = 0, self = 0;
+        for (int base = 0; base < k; base += 32 * kDirectChunks) {
+            int nb[kDirectChunks], tb[kDirectChunks];
+#pragma unroll
+            for (int c8 = 0; c8 < kDirectChunks; ++c8) {
+                const int idx = base + c8 * 32 + lane;
+                nb[c8] = idx < k ? (idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
+            }
+#pragma unroll
+            for (int c8 = 0; c8 < kDirectChunks; ++c8) tb[c8] = nb[c8] >= 0 ? md.b[nb[c8]] : -1;
+#pragma unroll
+            for (int c8 = 0; c8 < kDirectChunks; ++c8) {
+                const int idx = base + c8 * 32 + lane;
+                const bool is_out = idx < kout, is_self = nb[c8] == v;
+                self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
+                bool fresh = false;
+                if (tb[c8] >= 0 && !is_self) fresh = atomicAdd(&cnt[tb[c8]], is_out ? 1u : 0x10000u) == 0u;
+                const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+                if (fresh) list[nl + __popc(fm & ((1u << lane) - 1u))] = tb[c8];
+                nl += __popc(fm);
+            }
+        }
+        __syncwarp();
+        VertexCtx x;
+        x.v = v; x.r = r; x.s = s;
+        x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
+        const int D = nl;
+        evaluate_warp<DL32>(a, md, x, mv.w2, [&](auto &&f) {
+            for (int e = lane; e < D; e += 32) {
+                const int t = list[e];
+                const unsigned cc = cnt[t];
+                f(t, (int)(cc & 0xffffu), (int)(cc >> 16));
+            }
+        }, c);
+        __syncwarp();
+        for (int e = lane; e < D; e += 32) cnt[list[e]] = 0u;
+        __syncwarp();
+    }
+    if (lane == 0) flush_counts(md, c);
+}
+
+// ---------------------------------------------------------------------------
 // CTA per mover: tables beyond 4096 slots or degree >= 65536
 
 struct CtaScratch {
@@ -1088,9 +1159,17 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
             SBP_LAUNCHED();
         }
     }
-    // movers with k > 128: per-warp tables sized for min(max degree, B)
-    // distinct blocks while they fit, one CTA per mover beyond that
-    if (g->bin[4] > g->bin[3]) {
+    // movers with k > 128: per-warp direct-mapped counts while B is small,
+    // else per-warp tables sized for min(max degree, B) distinct blocks while
+    // they fit, one CTA per mover beyond that
+    if (g->bin[4] > g->bin[3] && B <= kDirectMaxB && g->max_deg < 65536) {
+        const int warp_words = 2 * B + 4;
+        const int nwarps = warp_words * 4 * kWarpsPerCta <= 64 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
+        const size_t smem = (size_t)warp_words * 4 * nwarps;
+        SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp_direct<DL32>, smem));
+        k_eval_warp_direct<DL32><<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, warp_words);
+        SBP_LAUNCHED();
+    } else if (g->bin[4] > g->bin[3]) {
         const int64_t dmax = g->max_deg < B ? g->max_deg : B;
         const int64_t need = dmax + dmax / 4 + 2;
         int cap_log2 = 6;
