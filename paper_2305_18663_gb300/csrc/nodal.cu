@@ -560,11 +560,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
         const int sb = 31 - __clz(fit);
         const int total = __shfl_sync(0xffffffffu, incl, sb) - fs;
         const bool act = lane >= sa && lane <= sb;
-        // ---- P2
-        for (int base = 0; base < total; base += 128) {
-            int nb[4], vq[4], tag[4];
+        // ---- P2 (eight 32-edge chunks in flight for the longer rows of MODE 1)
+        constexpr int kP2 = MODE == 1 ? 8 : 4;
+        for (int base = 0; base < total; base += 32 * kP2) {
+            int nb[kP2], vq[kP2], tag[kP2];
 #pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4) {
+            for (int c4 = 0; c4 < kP2; ++c4) {
                 const int pp = base + c4 * 32 + lane;
                 const int p = fs + pp;
                 int q = 0;
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                 nb[c4] = pp < total ? (e < kq ? g.oc[oq + e] : g.ic[iq + e - kq]) : -1;
             }
 #pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4) {
+            for (int c4 = 0; c4 < kP2; ++c4) {
                 const int pp = base + c4 * 32 + lane;
                 if (nb[c4] >= 0) {
                     const int t = md.b[nb[c4]];
