@@ -573,7 +573,7 @@ extern "C" int sbp_get_blockmodel_coo(const sbp_model_t *m, int64_t capacity, in
                 c.push_back(M[(size_t)i]);
             }
     } else {
-        const int64_t z = m->sp.nnz;
+        const int64_t z = sparse_nnz(const_cast<sbp_model *>(m));
         std::vector<uint32_t> rp((size_t)B + 1);
         std::vector<int32_t> rc((size_t)z), rv((size_t)z);
         SBP_CUDA(cudaMemcpy(rp.data(), m->sp.rp, rp.size() * 4, cudaMemcpyDeviceToHost));

@@ -335,7 +335,12 @@ int build_blockmodel(sbp_model *m, bool after_pass) {
         vals = m->M;
         nvals = BB;
     } else {
-        SBP_TRY(rebuild_sparse(m, after_pass));
+        bool dl_done = false;
+        SBP_TRY(rebuild_sparse(m, after_pass, &dl_done));
+        if (dl_done) {
+            SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, m->stream));
+            return SBP_OK;
+        }
         vals = m->sp.rv;
         nvals = m->sp.nnz;
     }

@@ -154,6 +154,7 @@ struct sbp_model {
         int32_t *cells = nullptr;  // B x B counts of the counting-sort rebuild
         int64_t cap_cells = 0;
         int32_t cells_B = 0;       // B the cells hold the counts of m->bnew for, else 0
+        int64_t *nnz_dev = nullptr;  // the nonzero count when only the device has it (nnz < 0)
     };
     Sparse sp;
     const sbp_graph *g = nullptr;
@@ -412,7 +413,8 @@ int ensure_capacity(sbp_model *m, int32_t B);
 int check_status(const sbp_model *m);
 int xlogx_table(int64_t need, const __int128 **table, int64_t *size);
 int ensure_sparse_capacity(sbp_model *m, int32_t B);
-int rebuild_sparse(sbp_model *m, bool after_pass);
+int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done);
+int64_t sparse_nnz(sbp_model *m);  // the nonzero count (read back once when only the device has it)
 void free_sparse(sbp_model *m);
 
 // sort.cu: exclusive scan of n uint32 (in may equal out; *total_dev, device,

@@ -17,7 +17,7 @@
 //      exact fixed-point sum over the nonzeros.
 #include <algorithm>
 
-#include "common.cuh"
+#include "apply.cuh"
 
 namespace sbp {
 
@@ -191,6 +191,186 @@ __global__ void k_cell_compact(const int32_t *__restrict__ cells, int B, const u
     }
 }
 
+// Small B (at most kSmallRowsB blocks): the rebuild from the cell counts in
+// four kernels with no host round trip -- CSR (offsets, columns, counts,
+// in-row prefixes, dout), CSC the same by column (rows ascending), the
+// per-row hash tables, the per-block scalars and DL (Eq. 2, exact fixed-point
+// sums, the same integer L as the general path).  The nonzero count stays on
+// the device.
+constexpr int kSmallRowsB = 1024;
+constexpr int kSmallThreads = 1024;
+
+__device__ uint32_t cta_excl_scan_1024(uint32_t v, uint32_t *sh, uint32_t *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t t = sh[lane];
+        uint32_t z = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        sh[lane] = z - t;
+        if (lane == 31) sh[32] = z;
+    }
+    __syncthreads();
+    const uint32_t r = sh[w] + x - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// (1) row and column lengths: a warp per row (warps [0, B)) or per column
+// (warps [B, 2B))
+__global__ void k_small_lengths(const int32_t *__restrict__ cells, int B, uint32_t *__restrict__ rlen,
+                                uint32_t *__restrict__ clen) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (w >= 2 * B) return;
+    const bool col = w >= B;
+    const int i = col ? w - B : w;
+    uint32_t c = 0;
+    for (int j0 = 0; j0 < B; j0 += 32) {
+        const int j = j0 + lane;
+        const bool nz = j < B && (col ? cells[j * B + i] : cells[i * B + j]) != 0;
+        c += (uint32_t)__popc(__ballot_sync(0xffffffffu, nz));
+    }
+    if (lane == 0) (col ? clen : rlen)[i] = c;
+}
+
+// (2) one CTA: offsets of the rows, the columns and the row tables
+__global__ void __launch_bounds__(kSmallThreads) k_small_offsets(const uint32_t *__restrict__ rlen,
+                                                                 const uint32_t *__restrict__ clen, int B,
+                                                                 uint32_t *__restrict__ rp, uint32_t *__restrict__ cp,
+                                                                 uint32_t *__restrict__ hoff,
+                                                                 int64_t *__restrict__ nnz_out) {
+    __shared__ uint32_t sh[33];
+    const int tid = threadIdx.x;
+    uint32_t total;
+    const uint32_t lr = tid < B ? rlen[tid] : 0u;
+    uint32_t ex = cta_excl_scan_1024(lr, sh, &total);
+    if (tid < B) rp[tid] = ex;
+    if (tid == 0) {
+        rp[B] = total;
+        *nnz_out = total;
+    }
+    ex = cta_excl_scan_1024(tid < B ? clen[tid] : 0u, sh, &total);
+    if (tid < B) cp[tid] = ex;
+    if (tid == 0) cp[B] = total;
+    uint32_t cap = 0;
+    if (tid < B) {
+        cap = 2;
+        while (cap < 2 * lr) cap <<= 1;
+    }
+    ex = cta_excl_scan_1024(cap, sh, &total);
+    if (tid < B) hoff[tid] = ex;
+    if (tid == 0) hoff[B] = total;
+}
+
+// (3) a warp per row (warps [0, B)): CSR entries, in-row prefixes, dout,
+// the row's hash table (cleared, then filled by the same warp); a warp per
+// column (warps [B, 2B)): CSC entries, prefixes, din.  Per warp, its share
+// of L (Eq. 1): + x ln x of the row's counts, - dout ln dout or
+// - din ln din, in fixed point.
+__global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uint32_t *__restrict__ rp,
+                             const uint32_t *__restrict__ cp, const uint32_t *__restrict__ hoff,
+                             int32_t *__restrict__ rc, int32_t *__restrict__ rv, int32_t *__restrict__ rowof,
+                             uint32_t *__restrict__ rpre, int32_t *__restrict__ cr, int32_t *__restrict__ cv,
+                             uint32_t *__restrict__ cpre, int32_t *__restrict__ hk, int32_t *__restrict__ hv,
+                             int32_t *__restrict__ dout, int32_t *__restrict__ din, const __int128 *__restrict__ T,
+                             __int128 *__restrict__ lpart, int32_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (w >= 2 * B) return;
+    const bool col = w >= B;
+    const int i = col ? w - B : w;
+    __int128 f = 0;
+    uint32_t p = col ? cp[i] : rp[i], carry = 0;
+    const uint32_t off = col ? 0u : hoff[i], cap = col ? 0u : hoff[i + 1] - off;
+    if (!col)
+        for (uint32_t q = lane; q < cap; q += 32) hk[off + q] = -1;
+    __syncwarp();
+    for (int j0 = 0; j0 < B; j0 += 32) {
+        const int j = j0 + lane;
+        const uint32_t v = j < B ? (uint32_t)(col ? cells[j * B + i] : cells[i * B + j]) : 0u;
+        const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (v != 0) {
+            const uint32_t q = p + (uint32_t)__popc(nz & ((1u << lane) - 1u));
+            if (col) {
+                cr[q] = j;
+                cv[q] = (int32_t)v;
+                cpre[q] = carry + incl;
+            } else {
+                rc[q] = j;
+                rv[q] = (int32_t)v;
+                rowof[q] = i;
+                rpre[q] = carry + incl;
+                f += T[v];
+                uint32_t h = sparse_hash(j) & (cap - 1);
+                bool done = false;
+                for (uint32_t t = 0; t < cap; ++t) {
+                    if (atomicCAS(&hk[off + h], -1, j) == -1) {
+                        hv[off + h] = (int32_t)v;
+                        done = true;
+                        break;
+                    }
+                    h = (h + 1) & (cap - 1);
+                }
+                if (!done) record_status(status, SBP_EHASHFULL);
+            }
+        }
+        p += (uint32_t)__popc(nz);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    f = warp_sum_128(f);
+    if (lane == 0) {
+        (col ? din : dout)[i] = (int32_t)carry;
+        lpart[w] = f - T[carry];
+    }
+}
+
+// (4) one CTA: per-block scalars and DL from the warps' shares of L (fixed
+// order, exact)
+__global__ void __launch_bounds__(kSmallThreads) k_small_finish(const int32_t *__restrict__ dout,
+                                                                const int32_t *__restrict__ din, int B,
+                                                                const __int128 *__restrict__ lpart,
+                                                                int32_t *__restrict__ dsum, double *__restrict__ rcp,
+                                                                float *__restrict__ rcp32, int64_t E, int64_t N,
+                                                                double *__restrict__ dl) {
+    __shared__ __int128 red[kSmallThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    __int128 f = 0;
+    for (int u = tid; u < B; u += kSmallThreads) {
+        const int64_t d = (int64_t)dout[u] + din[u];
+        dsum[u] = (int32_t)d;
+        rcp[u] = 1.0 / ((double)d + (double)B);
+        rcp32[u] = 1.0f / ((float)d + (float)B);
+    }
+    for (int q = tid; q < 2 * B; q += kSmallThreads) f += lpart[q];
+    f = warp_sum_128(f);
+    if (lane == 0) red[w] = f;
+    __syncthreads();
+    if (tid == 0) {
+        __int128 L = 0;
+        for (int q = 0; q < kSmallThreads / 32; ++q) L += red[q];
+        dl[0] = dl_eq2(E, N, B, fix_to_double(L));
+    }
+}
+
 __global__ void k_run_counts(const uint32_t *__restrict__ start, int64_t nnz, int64_t n, int32_t *__restrict__ val) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e = p + 1 < nnz ? start[p + 1] : (uint32_t)n;
@@ -332,6 +512,7 @@ int ensure_sparse_capacity(sbp_model *m, int32_t B) {
         const int64_t w = std::max(std::max(sort_scratch_words(E), scan_scratch_words(E) + 4),
                                    scan_scratch_words((int64_t)m->g->n + 1) + 4);
         SBP_TRY(alloc(m, &S.scratch, w + 1024));
+        SBP_TRY(alloc(m, &S.nnz_dev, 1));
         S.cap_e = E;
     }
     if (sparse_by_count(B, m->g->m) && S.cap_cells < (int64_t)B * B) {
@@ -389,7 +570,7 @@ int sort_and_encode(sbp_model *m, int bits, int64_t *nnz_out) {
 // per-block arrays.  One host read-back (the nonzero count) per rebuild.
 // after_pass: m->bnew holds the previous assignment, and cell counts kept
 // from the previous rebuild may be updated from the moves.
-int rebuild_sparse(sbp_model *m, bool after_pass) {
+int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
     const sbp_graph *g = m->g;
     sbp_model::Sparse &S = m->sp;
     const int B = m->B;
@@ -397,6 +578,31 @@ int rebuild_sparse(sbp_model *m, bool after_pass) {
     cudaStream_t st = m->stream;
     const int cap = 152 * 8;
     uint32_t *sscr = S.scratch + 4;
+    *dl_done = false;
+    if (sparse_by_count(B, E) && B <= kSmallRowsB && E < kMaxTable) {
+        // counting sort over the B x B keys, then everything in one CTA
+        if (after_pass && S.cells_B == B)
+            SBP_TRY(update_cells(m, S.cells));
+        else
+            SBP_TRY(count_cells(m, S.cells));
+        S.cells_B = B;
+        uint32_t *rlen = S.scratch + 8, *clen = rlen + kSmallRowsB;
+        __int128 *lpart = reinterpret_cast<__int128 *>(S.scratch + 8 + 2 * kSmallRowsB + 8);
+        const int wgrid = (int)((2 * (int64_t)B * 32 + kT - 1) / kT);
+        k_small_lengths<<<wgrid, kT, 0, st>>>(S.cells, B, rlen, clen);
+        SBP_LAUNCHED();
+        k_small_offsets<<<1, kSmallThreads, 0, st>>>(rlen, clen, B, S.rp, S.cp, S.hoff, S.nnz_dev);
+        SBP_LAUNCHED();
+        k_small_fill<<<wgrid, kT, 0, st>>>(S.cells, B, S.rp, S.cp, S.hoff, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv,
+                                           S.cpre, S.hk, S.hv, m->dout, m->din, m->T, lpart, m->status);
+        SBP_LAUNCHED();
+        k_small_finish<<<1, kSmallThreads, 0, st>>>(m->dout, m->din, B, lpart, m->dsum, m->rcp, m->rcp32, E, g->n,
+                                                    m->dl);
+        SBP_LAUNCHED();
+        S.nnz = -1;  // on the device until someone asks
+        *dl_done = true;
+        return SBP_OK;
+    }
     // 1-3. the nonzeros of M in row order: CSR offsets, columns, counts,
     // in-row prefixes, dout
     int64_t nnz = 0;
@@ -467,10 +673,22 @@ int rebuild_sparse(sbp_model *m, bool after_pass) {
     return SBP_OK;
 }
 
+int64_t sparse_nnz(sbp_model *m) {
+    if (m->sp.nnz >= 0) return m->sp.nnz;
+    int64_t h = 0;
+    if (cudaMemcpyAsync(&h, m->sp.nnz_dev, 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    m->sp.nnz = h;
+    return h;
+}
+
 void free_sparse(sbp_model *m) {
     sbp_model::Sparse &S = m->sp;
     void *ps[] = {S.key0, S.key1, S.start, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv, S.cpre, S.ckey0,
-                  S.ckey1, S.cval0, S.cval1, S.hk, S.hv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells};
+                  S.ckey1, S.cval0, S.cval1, S.hk, S.hv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells, S.nnz_dev};
     for (void *p : ps) model_free(p, m->stream);
     S = sbp_model::Sparse();
 }
