@@ -286,13 +286,15 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
                              uint32_t *__restrict__ rpre, int32_t *__restrict__ cr, int32_t *__restrict__ cv,
                              uint32_t *__restrict__ cpre, int32_t *__restrict__ hk, int32_t *__restrict__ hv,
                              int32_t *__restrict__ dout, int32_t *__restrict__ din, const __int128 *__restrict__ T,
-                             __int128 *__restrict__ lpart, int32_t *__restrict__ status) {
+                             int64_t XT, __int128 *__restrict__ lpart, double *__restrict__ lfb,
+                             int32_t *__restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (w >= 2 * B) return;
     const bool col = w >= B;
     const int i = col ? w - B : w;
     __int128 f = 0;
+    double fb = 0.0;  // counts beyond the table, in FP64
     uint32_t p = col ? cp[i] : rp[i], carry = 0;
     const uint32_t off = col ? 0u : hoff[i], cap = col ? 0u : hoff[i + 1] - off;
     if (!col)
@@ -319,7 +321,8 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
                 rv[q] = (int32_t)v;
                 rowof[q] = i;
                 rpre[q] = carry + incl;
-                f += T[v];
+                if ((int64_t)v < XT) f += T[v];
+                else fb += (double)v * log((double)v);
                 uint32_t h = sparse_hash(j) & (cap - 1);
                 bool done = false;
                 for (uint32_t t = 0; t < cap; ++t) {
@@ -337,9 +340,13 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
         carry += __shfl_sync(0xffffffffu, incl, 31);
     }
     f = warp_sum_128(f);
+    fb = warp_sum(fb);
     if (lane == 0) {
         (col ? din : dout)[i] = (int32_t)carry;
-        lpart[w] = f - T[carry];
+        if ((int64_t)carry < XT) f -= T[carry];
+        else fb -= (double)carry * log((double)carry);
+        lpart[w] = f;
+        lfb[w] = fb;
     }
 }
 
@@ -348,26 +355,40 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
 __global__ void __launch_bounds__(kSmallThreads) k_small_finish(const int32_t *__restrict__ dout,
                                                                 const int32_t *__restrict__ din, int B,
                                                                 const __int128 *__restrict__ lpart,
+                                                                const double *__restrict__ lfb,
                                                                 int32_t *__restrict__ dsum, double *__restrict__ rcp,
                                                                 float *__restrict__ rcp32, int64_t E, int64_t N,
                                                                 double *__restrict__ dl) {
     __shared__ __int128 red[kSmallThreads / 32];
+    __shared__ double redd[kSmallThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     __int128 f = 0;
+    double fb = 0.0;
     for (int u = tid; u < B; u += kSmallThreads) {
         const int64_t d = (int64_t)dout[u] + din[u];
         dsum[u] = (int32_t)d;
         rcp[u] = 1.0 / ((double)d + (double)B);
         rcp32[u] = 1.0f / ((float)d + (float)B);
     }
-    for (int q = tid; q < 2 * B; q += kSmallThreads) f += lpart[q];
+    for (int q = tid; q < 2 * B; q += kSmallThreads) {
+        f += lpart[q];
+        fb += lfb[q];
+    }
     f = warp_sum_128(f);
-    if (lane == 0) red[w] = f;
+    fb = warp_sum(fb);
+    if (lane == 0) {
+        red[w] = f;
+        redd[w] = fb;
+    }
     __syncthreads();
     if (tid == 0) {
         __int128 L = 0;
-        for (int q = 0; q < kSmallThreads / 32; ++q) L += red[q];
-        dl[0] = dl_eq2(E, N, B, fix_to_double(L));
+        double Lb = 0.0;
+        for (int q = 0; q < kSmallThreads / 32; ++q) {
+            L += red[q];
+            Lb += redd[q];
+        }
+        dl[0] = dl_eq2(E, N, B, fix_to_double(L) + Lb);
     }
 }
 
@@ -579,7 +600,7 @@ int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
     const int cap = 152 * 8;
     uint32_t *sscr = S.scratch + 4;
     *dl_done = false;
-    if (sparse_by_count(B, E) && B <= kSmallRowsB && E < kMaxTable) {
+    if (sparse_by_count(B, E) && B <= kSmallRowsB) {
         // counting sort over the B x B keys, then everything in one CTA
         if (after_pass && S.cells_B == B)
             SBP_TRY(update_cells(m, S.cells));
@@ -588,16 +609,17 @@ int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
         S.cells_B = B;
         uint32_t *rlen = S.scratch + 8, *clen = rlen + kSmallRowsB;
         __int128 *lpart = reinterpret_cast<__int128 *>(S.scratch + 8 + 2 * kSmallRowsB + 8);
+        double *lfb = reinterpret_cast<double *>(lpart + 2 * kSmallRowsB);
         const int wgrid = (int)((2 * (int64_t)B * 32 + kT - 1) / kT);
         k_small_lengths<<<wgrid, kT, 0, st>>>(S.cells, B, rlen, clen);
         SBP_LAUNCHED();
         k_small_offsets<<<1, kSmallThreads, 0, st>>>(rlen, clen, B, S.rp, S.cp, S.hoff, S.nnz_dev);
         SBP_LAUNCHED();
         k_small_fill<<<wgrid, kT, 0, st>>>(S.cells, B, S.rp, S.cp, S.hoff, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv,
-                                           S.cpre, S.hk, S.hv, m->dout, m->din, m->T, lpart, m->status);
+                                           S.cpre, S.hk, S.hv, m->dout, m->din, m->T, m->XT, lpart, lfb, m->status);
         SBP_LAUNCHED();
-        k_small_finish<<<1, kSmallThreads, 0, st>>>(m->dout, m->din, B, lpart, m->dsum, m->rcp, m->rcp32, E, g->n,
-                                                    m->dl);
+        k_small_finish<<<1, kSmallThreads, 0, st>>>(m->dout, m->din, B, lpart, lfb, m->dsum, m->rcp, m->rcp32, E,
+                                                    g->n, m->dl);
         SBP_LAUNCHED();
         S.nnz = -1;  // on the device until someone asks
         *dl_done = true;
