@@ -132,7 +132,7 @@ struct ModelDev {
     const int32_t *rc, *cr;           // column of each row entry, row of each column entry
     const int32_t *rv, *cv;           // their counts
     const uint32_t *rpre, *cpre;      // inclusive count prefixes inside each row / column
-    const int32_t *hk, *hv;           // table keys (-1 empty) and counts
+    const int2 *hkv;                  // table slots: (key, count), key -1 when empty
     int32_t *status;
     DevCounters *counters;
 };
@@ -149,7 +149,7 @@ struct sbp_model {
         uint32_t *rpre = nullptr, *cpre = nullptr;
         uint32_t *ckey0 = nullptr, *ckey1 = nullptr;
         uint64_t *cval0 = nullptr, *cval1 = nullptr;
-        int32_t *hk = nullptr, *hv = nullptr;
+        int2 *hkv = nullptr;  // per-row open-addressing slots (key, count)
         uint32_t *rp = nullptr, *cp = nullptr, *hoff = nullptr, *cnt = nullptr;
         int32_t *cells = nullptr;  // B x B counts of the counting-sort rebuild
         int64_t cap_cells = 0;
@@ -345,9 +345,9 @@ __device__ __forceinline__ int sparse_at(const ModelDev &md, int r, int c) {
     const uint32_t off = md.hoff[r], cap = md.hoff[r + 1] - off;
     uint32_t h = sparse_hash(c) & (cap - 1);
     for (uint32_t q = 0; q < cap; ++q) {
-        const int k = md.hk[off + h];
-        if (k == c) return md.hv[off + h];
-        if (k < 0) return 0;
+        const int2 kv = md.hkv[off + h];  // key and count in one load
+        if (kv.x == c) return kv.y;
+        if (kv.x < 0) return 0;
         h = (h + 1) & (cap - 1);
     }
     return 0;

@@ -1120,8 +1120,7 @@ ModelDev model_dev(sbp_model *m) {
     d.cv = m->sp.cv;
     d.rpre = m->sp.rpre;
     d.cpre = m->sp.cpre;
-    d.hk = m->sp.hk;
-    d.hv = m->sp.hv;
+    d.hkv = m->sp.hkv;
     d.status = m->status;
     d.counters = m->counters;
     return d;

@@ -12,7 +12,8 @@
 //   4. CSC: a stable radix sort of the nonzeros by column keeps ascending
 //      rows inside each column; offsets and prefixes as for the rows;
 //   5. per-row open-addressing tables (capacity the power of two at least
-//      twice the row's length) for M[r][c] lookups;
+//      twice the row's length; each slot holds the key and the count, so a
+//      probe is one 8-byte load) for M[r][c] lookups;
 //   6. block degrees from the last prefix of each row / column; DL as an
 //      exact fixed-point sum over the nonzeros.
 #include <algorithm>
@@ -284,7 +285,7 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
                              const uint32_t *__restrict__ cp, const uint32_t *__restrict__ hoff,
                              int32_t *__restrict__ rc, int32_t *__restrict__ rv, int32_t *__restrict__ rowof,
                              uint32_t *__restrict__ rpre, int32_t *__restrict__ cr, int32_t *__restrict__ cv,
-                             uint32_t *__restrict__ cpre, int32_t *__restrict__ hk, int32_t *__restrict__ hv,
+                             uint32_t *__restrict__ cpre, int2 *__restrict__ hkv,
                              int32_t *__restrict__ dout, int32_t *__restrict__ din, const __int128 *__restrict__ T,
                              int64_t XT, __int128 *__restrict__ lpart, double *__restrict__ lfb,
                              int32_t *__restrict__ status) {
@@ -298,7 +299,7 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
     uint32_t p = col ? cp[i] : rp[i], carry = 0;
     const uint32_t off = col ? 0u : hoff[i], cap = col ? 0u : hoff[i + 1] - off;
     if (!col)
-        for (uint32_t q = lane; q < cap; q += 32) hk[off + q] = -1;
+        for (uint32_t q = lane; q < cap; q += 32) hkv[off + q] = make_int2(-1, 0);
     __syncwarp();
     for (int j0 = 0; j0 < B; j0 += 32) {
         const int j = j0 + lane;
@@ -326,8 +327,8 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
                 uint32_t h = sparse_hash(j) & (cap - 1);
                 bool done = false;
                 for (uint32_t t = 0; t < cap; ++t) {
-                    if (atomicCAS(&hk[off + h], -1, j) == -1) {
-                        hv[off + h] = (int32_t)v;
+                    if (atomicCAS(&hkv[off + h].x, -1, j) == -1) {
+                        hkv[off + h].y = (int32_t)v;
                         done = true;
                         break;
                     }
@@ -454,7 +455,7 @@ __global__ void k_hash_caps(const uint32_t *__restrict__ ptr, int64_t R, uint32_
 
 __global__ void k_hash_fill(const uint32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                             const int32_t *__restrict__ val, const int32_t *__restrict__ rowof, int64_t nnz,
-                            const uint32_t *__restrict__ hoff, int32_t *__restrict__ hk, int32_t *__restrict__ hv,
+                            const uint32_t *__restrict__ hoff, int2 *__restrict__ hkv,
                             int32_t *__restrict__ status) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int r = rowof[p], c = col[p];
@@ -462,8 +463,8 @@ __global__ void k_hash_fill(const uint32_t *__restrict__ ptr, const int32_t *__r
         uint32_t h = sparse_hash(c) & (cap - 1);
         bool done = false;
         for (uint32_t q = 0; q < cap; ++q) {
-            if (atomicCAS(&hk[off + h], -1, c) == -1) {
-                hv[off + h] = val[p];
+            if (atomicCAS(&hkv[off + h].x, -1, c) == -1) {
+                hkv[off + h].y = val[p];
                 done = true;
                 break;
             }
@@ -528,8 +529,7 @@ int ensure_sparse_capacity(sbp_model *m, int32_t B) {
         SBP_TRY(alloc(m, &S.ckey1, E));
         SBP_TRY(alloc(m, &S.cval0, E));
         SBP_TRY(alloc(m, &S.cval1, E));
-        SBP_TRY(alloc(m, &S.hk, 4 * E + 2 * (int64_t)m->g->n));
-        SBP_TRY(alloc(m, &S.hv, 4 * E + 2 * (int64_t)m->g->n));
+        SBP_TRY(alloc(m, &S.hkv, 4 * E + 2 * (int64_t)m->g->n));
         const int64_t w = std::max(std::max(sort_scratch_words(E), scan_scratch_words(E) + 4),
                                    scan_scratch_words((int64_t)m->g->n + 1) + 4);
         SBP_TRY(alloc(m, &S.scratch, w + 1024));
@@ -616,7 +616,7 @@ int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
         k_small_offsets<<<1, kSmallThreads, 0, st>>>(rlen, clen, B, S.rp, S.cp, S.hoff, S.nnz_dev);
         SBP_LAUNCHED();
         k_small_fill<<<wgrid, kT, 0, st>>>(S.cells, B, S.rp, S.cp, S.hoff, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv,
-                                           S.cpre, S.hk, S.hv, m->dout, m->din, m->T, m->XT, lpart, lfb, m->status);
+                                           S.cpre, S.hkv, m->dout, m->din, m->T, m->XT, lpart, lfb, m->status);
         SBP_LAUNCHED();
         k_small_finish<<<1, kSmallThreads, 0, st>>>(m->dout, m->din, B, lpart, lfb, m->dsum, m->rcp, m->rcp32, E,
                                                     g->n, m->dl);
@@ -684,9 +684,9 @@ int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
     SBP_LAUNCHED();
     SBP_TRY(exclusive_scan_u32(S.cnt, S.hoff, (int64_t)B + 1, nullptr, sscr, st));
     // capacities are powers of two below 4 len + 2 per row
-    SBP_CUDA(cudaMemsetAsync(S.hk, 0xff, (size_t)(4 * nnz + 2 * (int64_t)B) * 4, st));
+    SBP_CUDA(cudaMemsetAsync(S.hkv, 0xff, (size_t)(4 * nnz + 2 * (int64_t)B) * sizeof(int2), st));
     if (nnz > 0) {
-        k_hash_fill<<<grid_of(nnz, cap), kT, 0, st>>>(S.rp, S.rc, S.rv, S.rowof, nnz, S.hoff, S.hk, S.hv, m->status);
+        k_hash_fill<<<grid_of(nnz, cap), kT, 0, st>>>(S.rp, S.rc, S.rv, S.rowof, nnz, S.hoff, S.hkv, m->status);
         SBP_LAUNCHED();
     }
     // 6. per-block scalars
@@ -710,7 +710,7 @@ int64_t sparse_nnz(sbp_model *m) {
 void free_sparse(sbp_model *m) {
     sbp_model::Sparse &S = m->sp;
     void *ps[] = {S.key0, S.key1, S.start, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv, S.cpre, S.ckey0,
-                  S.ckey1, S.cval0, S.cval1, S.hk, S.hv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells, S.nnz_dev};
+                  S.ckey1, S.cval0, S.cval1, S.hkv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells, S.nnz_dev};
     for (void *p : ps) model_free(p, m->stream);
     S = sbp_model::Sparse();
 }
