@@ -172,6 +172,18 @@ int sbp_nodal_sweep(sbp_model_t *m, uint64_t sweep_id, int64_t v_begin, int64_t 
  * NULL. */
 int sbp_nodal_decide(sbp_model_t *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
 
+/* Exchange of the pending assignment between ranks that decided disjoint
+ * ranges (the allgather of the new labels in Alg. 5).  sbp_get_pending copies
+ * the pending labels of [v_begin, v_end) to out (v_end - v_begin entries,
+ * host or device; synchronises the model's stream).  sbp_set_pending writes
+ * them from in (host or device) so that the next sbp_commit applies them.
+ * Labels must lie in [0, B): host input is checked before the copy
+ * (SBP_EINVAL, nothing written); on device input a label outside it keeps
+ * the vertex in its current block and the next status check reports
+ * SBP_EINVAL.  Errors: SBP_EINVAL for a NULL pointer or a bad range. */
+int sbp_get_pending(const sbp_model_t *m, int64_t v_begin, int64_t v_end, int32_t *out);
+int sbp_set_pending(sbp_model_t *m, int64_t v_begin, int64_t v_end, const int32_t *in);
+
 /* Applies the pending assignment, rebuilds M and DL, and resets the pending
  * assignment to the new b.  stats may be NULL (counters accumulated by the
  * decide calls since the previous commit). */

@@ -24,7 +24,7 @@ __all__ = [
     "SbpError", "Params", "SweepStats", "Trace", "load", "lib", "sbp_default_params", "sbp_last_error",
     "sbp_load_graph", "sbp_free_graph", "sbp_graph_info", "sbp_build_blockmodel", "sbp_set_assignment",
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
-    "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_B", "sbp_get_dl",
+    "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_pending", "sbp_set_pending", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
     "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_dxlogx32_check", "sbp_default_batch_options", "sbp_partition_batch",
     "BatchOptions", "BatchResult", "BatchStats", "partition_batch", "Server",
@@ -166,6 +166,8 @@ def load(path: str | None = None):
         "sbp_compact": (C.c_int, [vp, P(i32)]),
         "sbp_partition": (C.c_int, [vp, P(Params), vp, vp, P(i32), P(f64), P(i64)]),
         "sbp_get_assignment": (C.c_int, [vp, vp]),
+        "sbp_get_pending": (C.c_int, [vp, i64, i64, vp]),
+        "sbp_set_pending": (C.c_int, [vp, i64, i64, vp]),
         "sbp_get_B": (C.c_int, [vp, P(i32)]),
         "sbp_get_dl": (C.c_int, [vp, vp]),
         "sbp_get_blockmodel_dense": (C.c_int, [vp, vp]),
@@ -335,6 +337,14 @@ def sbp_partition_batch(graphs: list[int], b_outs, params: Params | None = None,
 
 def sbp_get_assignment(m: int, b_out) -> None:
     _check(lib().sbp_get_assignment(m, _ptr(b_out, np.int32)))
+
+
+def sbp_get_pending(m: int, v_begin: int, v_end: int, out) -> None:
+    _check(lib().sbp_get_pending(m, v_begin, v_end, _ptr(out, np.int32)))
+
+
+def sbp_set_pending(m: int, v_begin: int, v_end: int, labels) -> None:
+    _check(lib().sbp_set_pending(m, v_begin, v_end, _ptr(labels, np.int32)))
 
 
 def sbp_get_B(m: int) -> int:
@@ -559,13 +569,5 @@ class Model:
         return sbp_nodal_sweep(self.h, sweep_id, v_begin, self.g.n if v_end is None else v_end, stats)
 
 
-def deal_vertices(degrees: np.ndarray, world: int, rank: int) -> np.ndarray:
-    """Vertex ids a rank handles in a sharded nodal pass (Section III-B):
-    vertices sorted by degree are cut into chunks of 2*world; rank r takes
-    the r-th highest and the r-th lowest of each chunk."""
-    order = np.argsort(-np.asarray(degrees), kind="stable")
-    n = order.size
-    pos = np.arange(n)
-    chunk_pos = pos % (2 * world)
-    mine = (chunk_pos == rank) | (chunk_pos == 2 * world - 1 - rank)
-    return np.sort(order[mine])
+from .shard import deal_vertices  # noqa: E402  (Section III-B dealing)
+

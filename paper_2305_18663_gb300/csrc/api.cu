@@ -324,6 +324,51 @@ extern "C" int sbp_nodal_decide(sbp_model_t *m, uint64_t sweep_id, int64_t v_beg
     return launch_decide(m, sweep_id, v_begin, v_end, trace);
 }
 
+namespace sbp {
+namespace {
+
+// pending labels from device memory: out-of-range labels keep the vertex in
+// its block and record SBP_EINVAL
+__global__ void k_set_pending(const int32_t *__restrict__ in, int64_t v_begin, int64_t count, int32_t B,
+                              const int32_t *__restrict__ b, int32_t *__restrict__ bnew, int32_t *status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t lab = in[i];
+        const bool ok = lab >= 0 && lab < B;
+        bnew[v_begin + i] = ok ? lab : b[v_begin + i];
+        if (!ok) record_status(status, SBP_EINVAL);
+    }
+}
+
+}  // namespace
+}  // namespace sbp
+
+extern "C" int sbp_get_pending(const sbp_model_t *m, int64_t v_begin, int64_t v_end, int32_t *out) {
+    if (!m || !out) return fail(SBP_EINVAL, "sbp_get_pending: NULL argument");
+    if (v_begin < 0 || v_end > m->g->n || v_begin > v_end) return fail(SBP_EINVAL, "sbp_get_pending: bad vertex range");
+    if (v_begin < v_end)
+        SBP_CUDA(cudaMemcpyAsync(out, m->bnew + v_begin, (size_t)(v_end - v_begin) * 4, kind_from_dev(out), m->stream));
+    return check_status(m);
+}
+
+extern "C" int sbp_set_pending(sbp_model_t *m, int64_t v_begin, int64_t v_end, const int32_t *in) {
+    if (!m || !in) return fail(SBP_EINVAL, "sbp_set_pending: NULL argument");
+    if (v_begin < 0 || v_end > m->g->n || v_begin > v_end) return fail(SBP_EINVAL, "sbp_set_pending: bad vertex range");
+    const int64_t count = v_end - v_begin;
+    if (count == 0) return SBP_OK;
+    if (is_device_ptr(in)) {
+        const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
+        k_set_pending<<<grid, 256, 0, m->stream>>>(in, v_begin, count, m->B, m->b, m->bnew, m->status);
+        SBP_LAUNCHED();
+        return SBP_OK;
+    }
+    for (int64_t i = 0; i < count; ++i)
+        if (in[i] < 0 || in[i] >= m->B)
+            return fail(SBP_EINVAL, "sbp_set_pending: label out of [0, B) at vertex " + std::to_string(v_begin + i));
+    SBP_CUDA(cudaMemcpyAsync(m->bnew + v_begin, in, (size_t)count * 4, cudaMemcpyHostToDevice, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    return SBP_OK;
+}
+
 extern "C" int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats) {
     if (!m) return fail(SBP_EINVAL, "sbp_commit: NULL model");
     std::swap(m->b, m->bnew);
