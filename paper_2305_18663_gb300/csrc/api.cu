@@ -261,6 +261,11 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
                   m->rcp,      m->rcp32,  m->dsum,     m->dl,      m->partials, m->counters, m->status,
                   m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount, m->skip};
     for (void *p : ps) model_free(p, st);
+    for (int i = 0; i < 2; ++i) {
+        if (m->side[i]) cudaStreamDestroy(m->side[i]);
+        if (m->join_ev[i]) cudaEventDestroy(m->join_ev[i]);
+    }
+    if (m->fork_ev) cudaEventDestroy(m->fork_ev);
     free_sparse(m);
     pinned_put(m->pinned);
     if (st) cudaStreamSynchronize(st);

@@ -184,6 +184,10 @@ struct sbp_model {
     // nodal pass: proposals with s != r, in three lists by degree
     void *movers = nullptr;
     unsigned *mcount = nullptr;
+    // side streams of the decision pass: the three degree groups' kernels
+    // run concurrently so that each one's tail is filled by the others
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
     uint8_t *skip = nullptr;  // the hybrid pass's sequential vertices (n flags)
     int32_t skip_h = -1;      // the h skip was built for
     // pinned host mirror for small read-backs

@@ -1128,37 +1128,45 @@ ModelDev model_dev(sbp_model *m) {
 
 namespace {
 
+// graphs with at least this many edges run the three degree groups'
+// kernels on three streams
+constexpr int64_t kSideStreamEdges = int64_t(1) << 22;
+
+// streams of the three groups: the model's own one for the movers above 128
+// edges (launched first: the longest tail), side streams for the others
+// (forked after k_propose, joined back by join_evals)
+int fork_evals(sbp_model *m, cudaStream_t st[3]) {
+    st[0] = st[1] = st[2] = m->stream;
+    if (m->g->m < kSideStreamEdges) return SBP_OK;
+    if (!m->fork_ev) {
+        for (int i = 0; i < 2; ++i) {
+            SBP_CUDA(cudaStreamCreateWithFlags(&m->side[i], cudaStreamNonBlocking));
+            SBP_CUDA(cudaEventCreateWithFlags(&m->join_ev[i], cudaEventDisableTiming));
+        }
+        SBP_CUDA(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
+    }
+    SBP_CUDA(cudaEventRecord(m->fork_ev, m->stream));
+    for (int i = 0; i < 2; ++i) SBP_CUDA(cudaStreamWaitEvent(m->side[i], m->fork_ev, 0));
+    st[0] = m->side[1];
+    st[1] = m->side[0];
+    return SBP_OK;
+}
+
+int join_evals(sbp_model *m) {
+    if (m->g->m < kSideStreamEdges || !m->fork_ev) return SBP_OK;
+    for (int i = 0; i < 2; ++i) {
+        SBP_CUDA(cudaEventRecord(m->join_ev[i], m->side[i]));
+        SBP_CUDA(cudaStreamWaitEvent(m->stream, m->join_ev[i], 0));
+    }
+    return SBP_OK;
+}
+
 // the evaluation kernels of the three degree groups (after k_propose)
 template <bool DL32>
-int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
+int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t st[3]) {
     const sbp_graph *g = m->g;
     const int B = m->B;
-    // movers with k <= 32: batches of 32 per warp
-    if (g->bin[2] > g->bin[1]) {
-        const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
-        const size_t smem = (size_t)wb * kWarpsPerCta;
-        SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<0, DL32>, smem));
-        k_eval_batch<0, DL32><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 0, wb);
-        SBP_LAUNCHED();
-    }
     auto warp_smem = [](int cap, int nwarps) { return (size_t)nwarps * cap * 10 + (size_t)nwarps * 4 + 16; };
-    // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
-    // small, otherwise one warp each with a 256-slot table
-    if (g->bin[3] > g->bin[2]) {
-        if (B <= kDirectMaxB) {
-            const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
-            const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
-            const size_t smem = (size_t)wb * nwarps;
-            SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32>, smem));
-            k_eval_batch<1, DL32><<<sms * 3, nwarps * 32, smem, m->stream>>>(a, 1, wb);
-            SBP_LAUNCHED();
-        } else {
-            const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
-            SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp<DL32>, smem));
-            k_eval_warp<DL32><<<sms * 3, kWarpsPerCta * 32, smem, m->stream>>>(a, 1, kWarpCap, 8, 32);
-            SBP_LAUNCHED();
-        }
-    }
     // movers with k > 128: per-warp direct-mapped counts while B is small,
     // else per-warp tables sized for min(max degree, B) distinct blocks while
     // they fit, one CTA per mover beyond that
@@ -1167,7 +1175,7 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
         const int nwarps = warp_words * 4 * kWarpsPerCta <= 64 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
         const size_t smem = (size_t)warp_words * 4 * nwarps;
         SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp_direct<DL32>, smem));
-        k_eval_warp_direct<DL32><<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, warp_words);
+        k_eval_warp_direct<DL32><<<sms * 4, nwarps * 32, smem, st[2]>>>(a, 2, warp_words);
         SBP_LAUNCHED();
     } else if (g->bin[4] > g->bin[3]) {
         const int64_t dmax = g->max_deg < B ? g->max_deg : B;
@@ -1179,17 +1187,51 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
             const int nwarps = cap <= 2048 ? 8 : 4;
             const size_t smem = warp_smem(cap, nwarps);
             SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp<DL32>, smem));
-            k_eval_warp<DL32><<<sms * 4, nwarps * 32, smem, m->stream>>>(a, 2, cap, cap_log2, 1);
+            k_eval_warp<DL32><<<sms * 4, nwarps * 32, smem, st[2]>>>(a, 2, cap, cap_log2, 1);
             SBP_LAUNCHED();
         } else {
             const size_t smem = (size_t)cap * (8 + 4 + 4);
             if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
             SBP_TRY(ensure_dyn_smem((const void *)k_eval_cta<DL32>, smem));
-            k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, m->stream>>>(a, 2, cap, cap_log2);
+            k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, st[2]>>>(a, 2, cap, cap_log2);
+            SBP_LAUNCHED();
+        }
+    }
+    // movers with k <= 32: batches of 32 per warp
+    if (g->bin[2] > g->bin[1]) {
+        const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
+        const size_t smem = (size_t)wb * kWarpsPerCta;
+        SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<0, DL32>, smem));
+        k_eval_batch<0, DL32><<<sms * 3, kWarpsPerCta * 32, smem, st[0]>>>(a, 0, wb);
+        SBP_LAUNCHED();
+    }
+    // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
+    // small, otherwise one warp each with a 256-slot table
+    if (g->bin[3] > g->bin[2]) {
+        if (B <= kDirectMaxB) {
+            const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
+            const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
+            const size_t smem = (size_t)wb * nwarps;
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32>, smem));
+            k_eval_batch<1, DL32><<<sms * 3, nwarps * 32, smem, st[1]>>>(a, 1, wb);
+            SBP_LAUNCHED();
+        } else {
+            const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp<DL32>, smem));
+            k_eval_warp<DL32><<<sms * 3, kWarpsPerCta * 32, smem, st[1]>>>(a, 1, kWarpCap, 8, 32);
             SBP_LAUNCHED();
         }
     }
     return SBP_OK;
+}
+
+template <bool DL32>
+int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
+    cudaStream_t st[3];
+    SBP_TRY(fork_evals(m, st));
+    const int rc = launch_groups<DL32>(m, a, sms, st);
+    const int rj = join_evals(m);  // joined on every path
+    return rc != SBP_OK ? rc : rj;
 }
 
 }  // namespace

@@ -478,3 +478,43 @@ def test_incremental_commit_equals_full_rebuild(dmax):
         assert inc.dl() == full.dl()
     om.set_b(316, inc.assignment())
     check_blockmodel(inc, om)
+
+
+# ---------------------------------------------------------------------------
+# the full-size workload in the configuration the benchmark times: 1M
+# vertices, 20M edges, B = 316, FP32 Delta DL terms with the exact recheck,
+# three warm-up sweeps, then every vertex of one sweep against the oracle
+
+@pytest.fixture(scope="module")
+def full_size():
+    g = make_config("dcsbm_1m", seed=0)
+    b0 = perturb(g.planted, 316, 0.3, seed=0)
+    return g, b0, P.Graph(g.n, g.src, g.dst), O.Graph(g.n, g.src, g.dst)
+
+
+@pytest.mark.parametrize("m_form", ["sparse", "dense"])
+def test_full_size_sweep_in_benchmark_configuration(full_size, m_form):
+    g, b0, pg, G = full_size
+    B, seed = 316, 0
+    params = P.Params.default(seed=seed, dense_max_B=1 if m_form == "sparse" else 4096, dl_fp32=1)
+    pm = P.Model(pg, B, b0, params, torch.cuda.current_stream())
+    for k in range(3):
+        P.sbp_nodal_decide(pm.h, k, 0, g.n)
+        P.sbp_commit(pm.h, stats=False)
+    bcur = pm.assignment()
+    om = O.Model(G, B, bcur)
+    check_blockmodel(pm, om)
+    gd = gpu_decide(pm, g.n, 3)
+    od = om.nodal_decide(seed, 3, 3.0, nthreads=NT)
+    margin = compare_decisions(od, gd, bcur, np.arange(g.n))
+    moved = int(((gd[0] != bcur) & ((gd[1] & 1) != 0)).sum())
+    assert moved > 100_000  # the sweep exercises every degree group
+    st = P.sbp_commit(pm.h)
+    bg = pm.assignment()
+    want = od.b_new.copy()
+    want[margin] = bg[margin]
+    assert np.array_equal(bg, want)
+    assert st.n_accepted == int(((gd[1] & 2) != 0).sum())
+    om.set_b(B, bg)
+    check_blockmodel(pm, om)
+    pm.close()
