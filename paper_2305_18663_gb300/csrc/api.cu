@@ -259,7 +259,8 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     if (st) cudaStreamSynchronize(st);
     void *ps[] = {m->b,        m->bnew,   m->M,        m->P,       m->Pc,     m->dout,  m->din,
                   m->rcp,      m->rcp32,  m->dsum,     m->dl,      m->partials, m->counters, m->status,
-                  m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount, m->skip};
+                  m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount, m->skip,
+                  m->items};
     for (void *p : ps) model_free(p, st);
     for (int i = 0; i < 2; ++i) {
         if (m->side[i]) cudaStreamDestroy(m->side[i]);
@@ -360,6 +361,7 @@ extern "C" int sbp_set_pending(sbp_model_t *m, int64_t v_begin, int64_t v_end, c
     if (v_begin < 0 || v_end > m->g->n || v_begin > v_end) return fail(SBP_EINVAL, "sbp_set_pending: bad vertex range");
     const int64_t count = v_end - v_begin;
     if (count == 0) return SBP_OK;
+    m->list_ok = false;  // the accepted-move list no longer holds every change
     if (is_device_ptr(in)) {
         const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
         k_set_pending<<<grid, 256, 0, m->stream>>>(in, v_begin, count, m->B, m->b, m->bnew, m->status);
@@ -378,7 +380,10 @@ extern "C" int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats) {
     if (!m) return fail(SBP_EINVAL, "sbp_commit: NULL model");
     std::swap(m->b, m->bnew);
     SBP_CUDA(cudaMemcpyAsync(m->dl + 1, m->dl, 8, cudaMemcpyDeviceToDevice, m->stream));
-    SBP_TRY(commit_blockmodel(m));
+    const int rc = commit_blockmodel(m);
+    m->list_ok = true;
+    m->decided.clear();
+    SBP_TRY(rc);
     if (stats) SBP_TRY(read_stats(m, stats));
     SBP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream));
     return SBP_OK;

@@ -195,6 +195,58 @@ __global__ void __launch_bounds__(kThreads) k_delta_dense(GraphDev g, const int3
     }
 }
 
+// The same apply step driven by the accepted-move list: an item is one
+// kMoveChunk-edge slice of the concatenated (out, in) row of a moved vertex,
+// so hubs are spread over many warps and no warp scans unmoved vertices.
+// Lane j of the warp takes edges j, j + 32, ... of the slice, all loads in
+// flight together.
+__global__ void __launch_bounds__(kThreads) k_delta_items(GraphDev g, const int2 *__restrict__ items,
+                                                          const DevCounters *__restrict__ c, int64_t cap,
+                                                          const int32_t *__restrict__ bnew,
+                                                          const int32_t *__restrict__ bold, int32_t *__restrict__ M,
+                                                          int B, const int32_t *__restrict__ flag) {
+    if (*flag != 1) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)(c->items < (unsigned long long)cap ? c->items : (unsigned long long)cap);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int kPer = kMoveChunk / 32;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+        const int2 it = items[w];
+        const int v = it.x;
+        const int r = bold[v], s = bnew[v];
+        if (r == s) continue;
+        const int o0 = g.op[v], kout = g.op[v + 1] - o0;
+        const int i0 = g.ip[v], k = kout + (g.ip[v + 1] - i0);
+        const int lo = it.y * kMoveChunk;
+        int nb[kPer], t[kPer], u[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int idx = lo + j * 32 + lane;
+            nb[j] = idx < k ? (idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            t[j] = nb[j] >= 0 ? bold[nb[j]] : 0;
+            u[j] = nb[j] >= 0 ? bnew[nb[j]] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int idx = lo + j * 32 + lane;
+            if (nb[j] < 0) continue;
+            if (idx < kout) {
+                // out-edge v -> w: leaves (r, t), enters (s, u)
+                atomicAdd(&M[(size_t)r * B + t[j]], -1);
+                atomicAdd(&M[(size_t)s * B + u[j]], 1);
+            } else if (u[j] == t[j]) {
+                // in-edge w -> v from a vertex that stayed (a moved source
+                // applies it through its own out-row)
+                atomicAdd(&M[(size_t)t[j] * B + r], -1);
+                atomicAdd(&M[(size_t)t[j] * B + s], 1);
+            }
+        }
+    }
+}
+
 __global__ void k_relabel(int32_t *__restrict__ b, int32_t *__restrict__ bnew, int n, const int32_t *__restrict__ map) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int x = map[b[v]];
@@ -303,11 +355,17 @@ int update_cells(sbp_model *m, int32_t *cells) {
         k_hist_dense<<<grid_for((g->m + 3) / 4, kThreads, sms * 8), kThreads, smem, m->stream>>>(g->dev(), m->b, cells, B,
                                                                                                   flag);
         SBP_LAUNCHED();
-        const int64_t n_big = g->n - g->bin[3];
-        const int64_t warps = n_big + (g->n + 31) / 32;
-        k_delta_dense<<<grid_for(warps * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
-            g->dev(), g->order, (int)g->bin[3], (int)n_big, m->b, m->bnew, cells, B, flag);
-        SBP_LAUNCHED();
+        if (m->list_ok && m->items) {
+            k_delta_items<<<sms * 4, kThreads, 0, m->stream>>>(g->dev(), m->items, m->counters, m->cap_items, m->b,
+                                                               m->bnew, cells, B, flag);
+            SBP_LAUNCHED();
+        } else {
+            const int64_t n_big = g->n - g->bin[3];
+            const int64_t warps = n_big + (g->n + 31) / 32;
+            k_delta_dense<<<grid_for(warps * 32, kThreads, 1 << 30), kThreads, 0, m->stream>>>(
+                g->dev(), g->order, (int)g->bin[3], (int)n_big, m->b, m->bnew, cells, B, flag);
+            SBP_LAUNCHED();
+        }
     }
     return SBP_OK;
 }
@@ -356,7 +414,14 @@ int build_blockmodel(sbp_model *m, bool after_pass) {
 
 }  // namespace
 
-int rebuild_blockmodel(sbp_model *m) { return build_blockmodel(m, false); }
+// a rebuild from m->b drops the pending decisions, and with them the
+// accepted-move list
+int rebuild_blockmodel(sbp_model *m) {
+    m->list_ok = true;
+    m->decided.clear();
+    SBP_CUDA(cudaMemsetAsync(&m->counters->items, 0, sizeof(unsigned long long), m->stream));
+    return build_blockmodel(m, false);
+}
 
 // P, Pc, degrees and reciprocals of a dense model from its M
 int launch_prefix(sbp_model *m) {

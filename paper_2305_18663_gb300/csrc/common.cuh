@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "sbp.h"
 
@@ -107,7 +109,12 @@ namespace sbp {
 // device-side counters of a decision pass: proposed, moves, accepted, margin
 struct DevCounters {
     unsigned long long proposed, moves, accepted, margin, move_edges, acc_edges, recheck;
+    unsigned long long items;  // entries appended to the accepted-move list
 };
+
+// the accepted-move list: one (vertex, chunk) item per kMoveChunk edges of
+// every accepted mover, so the apply step's work units are all small
+constexpr int kMoveChunk = 256;
 
 struct ModelDev {
     int32_t B;
@@ -135,6 +142,8 @@ struct ModelDev {
     const int2 *hkv;                  // table slots: (key, count), key -1 when empty
     int32_t *status;
     DevCounters *counters;
+    int2 *items;        // accepted-move list (NULL: not kept)
+    int64_t cap_items;
 };
 
 }  // namespace sbp
@@ -184,6 +193,13 @@ struct sbp_model {
     // nodal pass: proposals with s != r, in three lists by degree
     void *movers = nullptr;
     unsigned *mcount = nullptr;
+    // accepted moves since the last commit, as (vertex, edge chunk) items;
+    // list_ok is false when the pending assignment has changes the list does
+    // not hold (labels set from outside, overlapping decide ranges)
+    int2 *items = nullptr;
+    int64_t cap_items = 0;
+    bool list_ok = true;
+    std::vector<std::pair<int64_t, int64_t>> decided;  // decide ranges since the last commit
     // side streams of the decision pass: the three degree groups' kernels
     // run concurrently so that each one's tail is filled by the others
     cudaStream_t side[2] = {nullptr, nullptr};
@@ -359,6 +375,45 @@ __device__ __forceinline__ int sparse_at(const ModelDev &md, int r, int c) {
 
 __device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) {
     return md.sparse ? sparse_at(md, r, c) : md.M[(size_t)r * md.B + c];
+}
+
+// continues a probe of row table [off, off + cap) for key c whose first
+// slot h has been loaded into kv (same bound and result as sparse_at)
+__device__ __forceinline__ int sparse_probe_from(const ModelDev &md, uint32_t off, uint32_t cap, uint32_t h, int c,
+                                                 int2 kv) {
+    for (uint32_t q = 1;; ++q) {
+        if (kv.x == c) return kv.y;
+        if (kv.x < 0 || q >= cap) return 0;
+        h = (h + 1) & (cap - 1);
+        kv = md.hkv[off + h];
+    }
+}
+
+// the four counts a neighbour block t contributes to a move r -> s:
+// M[r][t], M[s][t], M[t][r], M[t][s].  On sparse rows the three row offsets
+// and then the four first probe slots are loaded together (two dependent
+// rounds instead of eight); collisions continue one slot at a time.
+__device__ __forceinline__ void Mat4(const ModelDev &md, int r, int s, int t, int &Mrt, int &Mst, int &Mtr,
+                                     int &Mts) {
+    if (!md.sparse) {
+        const size_t B = (size_t)md.B;
+        Mrt = md.M[(size_t)r * B + t];
+        Mst = md.M[(size_t)s * B + t];
+        Mtr = md.M[(size_t)t * B + r];
+        Mts = md.M[(size_t)t * B + s];
+        return;
+    }
+    const uint32_t o_r = md.hoff[r], c_r = md.hoff[r + 1] - o_r;
+    const uint32_t o_s = md.hoff[s], c_s = md.hoff[s + 1] - o_s;
+    const uint32_t o_t = md.hoff[t], c_t = md.hoff[t + 1] - o_t;
+    const uint32_t ht = sparse_hash(t);
+    const uint32_t h1 = ht & (c_r - 1), h2 = ht & (c_s - 1);
+    const uint32_t h3 = sparse_hash(r) & (c_t - 1), h4 = sparse_hash(s) & (c_t - 1);
+    const int2 k1 = md.hkv[o_r + h1], k2 = md.hkv[o_s + h2], k3 = md.hkv[o_t + h3], k4 = md.hkv[o_t + h4];
+    Mrt = sparse_probe_from(md, o_r, c_r, h1, t, k1);
+    Mst = sparse_probe_from(md, o_s, c_s, h2, t, k2);
+    Mtr = sparse_probe_from(md, o_t, c_t, h3, r, k3);
+    Mts = sparse_probe_from(md, o_t, c_t, h4, s, k4);
 }
 
 // first i in a[lo, hi) with a[i] > t (one lane, binary search)

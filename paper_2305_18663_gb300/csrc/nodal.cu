@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
             }
             sh.dec = dec;
             if (dec >= 0) {
-                if (dec) md.bnew[v] = s;
+                if (dec) accept_move(md, v, s, x.k);
                 count_result(c, dec != 0, false, x.k);
             }
         }
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
                 }
                 corner_hastings_exact(x, cv, md.B, pft, pbt);
                 const Exact e = exact_decision(a.beta, dlt, fbt, pft, pbt, mv.w2);
-                if (e.accept) md.bnew[v] = s;
+                if (e.accept) accept_move(md, v, s, k);
                 count_exact(c, e.accept, e.margin, k);
                 write_trace(a, v, s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
             }
@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                     dec = fast_decision_f(a.beta32, fix48_to_float(dl48), has_fb ? (float)fb : 0.0f, pf, pb, w2, k);
             }
             if (dec >= 0) {
-                if (dec) md.bnew[v] = s;
+                if (dec) accept_move(md, v, s, k);
                 count_result(c, dec != 0, false, k);
             } else {
                 double pf64 = 0.0, pb64 = 0.0;
@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                 }
                 corner_hastings_exact(x, cv, B, pf64, pb64);
                 const Exact ex = exact_decision_d(a.beta, dL, pf64, pb64, w2);
-                if (ex.accept) md.bnew[v] = s;
+                if (ex.accept) accept_move(md, v, s, k);
                 count_exact(c, ex.accept, ex.margin, k);
                 write_trace(a, v, s, 1 | (ex.accept ? 2 : 0) | (ex.margin ? 4 : 0), ex.dH, ex.logA);
             }
@@ -1123,6 +1123,8 @@ ModelDev model_dev(sbp_model *m) {
     d.hkv = m->sp.hkv;
     d.status = m->status;
     d.counters = m->counters;
+    d.items = nullptr;  // set by the nodal pass only
+    d.cap_items = 0;
     return d;
 }
 
@@ -1245,9 +1247,25 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
             return fail(SBP_ENOMEM, "cudaMalloc failed for the mover lists");
         }
     }
+    if (!m->items) {
+        // at most one item per vertex plus one per kMoveChunk edge ends
+        const int64_t cap = g->n + (2 * g->m) / kMoveChunk + 1;
+        if (model_alloc((void **)&m->items, (size_t)cap * sizeof(int2), m->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SBP_ENOMEM, "cudaMalloc failed for the accepted-move list");
+        }
+        m->cap_items = cap;
+    }
+    // the list holds every accepted move only while the ranges decided since
+    // the last commit are disjoint
+    for (const auto &rg : m->decided)
+        if (v_begin < rg.second && rg.first < v_end) m->list_ok = false;
+    m->decided.emplace_back(v_begin, v_end);
     DecideArgs a;
     a.g = g->dev();
     a.md = model_dev(m);
+    a.md.items = m->items;
+    a.md.cap_items = m->cap_items;
     a.v_begin = v_begin;
     a.v_end = v_end;
     a.movers = static_cast<Mover *>(m->movers);

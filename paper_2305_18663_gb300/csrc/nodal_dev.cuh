@@ -76,7 +76,8 @@ struct VertexCtx {
 // one neighbour block t not in {r, s}: exact Delta L terms, FP32 Hastings terms
 __device__ __forceinline__ void entry_fast(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, __int128 &dl,
                                            double &fb, float &pf, float &pb) {
-    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    int Mrt, Mst, Mtr, Mts;
+    Mat4(md, x.r, x.s, t, Mrt, Mst, Mtr, Mts);
     // a zero count gives T[x] - T[x] = 0, so no branch is needed
     dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
     dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
@@ -89,11 +90,12 @@ __device__ __forceinline__ void entry_fast(const ModelDev &md, const VertexCtx &
 // the same Hastings terms in FP64 (the expression the FP64 test uses)
 __device__ __forceinline__ void entry_exact(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, double &pf,
                                             double &pb) {
-    const int64_t Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    int Mrt, Mst, Mtr, Mts;
+    Mat4(md, x.r, x.s, t, Mrt, Mst, Mtr, Mts);
     const double den = (double)((int64_t)md.dsum[t] + md.B);
     const double c = (double)(ko + ki);
-    pf += c * (double)(Mts + Mst + 1) / den;
-    pb += c * (double)((Mtr - ki) + (Mrt - ko) + 1) / den;
+    pf += c * (double)((int64_t)Mts + Mst + 1) / den;
+    pb += c * (double)(((int64_t)Mtr - ki) + ((int64_t)Mrt - ko) + 1) / den;
 }
 
 // ---------------------------------------------------------------------------
@@ -162,7 +164,8 @@ __device__ __forceinline__ float dl32_error(float am, int k) {
 // entry_fast with the FP32 Delta L terms
 __device__ __forceinline__ void entry_fast32(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki, float &dl,
                                              float &am, float &pf, float &pb) {
-    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    int Mrt, Mst, Mtr, Mts;
+    Mat4(md, x.r, x.s, t, Mrt, Mst, Mtr, Mts);
     dl += dxlogx32(Mrt, -ko, am) + dxlogx32(Mst, ko, am);
     dl += dxlogx32(Mtr, -ki, am) + dxlogx32(Mts, ki, am);
     const float rc = md.rcp32[t];
@@ -175,7 +178,8 @@ __device__ __forceinline__ void entry_fast32(const ModelDev &md, const VertexCtx
 // recheck of the precision form)
 __device__ __forceinline__ void entry_exact_all(const ModelDev &md, const VertexCtx &x, int t, int ko, int ki,
                                                 __int128 &dl, double &fb, double &pf, double &pb) {
-    const int Mrt = Mat(md, x.r, t), Mst = Mat(md, x.s, t), Mtr = Mat(md, t, x.r), Mts = Mat(md, t, x.s);
+    int Mrt, Mst, Mtr, Mts;
+    Mat4(md, x.r, x.s, t, Mrt, Mst, Mtr, Mts);
     dl += dT(md.T, md.XT, Mrt, -ko, fb) + dT(md.T, md.XT, Mst, ko, fb);
     dl += dT(md.T, md.XT, Mtr, -ki, fb) + dT(md.T, md.XT, Mts, ki, fb);
     const double den = (double)((int64_t)md.dsum[t] + md.B);
@@ -347,6 +351,18 @@ __device__ __forceinline__ bool table_add32(int *keys, unsigned *cnt, unsigned s
         h = (h + 1) & (unsigned)(cap - 1);
     }
     return false;
+}
+
+// an accepted move v -> s of a vertex with k edges: the pending label and
+// its items in the accepted-move list
+__device__ __forceinline__ void accept_move(const ModelDev &md, int v, int s, int k) {
+    md.bnew[v] = s;
+    if (md.items) {
+        const int nch = (k + kMoveChunk - 1) / kMoveChunk;
+        const unsigned long long base = atomicAdd(&md.counters->items, (unsigned long long)nch);
+        for (int c = 0; c < nch; ++c)
+            if (base + c < (unsigned long long)md.cap_items) md.items[base + c] = make_int2(v, c);
+    }
 }
 
 __device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin, int k) {
@@ -558,7 +574,7 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     }
     if (dec >= 0) {
         if (lane == 0) {
-            if (dec) md.bnew[x.v] = x.s;
+            if (dec) accept_move(md, x.v, x.s, x.k);
             count_result(c, dec != 0, false, x.k);
         }
         return;
@@ -584,7 +600,7 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
     corner_hastings_exact(x, cv, md.B, pf64, pb64);
     if (lane == 0) {
         const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
-        if (e.accept) md.bnew[x.v] = x.s;
+        if (e.accept) accept_move(md, x.v, x.s, x.k);
         count_exact(c, e.accept, e.margin, x.k);
         write_trace(a, x.v, x.s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
     }

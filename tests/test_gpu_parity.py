@@ -327,6 +327,37 @@ def test_shards_then_commit_equal_one_sweep():
     assert np.array_equal(full.dense(), shard.dense())
 
 
+@pytest.mark.parametrize("dmax", [4096, 1])
+def test_repeated_and_discarded_decisions_before_commit(dmax):
+    # a range decided twice (the accepted-move list no longer holds every
+    # change once: the apply step scans the assignment instead), and
+    # decisions dropped by a rebuild before the next pass
+    g = make_config("dcsbm_1m", scale=0.02)
+    B = 316
+    b = perturb(g.planted, B, 0.3, seed=9)  # few accepted moves: the incremental apply step
+    pg = P.Graph(g.n, g.src, g.dst)
+    prm = P.Params.default(seed=5, dense_max_B=dmax)
+    full = P.Model(pg, B, b, prm)
+    full.sweep(2)
+    twice = P.Model(pg, B, b, prm)
+    P.sbp_nodal_decide(twice.h, 2, 0, g.n)
+    P.sbp_nodal_decide(twice.h, 2, 1000, 3000)
+    P.sbp_commit(twice.h)
+    assert np.array_equal(full.assignment(), twice.assignment())
+    assert np.array_equal(full.coo()[0], twice.coo()[0]) and np.array_equal(full.coo()[1], twice.coo()[1])
+    dropped = P.Model(pg, B, b, prm)
+    P.sbp_nodal_decide(dropped.h, 7, 0, g.n)  # discarded by the rebuild below
+    P.sbp_set_assignment(dropped.h, B, b)
+    P.sbp_nodal_decide(dropped.h, 2, 0, g.n)
+    P.sbp_commit(dropped.h)
+    assert np.array_equal(full.assignment(), dropped.assignment())
+    assert np.array_equal(full.coo()[1], dropped.coo()[1])
+    G = O.Graph(g.n, g.src, g.dst)
+    check_blockmodel(dropped, O.Model(G, B, dropped.assignment()))
+    for m in (full, twice, dropped):
+        m.close()
+
+
 def test_single_block_and_no_edges():
     g = make_config("plain_1k")
     pg = P.Graph(g.n, g.src, g.dst)
