@@ -398,6 +398,14 @@ def run_batch(args):
     t_gen = time.perf_counter() - t0
     graphs = [P.Graph(n, src, dst) for n, src, dst in raw]
     opts = P.BatchOptions.default(workers=args.batch_workers)
+    tuned = None
+    if args.autotune > 0:
+        # the autotuner on a sample of the same graphs, before the timed call
+        t0 = time.perf_counter()
+        opts, rate, trials = P.autotune_batch(graphs, P.Params.default(seed=args.seed), args.autotune, opts)
+        tuned = {"sample": min(args.autotune, len(graphs)), "trials": trials, "seconds": time.perf_counter() - t0,
+                 "sample_graphs_per_s": rate,
+                 "options": {f: getattr(opts, f) for f, _ in P.BatchOptions._fields_}}
     params = P.Params.default(seed=args.seed, dense_max_B=opts.dense_max_B)
     torch.cuda.synchronize()
     bstats = P.BatchStats()
@@ -416,6 +424,7 @@ def run_batch(args):
            "unit": "graphs/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
            "plain": {"value": len(graphs) / t_plain, "unit": "graphs/s", "seconds": t_plain},
            "batched_seconds": t_batch, "speedup_vs_plain": t_plain / t_batch, "batch_stats": bstats.as_dict(),
+           "autotune": tuned,
            "results_equal": mismatch == 0, "mismatches": mismatch,
            "completion_s": {"p50": float(np.percentile(done, 50)), "p99": float(np.percentile(done, 99))},
            "dtype": "f32 terms, exact recheck", "data": "synthetic",
@@ -525,6 +534,8 @@ def main():
     ap.add_argument("--batch-total", type=int, default=4096, help="graphs of the batching workload")
     ap.add_argument("--batch-count", type=int, default=256, help="graphs actually run (an evenly strided subset)")
     ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--autotune", type=int, default=32,
+                    help="batch mode: graphs in the autotuner's sample (0: default options)")
     ap.add_argument("--m-form", default="sparse", choices=["dense", "sparse"],
                     help="sparse: hashed sparse rows at every B (the M form of the 1M-vertex precision "
                          "configuration; a dense run of the same sweeps is reported beside it); dense: M dense")

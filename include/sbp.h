@@ -277,15 +277,18 @@ int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_
  * (1..1024); max_n: largest graph (vertices) whose phases are batched (a CTA
  * takes a whole phase, so big graphs are better served by the per-graph
  * kernels); dense_max_B: dense/sparse switch of the batch's models
- * (max_B..16384); ctas_per_sm: persistent CTAs per SM (1..8); mem_fraction:
- * (0, 0.95]. */
+ * (max_B..16384); ctas_per_sm: persistent CTAs per SM (1..8);
+ * movers_per_warp: movers a warp of the persistent kernel evaluates at once
+ * (1, 2 or 4: 32, 16 or 8 lanes each; fewer when their per-mover count rows
+ * would not fit shared memory); mem_fraction: (0, 0.95].  No option changes
+ * a result. */
 typedef struct sbp_batch_options {
     int32_t workers;
     int32_t max_B;
     int32_t dense_max_B;
     int32_t ctas_per_sm;
     int32_t max_n;
-    int32_t reserved;
+    int32_t movers_per_warp;
     double mem_fraction;
 } sbp_batch_options;
 
@@ -318,7 +321,7 @@ typedef struct sbp_batch_stats {
 } sbp_batch_stats;
 
 /* Fills o with the defaults: 16 workers, max_B 512, max_n 4096, dense_max_B
- * 4096, 2 CTAs per SM, mem_fraction 0.5. */
+ * 4096, 2 CTAs per SM, 2 movers per warp, mem_fraction 0.5. */
 int sbp_default_batch_options(sbp_batch_options *o);
 
 /* Partitions graphs[0..count).  p: NULL for the defaults (shared by every
@@ -329,6 +332,20 @@ int sbp_default_batch_options(sbp_batch_options *o);
 int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
                         const sbp_batch_options *o, int32_t *const *b_out, sbp_batch_result *res,
                         sbp_batch_stats *stats);
+
+/* Autotuner of the batching form: times sbp_partition_batch on a sample of
+ * graphs (`sample` of them, evenly spaced in size order; all when sample <= 0
+ * or >= count) under candidate options and returns the fastest in *best.
+ * The search starts from *best when `start` is nonzero (else from the
+ * defaults) and tunes one option at a time, in this order: movers_per_warp
+ * {1, 2, 4}, ctas_per_sm {1, 2, 3, 4}, max_B {128, 256, 512, 1024}, max_n
+ * {1024, 4096, 16384, 65536}, dense_max_B {1024, 4096}; workers and
+ * mem_fraction are kept.  *graphs_per_s (may be NULL) receives the best
+ * rate on the sample, *trials (may be NULL) the number of timed runs.
+ * Every run must give the same B and DL for every graph; SBP_ESTATE
+ * otherwise.  p: NULL for the defaults. */
+int sbp_autotune_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p, int32_t sample,
+                       int32_t start, sbp_batch_options *best, double *graphs_per_s, int32_t *trials);
 
 /* ---------------------------------------------------------------------
  * Serving form: the batch engine fed while it runs (continuous batching).

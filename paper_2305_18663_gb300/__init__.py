@@ -27,7 +27,7 @@ __all__ = [
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_pending", "sbp_set_pending", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
     "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_dxlogx32_check", "sbp_default_batch_options", "sbp_partition_batch",
-    "BatchOptions", "BatchResult", "BatchStats", "partition_batch", "Server",
+    "BatchOptions", "BatchResult", "BatchStats", "partition_batch", "Server", "sbp_autotune_batch", "autotune_batch",
     "sbp_server_create", "sbp_server_submit", "sbp_server_poll", "sbp_server_wait", "sbp_server_stats",
     "sbp_server_destroy",
     "Graph", "Model", "deal_vertices",
@@ -90,7 +90,7 @@ class BatchOptions(C.Structure):
         ("dense_max_B", C.c_int32),
         ("ctas_per_sm", C.c_int32),
         ("max_n", C.c_int32),
-        ("reserved", C.c_int32),
+        ("movers_per_warp", C.c_int32),
         ("mem_fraction", C.c_double),
     ]
 
@@ -181,6 +181,7 @@ def load(path: str | None = None):
         "sbp_default_batch_options": (C.c_int, [P(BatchOptions)]),
         "sbp_dxlogx32_check": (C.c_int, [vp, vp, i32, vp, vp]),
         "sbp_partition_batch": (C.c_int, [vp, i32, P(Params), P(BatchOptions), vp, P(BatchResult), P(BatchStats)]),
+        "sbp_autotune_batch": (C.c_int, [vp, i32, P(Params), i32, i32, P(BatchOptions), P(f64), P(i32)]),
         "sbp_server_create": (C.c_int, [P(Params), P(BatchOptions), P(vp)]),
         "sbp_server_submit": (C.c_int, [vp, vp, vp, P(i64)]),
         "sbp_server_poll": (C.c_int, [vp, i64, P(i32)]),
@@ -450,6 +451,24 @@ def partition_batch(graphs: list["Graph"], params: Params | None = None, options
     outs = [np.zeros(g.n, np.int32) for g in graphs]
     res = sbp_partition_batch([g.h for g in graphs], outs, params, options, stats)
     return [(outs[i], r.B, r.dl, r.n_sweeps, r.t_admit, r.t_done) for i, r in enumerate(res)]
+
+
+def sbp_autotune_batch(graphs: list[int], params: Params | None = None, sample: int = 64,
+                       start: BatchOptions | None = None) -> tuple[BatchOptions, float, int]:
+    """graphs: handles.  Returns (best options, graphs/s on the sample, timed runs)."""
+    n = len(graphs)
+    ga = (C.c_void_p * max(n, 1))(*graphs)
+    best = start if start is not None else BatchOptions.default()
+    rate, trials = C.c_double(), C.c_int32()
+    _check(lib().sbp_autotune_batch(ga, n, C.byref(params) if params else None, sample, 1 if start is not None else 0,
+                                    C.byref(best), C.byref(rate), C.byref(trials)))
+    return best, rate.value, trials.value
+
+
+def autotune_batch(graphs: list["Graph"], params: Params | None = None, sample: int = 64,
+                   start: BatchOptions | None = None) -> tuple[BatchOptions, float, int]:
+    """Options of the batching form tuned on a sample of these graphs."""
+    return sbp_autotune_batch([g.h for g in graphs], params, sample, start)
 
 
 def sbp_server_create(params: Params | None = None, options: BatchOptions | None = None) -> int:

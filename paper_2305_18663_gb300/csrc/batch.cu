@@ -42,6 +42,7 @@ namespace {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr size_t kBatchSmemCap = 96 * 1024;  // dynamic shared memory of a CTA (two per SM)
 
 // the blockmodel arrays the apply step writes (the decision pass sees them
 // read-only through DecideArgs)
@@ -112,17 +113,22 @@ __device__ __int128 cta_sum_128(__int128 v, __int128 *sh) {
     return s;
 }
 
-template <bool DL32>
+// G: lanes per mover in the evaluation (32 / G movers per warp at a time);
+// group_words: shared-memory words of one group (counts, then the list)
+template <bool DL32, int G>
 __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob *__restrict__ jobs, int njobs,
-                                                                  unsigned *__restrict__ queue, int warp_words) {
+                                                                  unsigned *__restrict__ queue, int group_words) {
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ DecideArgs sa;
     __shared__ ModelOut sw;
     __shared__ __int128 red[kBatchWarps];
     __shared__ unsigned s_job, s_nmov;
     __shared__ int s_stop;
+    constexpr int V = 32 / G;  // movers per warp
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    unsigned *cnt = reinterpret_cast<unsigned *>(bsm) + (size_t)wid * warp_words;
+    const int gid = lane / G, gl = lane & (G - 1);
+    const unsigned gm = group_mask<G>();
+    unsigned *cnt = reinterpret_cast<unsigned *>(bsm) + ((size_t)wid * V + gid) * group_words;
     for (;;) {
         if (tid == 0) s_job = atomicAdd(queue, 1u);
         __syncthreads();
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob 
         const ModelDev &md = sa.md;
         const int B = md.B, n = g.n;
         int *list = reinterpret_cast<int *>(cnt + B);
-        for (int i = lane; i < B; i += 32) cnt[i] = 0u;
+        for (int i = gl; i < B; i += G) cnt[i] = 0u;
         // sum over the cells of T[M] at the phase start (exact)
         __int128 c = 0;
         for (int64_t i = tid; i < (int64_t)B * B; i += kBatchThreads) c += md.T[md.M[i]];
@@ -174,33 +180,34 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob 
                 }
             }
             __syncthreads();
-            // 2. evaluation, one warp per mover
+            // 2. evaluation, G lanes per mover
             const int nmov = (int)s_nmov;
             Counts cts;
-            for (int q = wid; q < nmov; q += kBatchWarps) {
+            __syncwarp();
+            for (int q = wid * V + gid; q < nmov; q += kBatchWarps * V) {
                 const Mover mv = sa.movers[q];
                 const int v = mv.v;
                 const int o0 = g.op[v], kout = g.op[v + 1] - o0;
                 const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
                 const int kk = kout + kin;
                 int nl = 0, self = 0;
-                for (int base = 0; base < kk; base += 32) {
-                    const int idx = base + lane;
+                for (int base = 0; base < kk; base += G) {
+                    const int idx = base + gl;
                     const bool valid = idx < kk, is_out = idx < kout;
                     const int nb = valid ? (is_out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
                     const bool is_self = valid && nb == v;
-                    self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
+                    self += __popc(__ballot_sync(gm, is_self && is_out));
                     bool fresh = false;
                     int t = 0;
                     if (valid && !is_self) {
                         t = md.b[nb];
                         fresh = atomicAdd(&cnt[t], is_out ? 1u : 0x10000u) == 0u;
                     }
-                    const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+                    const unsigned fm = __ballot_sync(gm, fresh);  // bits of this group only
                     if (fresh) list[nl + __popc(fm & ((1u << lane) - 1u))] = t;
                     nl += __popc(fm);
                 }
-                __syncwarp();
+                __syncwarp(gm);
                 VertexCtx x;
                 x.v = v;
                 x.r = md.b[v];
@@ -209,16 +216,16 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob 
                 x.Kin = kin;
                 x.self = self;
                 x.k = kk;
-                evaluate_warp<DL32>(sa, md, x, mv.w2, [&](auto &&f) {
-                    for (int e = lane; e < nl; e += 32) {
+                evaluate_group<DL32, G>(sa, md, x, mv.w2, [&](auto &&f) {
+                    for (int e = gl; e < nl; e += G) {
                         const int t = list[e];
                         const unsigned cc = cnt[t];
                         f(t, (int)(cc & 0xffffu), (int)(cc >> 16));
                     }
                 }, cts);
-                __syncwarp();
-                for (int e = lane; e < nl; e += 32) cnt[list[e]] = 0u;
-                __syncwarp();
+                __syncwarp(gm);
+                for (int e = gl; e < nl; e += G) cnt[list[e]] = 0u;
+                __syncwarp(gm);
             }
             __syncthreads();
             // 3. apply: warp per 32 vertex ids, rows of the moved ones
@@ -370,19 +377,27 @@ int batch_enqueue(const std::vector<sbp_model *> &models, const std::vector<uint
     SBP_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)nj * sizeof(BatchJob), cudaMemcpyHostToDevice, st));
     SBP_CUDA(cudaMemcpyAsync(d_hist, h0.data(), h0.size() * 8, cudaMemcpyHostToDevice, st));
     SBP_CUDA(cudaMemsetAsync(d_queue, 0, 4, st));
-    // per warp: B counts and a list of up to B blocks
-    const int warp_words = 2 * maxB + 4;
-    const size_t smem = (size_t)kBatchWarps * warp_words * 4;
+    // per mover group: B counts and a list of up to B blocks; as many movers
+    // per warp as asked for while the CTA's share of shared memory holds them
+    const int group_words = 2 * maxB + 4;
+    int V = tune.movers_per_warp == 4 ? 4 : tune.movers_per_warp == 2 ? 2 : 1;
+    while (V > 1 && (size_t)kBatchWarps * V * group_words * 4 > kBatchSmemCap) V /= 2;
+    const size_t smem = (size_t)kBatchWarps * V * group_words * 4;
     const int per_sm = tune.ctas_per_sm > 0 ? tune.ctas_per_sm : 2;
     const int grid = std::min(nj, sm_count_b() * per_sm);
+    auto launch = [&](auto kern) -> int {
+        SBP_TRY(ensure_dyn_smem((const void *)kern, smem));
+        kern<<<grid, kBatchThreads, smem, st>>>(d_jobs, nj, d_queue, group_words);
+        SBP_LAUNCHED();
+        return SBP_OK;
+    };
     if (dl32) {
-        SBP_TRY(ensure_dyn_smem((const void *)k_batch_mcmc<true>, smem));
-        k_batch_mcmc<true><<<grid, kBatchThreads, smem, st>>>(d_jobs, nj, d_queue, warp_words);
+        SBP_TRY(V == 4 ? launch(k_batch_mcmc<true, 8>) : V == 2 ? launch(k_batch_mcmc<true, 16>)
+                                                          : launch(k_batch_mcmc<true, 32>));
     } else {
-        SBP_TRY(ensure_dyn_smem((const void *)k_batch_mcmc<false>, smem));
-        k_batch_mcmc<false><<<grid, kBatchThreads, smem, st>>>(d_jobs, nj, d_queue, warp_words);
+        SBP_TRY(V == 4 ? launch(k_batch_mcmc<false, 8>) : V == 2 ? launch(k_batch_mcmc<false, 16>)
+                                                           : launch(k_batch_mcmc<false, 32>));
     }
-    SBP_LAUNCHED();
     SBP_CUDA(cudaFreeAsync(buf, st));
     return SBP_OK;
 }
@@ -396,7 +411,7 @@ extern "C" int sbp_default_batch_options(sbp_batch_options *o) {
     o->dense_max_B = 4096;
     o->ctas_per_sm = 2;
     o->max_n = 4096;
-    o->reserved = 0;
+    o->movers_per_warp = 2;
     o->mem_fraction = 0.5;
     return SBP_OK;
 }

@@ -16,6 +16,7 @@ struct BatchTuning {
     int max_B = 512;         // phases at B above this run on the per-graph kernels
     int64_t max_n = 4096;    // and so do graphs with more vertices
     int dense_max_B = 4096;  // dense / sparse switch of the models in the batch
+    int movers_per_warp = 1; // evaluation: 1 (32 lanes each), 2 (16) or 4 (8)
 };
 
 struct BatchOptions {

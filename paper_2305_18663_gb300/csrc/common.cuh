@@ -274,6 +274,32 @@ __device__ __forceinline__ __int128 warp_sum_128(__int128 v) {
     return v;
 }
 
+// reductions over an aligned group of G lanes (G = 8, 16, 32) that share
+// a mover; every lane of the group gets the sum
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G == 32) return 0xffffffffu;
+    return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+}
+
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T v, unsigned gm) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ __int128 group_sum_128(__int128 v, unsigned gm) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(gm, (unsigned long long)v, o);
+        const long long hi = __shfl_xor_sync(gm, (long long)(v >> 64), o);
+        v += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+    }
+    return v;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -422,6 +422,8 @@ int batch_options(const sbp_batch_options *o, BatchOptions &opt) {
         return fail(SBP_EINVAL, "batch options: dense_max_B must be in [max_B, 16384]");
     if (bo.ctas_per_sm < 1 || bo.ctas_per_sm > 8) return fail(SBP_EINVAL, "batch options: ctas_per_sm must be in [1, 8]");
     if (bo.max_n < 0) return fail(SBP_EINVAL, "batch options: max_n must be >= 0");
+    if (bo.movers_per_warp != 1 && bo.movers_per_warp != 2 && bo.movers_per_warp != 4)
+        return fail(SBP_EINVAL, "batch options: movers_per_warp must be 1, 2 or 4");
     if (!(bo.mem_fraction > 0.0 && bo.mem_fraction <= 0.95))
         return fail(SBP_EINVAL, "batch options: mem_fraction must be in (0, 0.95]");
     opt.workers = bo.workers;
@@ -430,6 +432,7 @@ int batch_options(const sbp_batch_options *o, BatchOptions &opt) {
     opt.tune.dense_max_B = bo.dense_max_B;
     opt.tune.ctas_per_sm = bo.ctas_per_sm;
     opt.tune.max_n = bo.max_n;
+    opt.tune.movers_per_warp = bo.movers_per_warp;
     return SBP_OK;
 }
 
@@ -467,6 +470,85 @@ extern "C" int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t cou
         res[i] = it.res;
     }
     if (stats) *stats = e.st;
+    return SBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the batching form: coordinate search over the options, each
+// candidate timed on the same sample of graphs, every result checked equal
+
+extern "C" int sbp_autotune_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p,
+                                  int32_t sample, int32_t start, sbp_batch_options *best, double *graphs_per_s,
+                                  int32_t *trials) {
+    if (!graphs || !best || count < 1) return fail(SBP_EINVAL, "sbp_autotune_batch: needs graphs and best");
+    for (int i = 0; i < count; ++i)
+        if (!graphs[i]) return fail(SBP_EINVAL, "sbp_autotune_batch: NULL graph " + std::to_string(i));
+    // the sample: evenly spaced in size order, so that it spans the sizes
+    std::vector<int> idx((size_t)count);
+    for (int i = 0; i < count; ++i) idx[(size_t)i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return graphs[x]->n + graphs[x]->m < graphs[y]->n + graphs[y]->m;
+    });
+    const int ns = (sample <= 0 || sample >= count) ? count : sample;
+    std::vector<const sbp_graph_t *> pick((size_t)ns);
+    for (int i = 0; i < ns; ++i) pick[(size_t)i] = graphs[idx[(size_t)((int64_t)i * count / ns)]];
+
+    sbp_batch_options cur;
+    if (start) cur = *best;
+    else sbp_default_batch_options(&cur);
+    sbp::BatchOptions chk;
+    SBP_TRY(sbp::batch_options(&cur, chk));
+    std::vector<sbp_batch_result> res((size_t)ns), ref((size_t)ns);
+    bool have_ref = false;
+    int ntr = 0;
+    auto run = [&](const sbp_batch_options &o, double *rate) -> int {
+        const auto t0 = std::chrono::steady_clock::now();
+        SBP_TRY(sbp_partition_batch(pick.data(), ns, p, &o, nullptr, res.data(), nullptr));
+        const double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        ++ntr;
+        if (!have_ref) {
+            ref = res;
+            have_ref = true;
+        } else {
+            for (int i = 0; i < ns; ++i)
+                if (res[(size_t)i].B != ref[(size_t)i].B || res[(size_t)i].dl != ref[(size_t)i].dl ||
+                    res[(size_t)i].n_sweeps != ref[(size_t)i].n_sweeps)
+                    return fail(SBP_ESTATE, "sbp_autotune_batch: results differ between options");
+        }
+        *rate = ns / std::max(s, 1e-9);
+        return SBP_OK;
+    };
+    double best_rate = 0.0;
+    SBP_TRY(run(cur, &best_rate));  // warm-up: one-time set-up costs
+    SBP_TRY(run(cur, &best_rate));
+    struct Knob {
+        int32_t sbp_batch_options::*field;
+        std::vector<int32_t> values;
+    };
+    const Knob knobs[] = {
+        {&sbp_batch_options::movers_per_warp, {1, 2, 4}},
+        {&sbp_batch_options::ctas_per_sm, {1, 2, 3, 4}},
+        {&sbp_batch_options::max_B, {128, 256, 512, 1024}},
+        {&sbp_batch_options::max_n, {1024, 4096, 16384, 65536}},
+        {&sbp_batch_options::dense_max_B, {1024, 4096}},
+    };
+    for (const Knob &kb : knobs) {
+        for (int32_t v : kb.values) {
+            if (cur.*kb.field == v) continue;
+            sbp_batch_options trial = cur;
+            trial.*kb.field = v;
+            if (trial.dense_max_B < trial.max_B) continue;
+            double rate = 0.0;
+            SBP_TRY(run(trial, &rate));
+            if (rate > best_rate * 1.02) {  // a clear gain only: runs are noisy
+                cur = trial;
+                best_rate = rate;
+            }
+        }
+    }
+    *best = cur;
+    if (graphs_per_s) *graphs_per_s = best_rate;
+    if (trials) *trials = ntr;
     return SBP_OK;
 }
 

@@ -501,13 +501,18 @@ __device__ __forceinline__ Proposal propose_vertex(const GraphDev &g, const Mode
 // ---------------------------------------------------------------------------
 // moves of vertices with 33 <= k (one warp per vertex)
 
-// Evaluates the move v: r -> s once the entries are aggregated.
-// each_entry(f) calls f(t, ko, ki) for each entry the calling lane holds.
-// All 32 lanes call this; the result is written by lane 0.
-template <bool DL32, class EachEntry>
-__device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
-                                              EachEntry each_entry, Counts &c) {
-    const int lane = threadIdx.x & 31;
+// Evaluates the move v: r -> s once the entries are aggregated, on an
+// aligned group of G lanes (G = 32: the whole warp; 8 or 16: several movers
+// per warp).  each_entry(f) calls f(t, ko, ki) for each entry the calling
+// lane holds.  All G lanes call this; the result is written by the group's
+// first lane.
+template <bool DL32, int G, class EachEntry>
+__device__ __forceinline__ void evaluate_group(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
+                                               EachEntry each_entry, Counts &c) {
+    static_assert(G == 8 || G == 16 || G == 32, "group of 8, 16 or 32 lanes");
+    const unsigned gm = group_mask<G>();
+    const int gl = (threadIdx.x & 31) & (G - 1);
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
     // neighbours in r and in s (one lane holds each); 16-bit fields when
     // the degree allows it
     if (x.k < 65536) {
@@ -516,8 +521,8 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
             if (t == x.r) pr += ko | (ki << 16);
             else if (t == x.s) ps += ko | (ki << 16);
         });
-        pr = warp_sum_i(pr);
-        ps = warp_sum_i(ps);
+        pr = group_sum<G>(pr, gm);
+        ps = group_sum<G>(ps, gm);
         x.ko_r = pr & 0xffff;
         x.ki_r = pr >> 16;
         x.ko_s = ps & 0xffff;
@@ -528,10 +533,10 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
             if (t == x.r) { a0 += ko; a1 += ki; }
             else if (t == x.s) { a2 += ko; a3 += ki; }
         });
-        x.ko_r = warp_sum_i(a0);
-        x.ki_r = warp_sum_i(a1);
-        x.ko_s = warp_sum_i(a2);
-        x.ki_s = warp_sum_i(a3);
+        x.ko_r = group_sum<G>(a0, gm);
+        x.ki_r = group_sum<G>(a1, gm);
+        x.ko_s = group_sum<G>(a2, gm);
+        x.ki_s = group_sum<G>(a3, gm);
     }
 
     __int128 dl = 0;
@@ -543,37 +548,38 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
         each_entry([&](int t, int ko, int ki) {
             if (t != x.r && t != x.s) entry_fast32(md, x, t, ko, ki, dlf, am, pf, pb);
         });
-        val = special_terms32(md, x, lane, dlf, am);
+        val = special_terms32(md, x, gl, dlf, am);
     } else {
         each_entry([&](int t, int ko, int ki) {
             if (t != x.r && t != x.s) entry_fast(md, x, t, ko, ki, dl, fb, pf, pb);
         });
-        val = special_terms(md, x, lane, dl, fb);
+        val = special_terms(md, x, gl, dl, fb);
     }
     CornerVals cv;
-    cv.Mrr = __shfl_sync(0xffffffffu, val, 0);
-    cv.Mss = __shfl_sync(0xffffffffu, val, 1);
-    cv.Mrs = __shfl_sync(0xffffffffu, val, 2);
-    cv.Msr = __shfl_sync(0xffffffffu, val, 3);
+    cv.Mrr = __shfl_sync(gm, val, gbase + 0);
+    cv.Mss = __shfl_sync(gm, val, gbase + 1);
+    cv.Mrs = __shfl_sync(gm, val, gbase + 2);
+    cv.Msr = __shfl_sync(gm, val, gbase + 3);
     cv.dr = md.dsum[x.r];
     cv.ds = md.dsum[x.s];
-    pf = warp_sum_f(pf);
-    pb = warp_sum_f(pb);
+    pf = group_sum<G>(pf, gm);
+    pb = group_sum<G>(pb, gm);
     corner_hastings_fast(x, cv, md.B, pf, pb);
     int dec = -1;
     bool has_fb = false;
     if (DL32) {
-        dlf = warp_sum_f(dlf);
-        am = warp_sum_f(am);
-        if (!a.trace_on) dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, x.k, dl32_error(am, x.k));
+        dlf = group_sum<G>(dlf, gm);
+        am = group_sum<G>(am, gm);
+        // at most k / G entries per lane before the group tree
+        if (!a.trace_on) dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, x.k, dl32_error(am, x.k * (32 / G)));
     } else {
-        dl = warp_sum_128(dl);
-        has_fb = __any_sync(0xffffffffu, __double_as_longlong(fb) != 0);
-        if (has_fb) fb = warp_sum(fb);
+        dl = group_sum_128<G>(dl, gm);
+        has_fb = __any_sync(gm, __double_as_longlong(fb) != 0);
+        if (has_fb) fb = group_sum<G>(fb, gm);
         if (!a.trace_on) dec = fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
     }
     if (dec >= 0) {
-        if (lane == 0) {
+        if (gl == 0) {
             if (dec) accept_move(md, x.v, x.s, x.k);
             count_result(c, dec != 0, false, x.k);
         }
@@ -587,23 +593,30 @@ __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDe
         each_entry([&](int t, int ko, int ki) {
             if (t != x.r && t != x.s) entry_exact_all(md, x, t, ko, ki, dl, fb, pf64, pb64);
         });
-        special_terms(md, x, lane, dl, fb);
-        dl = warp_sum_128(dl);
-        if (__any_sync(0xffffffffu, __double_as_longlong(fb) != 0)) fb = warp_sum(fb);
+        special_terms(md, x, gl, dl, fb);
+        dl = group_sum_128<G>(dl, gm);
+        if (__any_sync(gm, __double_as_longlong(fb) != 0)) fb = group_sum<G>(fb, gm);
     } else {
         each_entry([&](int t, int ko, int ki) {
             if (t != x.r && t != x.s) entry_exact(md, x, t, ko, ki, pf64, pb64);
         });
     }
-    pf64 = warp_sum(pf64);
-    pb64 = warp_sum(pb64);
+    pf64 = group_sum<G>(pf64, gm);
+    pb64 = group_sum<G>(pb64, gm);
     corner_hastings_exact(x, cv, md.B, pf64, pb64);
-    if (lane == 0) {
+    if (gl == 0) {
         const Exact e = exact_decision(a.beta, dl, fb, pf64, pb64, w2);
         if (e.accept) accept_move(md, x.v, x.s, x.k);
         count_exact(c, e.accept, e.margin, x.k);
         write_trace(a, x.v, x.s, 1 | (e.accept ? 2 : 0) | (e.margin ? 4 : 0), e.dH, e.logA);
     }
+}
+
+// the whole warp on one mover
+template <bool DL32, class EachEntry>
+__device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
+                                              EachEntry each_entry, Counts &c) {
+    evaluate_group<DL32, 32>(a, md, x, w2, each_entry, c);
 }
 
 }  // namespace

@@ -33,6 +33,8 @@ def _plain(pg, params):
     dict(),                                            # defaults
     dict(workers=3, max_B=64, dense_max_B=128),        # more per-graph phases, sparse rows above 128
     dict(workers=2, max_B=1024, mem_fraction=1e-9),    # one graph admitted at a time
+    dict(movers_per_warp=1, max_n=100000),             # a warp per mover, every graph batched
+    dict(movers_per_warp=4, max_B=256, ctas_per_sm=3), # 8 lanes per mover
 ])
 def test_batch_equals_plain(opts):
     gs, pgs = _graphs(10, 4000)
@@ -62,4 +64,19 @@ def test_batch_bad_options_raise():
         P.partition_batch(pgs, None, P.BatchOptions.default(max_B=5000))
     with pytest.raises(P.SbpError):
         P.partition_batch(pgs, None, P.BatchOptions.default(workers=0))
+    with pytest.raises(P.SbpError):
+        P.partition_batch(pgs, None, P.BatchOptions.default(movers_per_warp=3))
     assert P.partition_batch([], None, None) == []
+
+
+def test_autotuner_returns_valid_options_with_unchanged_results():
+    gs, pgs = _graphs(8, 3000, seed=13)
+    params = P.Params.default(seed=2)
+    best, rate, trials = P.autotune_batch(pgs, params, sample=4)
+    assert rate > 0.0 and trials >= 2 + 5  # warm-up, baseline and one run per knob at least
+    assert best.movers_per_warp in (1, 2, 4) and 1 <= best.ctas_per_sm <= 4
+    assert best.max_B in (128, 256, 512, 1024) and best.dense_max_B >= best.max_B
+    out = P.partition_batch(pgs, params, best)
+    for pg, (b, B, dl, ns, ta, td) in zip(pgs, out):
+        pb, pB, pdl, pns = _plain(pg, params)
+        assert B == pB and dl == pdl and ns == pns and np.array_equal(b, pb)
