@@ -44,6 +44,41 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def sources_sha256() -> str:
+    """Hash of the library's sources (kernels, host code, C header)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_18663_gb300", "csrc")
+    names = [x for x in sorted(os.listdir(csrc)) if x.endswith((".cu", ".cuh", ".h"))]
+    for name in names + ["../../include/sbp.h"]:
+        path = os.path.normpath(os.path.join(csrc, name))
+        if os.path.isfile(path):
+            h.update(name.encode())
+            with open(path, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def decide_traffic(m_form: str):
+    """DRAM bytes of one decide pass from the committed ncu summary, when it
+    was taken on the current sources and this M form; else None."""
+    path = os.path.join(ROOT, "profiles", "decide_traffic_dcsbm_1m.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("sources_sha256") != sources_sha256() or kv.get("m_form") != m_form:
+            return None
+        return {"bytes": float(kv["dram_bytes_per_pass"]), "sweep": kv["sweep"],
+                "algorithmic_bytes": float(kv["algorithmic_bytes_of_that_sweep"])}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload(name: str, scale: float):
     g = make_config(name, seed=0, scale=scale)
     B = CONFIGS[name]["n_blocks"]
@@ -231,10 +266,19 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = float(t.item())
     st = P.sbp_nodal_sweep(model.h, sweep_id, 0, g.n, stats=True)
     precision = dl_vs_fp64(P, torch, model, g, B, dev)
+    # the timed sweeps replayed (the chain is deterministic) with their
+    # statistics read back: the mover edges of exactly those sweeps
+    model.close()
+    replay = P.Model(graph, B, b0, params, stream)
+    move_edges = []
+    for k in range(args.warmup + args.steps):
+        rs = P.sbp_nodal_sweep(replay.h, k, 0, g.n, stats=True)
+        if k >= args.warmup:
+            move_edges.append(rs.n_move_edges)
+    replay.close()
     dense_comparison = None
     if args.m_form == "sparse" and B <= 4096:
         # the same sweeps with M held dense (the comparison form)
-        model.close()
         dm = P.Model(graph, B, b0, P.Params.default(seed=args.seed, dense_max_B=4096, dl_fp32=params.dl_fp32), stream)
         for k in range(args.warmup):
             P.sbp_nodal_decide(dm.h, k, 0, g.n)
@@ -256,9 +300,10 @@ def run_ours(args, rank, world, local_rank):
     res = None
     if rank == 0:
         hbm, hbm_kind = peaks()
-        dec_b, reb_b = algorithmic_bytes(g.n, g.m, B, st.n_move_edges)
+        dec_b, reb_b = algorithmic_bytes(g.n, g.m, B, statistics.mean(move_edges))
         dec_avg = statistics.mean(decide_ms)
         achieved = dec_b / (dec_avg * 1e-3) / 1e9
+        traffic = decide_traffic(args.m_form) if args.config == "dcsbm_1m" and args.scale == 1.0 else None
         ms_step = total_ms / args.steps
         value = g.n * args.steps * world / (total_ms * 1e-3)
         res = {
@@ -281,7 +326,11 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches,
             "roofline": {"kernel": "nodal decide pass (k_propose, k_eval_batch, k_eval_warp, k_eval_cta)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "peak_kind": hbm_kind, "algorithmic_bytes": dec_b, "traffic": None},
+                         "peak_kind": hbm_kind, "algorithmic_bytes": dec_b,
+                         "algorithmic_bytes_note": "mean over the timed sweeps (replayed with statistics)",
+                         "traffic": traffic["bytes"] if traffic else None,
+                         "traffic_note": (f"ncu DRAM bytes of the decide pass of {traffic['sweep']}, whose algorithmic "
+                                          f"bytes are {traffic['algorithmic_bytes']:.4g}") if traffic else None},
             "breakdown_ms": {"decide": dec_avg, "commit": statistics.mean(commit_ms),
                              "decide_min": min(decide_ms), "commit_bytes": reb_b},
             "last_sweep": st.as_dict(),
