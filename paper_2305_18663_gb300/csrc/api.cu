@@ -260,7 +260,7 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     void *ps[] = {m->b,        m->bnew,   m->M,        m->P,       m->Pc,     m->dout,  m->din,
                   m->rcp,      m->rcp32,  m->dsum,     m->dl,      m->partials, m->counters, m->status,
                   m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount, m->skip,
-                  m->items};
+                  m->items,    m->nbo,    m->nbi};
     for (void *p : ps) model_free(p, st);
     for (int i = 0; i < 2; ++i) {
         if (m->side[i]) cudaStreamDestroy(m->side[i]);
@@ -380,7 +380,9 @@ extern "C" int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats) {
     if (!m) return fail(SBP_EINVAL, "sbp_commit: NULL model");
     std::swap(m->b, m->bnew);
     SBP_CUDA(cudaMemcpyAsync(m->dl + 1, m->dl, 8, cudaMemcpyDeviceToDevice, m->stream));
-    const int rc = commit_blockmodel(m);
+    int rc = commit_blockmodel(m);
+    if (rc == SBP_OK) rc = nb_rows_after_commit(m);
+    if (rc != SBP_OK) m->nb_ok = false;
     m->list_ok = true;
     m->decided.clear();
     SBP_TRY(rc);

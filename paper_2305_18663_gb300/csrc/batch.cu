@@ -331,6 +331,7 @@ int batch_enqueue(const std::vector<sbp_model *> &models, const std::vector<uint
     for (int q = 0; q < nj; ++q) {
         const int i = order[(size_t)q];
         sbp_model *m = models[(size_t)i];
+        m->nb_ok = false;  // the persistent kernel moves labels without the block-labelled rows
         if (!m->movers) {
             // on this stream, which runs the kernel that first uses them
             if (model_alloc(&m->movers, (size_t)(m->g->n > 0 ? m->g->n : 1) * sizeof(Mover), st) != cudaSuccess ||

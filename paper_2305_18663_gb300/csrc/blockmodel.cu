@@ -247,6 +247,55 @@ __global__ void __launch_bounds__(kThreads) k_delta_items(GraphDev g, const int2
     }
 }
 
+// block-labelled rows from scratch: out-entry e (u -> w) gets b[w], its twin
+// in w's in-row gets b[u]; bit 31 marks a self-loop
+__global__ void k_nb_full(GraphDev g, const int32_t *__restrict__ b, int32_t *__restrict__ nbo,
+                          int32_t *__restrict__ nbi) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int u = g.esrc[e], w = g.oc[e];
+        const int32_t self = u == w ? kNbSelf : 0;
+        nbo[e] = b[w] | self;
+        nbi[g.tw_oi[e]] = b[u] | self;
+    }
+}
+
+// the entries that name a moved vertex, after a pass: for every item of
+// the accepted-move list (a 256-edge slice of moved vertex v's rows), the
+// twin of each of v's edges takes v's new label
+__global__ void __launch_bounds__(kThreads) k_nb_items(GraphDev g, const int2 *__restrict__ items,
+                                                       const DevCounters *__restrict__ c, int64_t cap,
+                                                       const int32_t *__restrict__ b, int32_t *__restrict__ nbo,
+                                                       int32_t *__restrict__ nbi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)(c->items < (unsigned long long)cap ? c->items : (unsigned long long)cap);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int kPer = kMoveChunk / 32;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+        const int2 it = items[w];
+        const int v = it.x;
+        const int s = b[v];
+        const int o0 = g.op[v], kout = g.op[v + 1] - o0;
+        const int i0 = g.ip[v], k = kout + (g.ip[v + 1] - i0);
+        const int lo = it.y * kMoveChunk;
+        int nb[kPer], tw[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int idx = lo + j * 32 + lane;
+            const bool ok = idx < k, out = idx < kout;
+            nb[j] = ok ? (out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
+            tw[j] = ok ? (out ? g.tw_oi[o0 + idx] : g.tw_io[i0 + idx - kout]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int idx = lo + j * 32 + lane;
+            if (nb[j] < 0) continue;
+            const int32_t x = s | (nb[j] == v ? kNbSelf : 0);
+            if (idx < kout) nbi[tw[j]] = x;  // v -> w: in w's in-row
+            else nbo[tw[j]] = x;             // w -> v: in w's out-row
+        }
+    }
+}
+
 __global__ void k_relabel(int32_t *__restrict__ b, int32_t *__restrict__ bnew, int n, const int32_t *__restrict__ map) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int x = map[b[v]];
@@ -417,6 +466,7 @@ int build_blockmodel(sbp_model *m, bool after_pass) {
 // a rebuild from m->b drops the pending decisions, and with them the
 // accepted-move list
 int rebuild_blockmodel(sbp_model *m) {
+    m->nb_ok = false;
     m->list_ok = true;
     m->decided.clear();
     SBP_CUDA(cudaMemsetAsync(&m->counters->items, 0, sizeof(unsigned long long), m->stream));
@@ -438,6 +488,43 @@ int launch_prefix(sbp_model *m) {
 // moved edges (decided on the device, no host round trip); the result is
 // the same M as a recount.
 int commit_blockmodel(sbp_model *m) { return build_blockmodel(m, !m->p.full_rebuild); }
+
+// block-labelled rows from m->b (allocated on first use).  Without the
+// memory for them nb_ok stays false and the pass gathers labels instead.
+int nb_rows_rebuild(sbp_model *m) {
+    const sbp_graph *g = m->g;
+    if (!m->nbo) {
+        const size_t bytes = (size_t)(g->m > 0 ? g->m : 1) * 4;
+        if (model_alloc((void **)&m->nbo, bytes, m->stream) != cudaSuccess ||
+            model_alloc((void **)&m->nbi, bytes, m->stream) != cudaSuccess) {
+            cudaGetLastError();
+            model_free(m->nbo, m->stream);
+            model_free(m->nbi, m->stream);
+            m->nbo = m->nbi = nullptr;
+            return SBP_OK;
+        }
+    }
+    if (g->m > 0) {
+        k_nb_full<<<grid_for(g->m, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(g->dev(), m->b, m->nbo, m->nbi);
+        SBP_LAUNCHED();
+    }
+    m->nb_ok = true;
+    return SBP_OK;
+}
+
+// after a commit: the block-labelled rows follow the accepted moves, or are
+// marked stale when the list does not hold every change
+int nb_rows_after_commit(sbp_model *m) {
+    if (!m->nb_ok || !m->nbo) return SBP_OK;
+    if (!m->list_ok || !m->items) {
+        m->nb_ok = false;
+        return SBP_OK;
+    }
+    k_nb_items<<<num_sms() * 4, kThreads, 0, m->stream>>>(m->g->dev(), m->items, m->counters, m->cap_items, m->b,
+                                                          m->nbo, m->nbi);
+    SBP_LAUNCHED();
+    return SBP_OK;
+}
 
 int launch_relabel(sbp_model *m, const int32_t *map_dev) {
     const int n = (int)m->g->n;

@@ -85,6 +85,8 @@ struct GraphDev {
     const int32_t *op, *ip;  // [n+1] out / in row offsets
     const int32_t *oc, *ic;  // [m] neighbours, ascending per row
     const int32_t *esrc;     // [m] source vertex of each out-edge (CSR order)
+    const int32_t *tw_oi;    // [m] in-row position of each out-row entry (the same edge)
+    const int32_t *tw_io;    // [m] out-row position of each in-row entry
 };
 
 }  // namespace sbp
@@ -93,6 +95,7 @@ struct sbp_graph {
     int64_t n = 0, m = 0;
     int device = 0;
     int32_t *op = nullptr, *ip = nullptr, *oc = nullptr, *ic = nullptr, *esrc = nullptr;
+    int32_t *tw_oi = nullptr, *tw_io = nullptr;  // twin positions of each edge in the other CSR
     int32_t *order = nullptr;  // vertices grouped: k=0 | 1..32 | 33..128 | >128
     int32_t *by_degree = nullptr;  // all vertices by degree, descending (ties: lower id first)
     int64_t bin[5] = {0, 0, 0, 0, 0};
@@ -100,6 +103,7 @@ struct sbp_graph {
     sbp::GraphDev dev() const {
         sbp::GraphDev d;
         d.n = (int32_t)n; d.m = m; d.op = op; d.ip = ip; d.oc = oc; d.ic = ic; d.esrc = esrc;
+        d.tw_oi = tw_oi; d.tw_io = tw_io;
         return d;
     }
 };
@@ -139,12 +143,19 @@ struct ModelDev {
     const int32_t *rc, *cr;           // column of each row entry, row of each column entry
     const int32_t *rv, *cv;           // their counts
     const uint32_t *rpre, *cpre;      // inclusive count prefixes inside each row / column
+    const uint32_t *rpc, *cpc;        // [B * 32]: pivot i of a row is its prefix at the end of
+                                      // the i-th of 32 equal segments (all ones past the row)
     const int2 *hkv;                  // table slots: (key, count), key -1 when empty
     int32_t *status;
     DevCounters *counters;
     int2 *items;        // accepted-move list (NULL: not kept)
     int64_t cap_items;
+    // block-labelled rows: nbo[e] = b[oc[e]], nbi[j] = b[ic[j]], bit 31 set
+    // when the neighbour is the row's own vertex (NULL: gather b instead)
+    const int32_t *nbo, *nbi;
 };
+
+constexpr int32_t kNbSelf = INT32_MIN;  // self-loop bit of a block-labelled entry
 
 }  // namespace sbp
 
@@ -160,6 +171,7 @@ struct sbp_model {
         uint64_t *cval0 = nullptr, *cval1 = nullptr;
         int2 *hkv = nullptr;  // per-row open-addressing slots (key, count)
         uint32_t *rp = nullptr, *cp = nullptr, *hoff = nullptr, *cnt = nullptr;
+        uint32_t *rpc = nullptr, *cpc = nullptr;  // [B * 32] coarse pivots of rpre / cpre per row / column
         int32_t *cells = nullptr;  // B x B counts of the counting-sort rebuild
         int64_t cap_cells = 0;
         int32_t cells_B = 0;       // B the cells hold the counts of m->bnew for, else 0
@@ -198,6 +210,10 @@ struct sbp_model {
     // not hold (labels set from outside, overlapping decide ranges)
     int2 *items = nullptr;
     int64_t cap_items = 0;
+    // block-labelled copy of the adjacency (nbo: out-rows, nbi: in-rows);
+    // nb_ok: it matches m->b
+    int32_t *nbo = nullptr, *nbi = nullptr;
+    bool nb_ok = false;
     bool list_ok = true;
     std::vector<std::pair<int64_t, int64_t>> decided;  // decide ranges since the last commit
     // side streams of the decision pass: the three degree groups' kernels
@@ -403,6 +419,23 @@ __device__ __forceinline__ int Mat(const ModelDev &md, int r, int c) {
     return md.sparse ? sparse_at(md, r, c) : md.M[(size_t)r * md.B + c];
 }
 
+// v's idx-th neighbour entry (out-row first): its block-labelled entry when
+// the pass keeps them, else the neighbour's id
+__device__ __forceinline__ int nb_raw(const GraphDev &g, const ModelDev &md, int o0, int i0, int kout, int idx) {
+    if (md.nbo) return idx < kout ? md.nbo[o0 + idx] : md.nbi[i0 + idx - kout];
+    return idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout];
+}
+
+// the block of an entry from nb_raw, and whether the neighbour is v itself
+__device__ __forceinline__ int nb_block(const ModelDev &md, int raw, int v, bool &self) {
+    if (md.nbo) {
+        self = raw < 0;
+        return raw & 0x7fffffff;
+    }
+    self = raw == v;
+    return md.b[raw];
+}
+
 // continues a probe of row table [off, off + cap) for key c whose first
 // slot h has been loaded into kv (same bound and result as sparse_at)
 __device__ __forceinline__ int sparse_probe_from(const ModelDev &md, uint32_t off, uint32_t cap, uint32_t h, int c,
@@ -472,14 +505,51 @@ __device__ __forceinline__ uint32_t lane_lower_i32(const int32_t *__restrict__ a
     return lo;
 }
 
+// first i in pre[lo, hi) with pre[i] > t (pre non-decreasing, pre[hi-1] > t),
+// with the row's 32 pivots: the eight 16-byte pivot loads and then up to
+// eight entries of the segment are in flight together
+__device__ __forceinline__ uint32_t pivot_upper(const uint32_t *pre, const uint32_t *piv, uint32_t lo, uint32_t hi,
+                                                uint32_t t) {
+    const uint32_t len = hi - lo;
+    uint32_t seg = len;
+    if (len > 32) {
+        uint4 pv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pv[i] = reinterpret_cast<const uint4 *>(piv)[i];
+        uint32_t fp = 31;
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
+            if (pv[i].w > t) fp = 4 * i + 3;
+            if (pv[i].z > t) fp = 4 * i + 2;
+            if (pv[i].y > t) fp = 4 * i + 1;
+            if (pv[i].x > t) fp = 4 * i;
+        }
+        const uint32_t step = (len + 31) / 32;
+        lo += fp * step;
+        seg = step < hi - lo ? step : hi - lo;
+    }
+    if (seg > 32) return lane_upper(pre, lo, lo + seg, t);
+    for (uint32_t g0 = 0; g0 < seg; g0 += 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = g0 + i < seg ? pre[lo + g0 + i] : 0xffffffffu;
+        int idx = -1;
+#pragma unroll
+        for (int i = 7; i >= 0; --i)
+            if (x[i] > t) idx = i;
+        if (idx >= 0) return lo + g0 + (uint32_t)idx;
+    }
+    return lo + seg - 1;
+}
+
 // Sparse inverse CDF over row u then column u of M (weights M[u][c], then
 // M[c][u]), t < dout_u + din_u: the block at that position.  One lane.
 __device__ __forceinline__ int sparse_cdf_block(const ModelDev &md, int u, uint32_t t, uint32_t dout_u) {
     if (t < dout_u) {
-        const uint32_t i = lane_upper(md.rpre, md.rp[u], md.rp[u + 1], t);
+        const uint32_t i = pivot_upper(md.rpre, md.rpc + (size_t)u * 32, md.rp[u], md.rp[u + 1], t);
         return md.rc[i];
     }
-    const uint32_t i = lane_upper(md.cpre, md.cp[u], md.cp[u + 1], t - dout_u);
+    const uint32_t i = pivot_upper(md.cpre, md.cpc + (size_t)u * 32, md.cp[u], md.cp[u + 1], t - dout_u);
     return md.cr[i];
 }
 
@@ -491,6 +561,8 @@ int update_cells(sbp_model *m, int32_t *cells);  // counts of m->bnew -> counts 
 int launch_prefix(sbp_model *m);                 // P, Pc, degrees, reciprocals from a dense M
 int commit_blockmodel(sbp_model *m);   // the same after a pass: m->b new labels, m->bnew the previous ones
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace);
+int nb_rows_rebuild(sbp_model *m);       // block-labelled rows from m->b (nb_ok when there is memory)
+int nb_rows_after_commit(sbp_model *m);  // ... brought up to date after a commit
 int launch_merge_proposals(sbp_model *m, uint64_t round_id);
 int launch_relabel(sbp_model *m, const int32_t *map_dev);
 int launch_vertex_count(sbp_model *m);

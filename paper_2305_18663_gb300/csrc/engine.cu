@@ -43,7 +43,7 @@ double now_s() {
 // device bytes of a graph's model at its largest (sparse rows at B = N)
 size_t model_bytes(const sbp_graph *g, int dense_max_B) {
     const size_t n = (size_t)g->n, m = (size_t)std::max<int64_t>(g->m, 1);
-    return 144 * m + 128 * n + 12 * (size_t)dense_max_B * (size_t)dense_max_B + (1u << 20);
+    return 152 * m + 128 * n + 12 * (size_t)dense_max_B * (size_t)dense_max_B + (1u << 20);
 }
 
 }  // namespace

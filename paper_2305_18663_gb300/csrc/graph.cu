@@ -83,6 +83,18 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     std::vector<int32_t> esrc((size_t)std::max<int64_t>(m, 1));
     for (int64_t v = 0; v < n; ++v)
         for (int32_t e = op[(size_t)v]; e < op[(size_t)v + 1]; ++e) esrc[(size_t)e] = (int32_t)v;
+    // twins: out-rows visited by ascending source meet every in-row's
+    // entries (ascending source, duplicates adjacent) in their order, so a
+    // cursor per in-row pairs the k-th copy of an edge with its k-th copy
+    std::vector<int32_t> tw_oi((size_t)std::max<int64_t>(m, 1)), tw_io((size_t)std::max<int64_t>(m, 1));
+    {
+        std::vector<int32_t> cur(ip.begin(), ip.end() - 1);
+        for (int64_t e = 0; e < m; ++e) {
+            const int32_t j = cur[(size_t)oc[(size_t)e]]++;
+            tw_oi[(size_t)e] = j;
+            tw_io[(size_t)j] = (int32_t)e;
+        }
+    }
 
     // degree groups: k = 0 | 1..32 | 33..128 | > 128, each in id order
     std::vector<int32_t> order((size_t)n);
@@ -118,6 +130,8 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     if (rc == SBP_OK) rc = upload(&g->oc, oc.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->ic, ic.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->esrc, esrc.data(), (size_t)m);
+    if (rc == SBP_OK) rc = upload(&g->tw_oi, tw_oi.data(), (size_t)m);
+    if (rc == SBP_OK) rc = upload(&g->tw_io, tw_io.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->order, order.data(), (size_t)n);
     if (rc == SBP_OK) rc = upload(&g->by_degree, by_degree.data(), (size_t)n);
     if (rc != SBP_OK) {
@@ -142,6 +156,8 @@ extern "C" void sbp_free_graph(sbp_graph_t *g) {
     cudaFree(g->oc);
     cudaFree(g->ic);
     cudaFree(g->esrc);
+    cudaFree(g->tw_oi);
+    cudaFree(g->tw_io);
     cudaFree(g->order);
     cudaFree(g->by_degree);
     delete g;

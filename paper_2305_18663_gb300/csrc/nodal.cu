@@ -124,20 +124,25 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             bool ok = true;
             for (int base = 0; base < k; base += 128) {
                 int nb[4], tb[4];
+                bool sf[4];
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
                     const int idx = base + c4 * 32 + lane;
-                    nb[c4] = idx < k ? (idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
+                    nb[c4] = idx < k ? nb_raw(g, md, o0, i0, kout, idx) : 0;
                 }
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) tb[c4] = nb[c4] >= 0 ? md.b[nb[c4]] : -1;
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int idx = base + c4 * 32 + lane;
+                    sf[c4] = false;
+                    tb[c4] = idx < k ? nb_block(md, nb[c4], v, sf[c4]) : -1;
+                }
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
                     const int cb = base + c4 * 32;
                     if (cb >= k) break;
                     const int idx = cb + lane;
                     const bool valid = idx < k, is_out = idx < kout;
-                    const bool is_self = valid && nb[c4] == v;
+                    const bool is_self = valid && sf[c4];
                     self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
                     const int key = (valid && !is_self) ? tb[c4] : -1;
                     const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -211,14 +216,19 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
 #pragma unroll
             for (int c8 = 0; c8 < kDirectChunks; ++c8) {
                 const int idx = base + c8 * 32 + lane;
-                nb[c8] = idx < k ? (idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
+                nb[c8] = idx < k ? nb_raw(g, md, o0, i0, kout, idx) : 0;
             }
-#pragma unroll
-            for (int c8 = 0; c8 < kDirectChunks; ++c8) tb[c8] = nb[c8] >= 0 ? md.b[nb[c8]] : -1;
+            bool sf[kDirectChunks];
 #pragma unroll
             for (int c8 = 0; c8 < kDirectChunks; ++c8) {
                 const int idx = base + c8 * 32 + lane;
-                const bool is_out = idx < kout, is_self = nb[c8] == v;
+                sf[c8] = false;
+                tb[c8] = idx < k ? nb_block(md, nb[c8], v, sf[c8]) : -1;
+            }
+#pragma unroll
+            for (int c8 = 0; c8 < kDirectChunks; ++c8) {
+                const int idx = base + c8 * 32 + lane;
+                const bool is_out = idx < kout, is_self = idx < k && sf[c8];
                 self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
                 bool fresh = false;
                 if (tb[c8] >= 0 && !is_self) fresh = atomicAdd(&cnt[tb[c8]], is_out ? 1u : 0x10000u) == 0u;
@@ -294,9 +304,9 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         for (int base = 0; base < k; base += blockDim.x) {
             const int idx = base + tid;
             const bool valid = idx < k, is_out = idx < kout;
-            const int nb = valid ? (is_out ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
-            const int tb = valid ? md.b[nb] : -1;
-            const bool is_self = valid && nb == v;
+            bool sfl = false;
+            const int tb = valid ? nb_block(md, nb_raw(g, md, o0, i0, kout, idx), v, sfl) : -1;
+            const bool is_self = valid && sfl;
             const int nself = __popc(__ballot_sync(0xffffffffu, is_self && is_out));
             if (lane == 0 && nself) atomicAdd(&sh.self, nself);
             const int key = (valid && !is_self) ? tb : -1;
@@ -581,14 +591,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                 vq[c4] = __shfl_sync(0xffffffffu, v, q);
                 const int e = p - fq;
                 tag[c4] = (q << 26) | (e < kq ? 0 : 1);
-                nb[c4] = pp < total ? (e < kq ? g.oc[oq + e] : g.ic[iq + e - kq]) : -1;
+                nb[c4] = pp < total ? nb_raw(g, md, oq, iq, kq, e) : 0;
             }
 #pragma unroll
             for (int c4 = 0; c4 < kP2; ++c4) {
                 const int pp = base + c4 * 32 + lane;
-                if (nb[c4] >= 0) {
-                    const int t = md.b[nb[c4]];
-                    W.key[pp] = nb[c4] == vq[c4] ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
+                if (pp < total) {
+                    bool sfl;
+                    const int t = nb_block(md, nb[c4], vq[c4], sfl);
+                    W.key[pp] = sfl ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
                 }
             }
         }
@@ -1120,11 +1131,15 @@ ModelDev model_dev(sbp_model *m) {
     d.cv = m->sp.cv;
     d.rpre = m->sp.rpre;
     d.cpre = m->sp.cpre;
+    d.rpc = m->sp.rpc;
+    d.cpc = m->sp.cpc;
     d.hkv = m->sp.hkv;
     d.status = m->status;
     d.counters = m->counters;
     d.items = nullptr;  // set by the nodal pass only
     d.cap_items = 0;
+    d.nbo = nullptr;
+    d.nbi = nullptr;
     return d;
 }
 
@@ -1266,6 +1281,16 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.md = model_dev(m);
     a.md.items = m->items;
     a.md.cap_items = m->cap_items;
+    const int64_t h_seq = std::min<int64_t>(m->p.hybrid_h, g->n);
+    if (h_seq > 0 && m->dense && v_begin == 0 && v_end == g->n) {
+        m->nb_ok = false;  // the sequential part moves vertices in place
+    } else {
+        if (!m->nb_ok) SBP_TRY(nb_rows_rebuild(m));
+        if (m->nb_ok) {
+            a.md.nbo = m->nbo;
+            a.md.nbi = m->nbi;
+        }
+    }
     a.v_begin = v_begin;
     a.v_end = v_end;
     a.movers = static_cast<Mover *>(m->movers);

@@ -481,8 +481,8 @@ __device__ __forceinline__ Proposal propose_vertex(const GraphDev &g, const Mode
     if (p.k == 0) return p;
     const U64x4 w = philox4x64_10(sweep_id, (uint64_t)v, 0, 0, seed, 0);
     const int j = (int)draw_below(w.x, (uint64_t)p.k);
-    const int nb = j < kout ? g.oc[o0 + j] : g.ic[i0 + j - kout];
-    const int u = md.b[nb];
+    bool self_nb;
+    const int u = nb_block(md, nb_raw(g, md, o0, i0, kout, j), v, self_nb);
     const int64_t du = md.dsum[u];
     const int64_t y = draw_below(w.y, (uint64_t)(du + B));
     if (y < B) {

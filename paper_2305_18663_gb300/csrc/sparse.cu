@@ -501,6 +501,29 @@ int alloc(sbp_model *m, T **p, int64_t count) {
     return SBP_OK;
 }
 
+// the 32 pivots of every row (threads [0, 32 B)) and column (threads
+// [32 B, 64 B)) of the sparse M: pivot i is the row's inclusive prefix at the
+// end of its i-th segment of ceil(len / 32) entries, all ones past the row
+__global__ void k_sparse_pivots(const uint32_t *__restrict__ rp, const uint32_t *__restrict__ rpre,
+                                const uint32_t *__restrict__ cp, const uint32_t *__restrict__ cpre, int B,
+                                uint32_t *__restrict__ rpc, uint32_t *__restrict__ cpc) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= 64 * (int64_t)B) return;
+    const bool col = x >= 32 * (int64_t)B;
+    const int64_t y = col ? x - 32 * (int64_t)B : x;
+    const int u = (int)(y >> 5), i = (int)(y & 31);
+    const uint32_t *p = col ? cp : rp;
+    const uint32_t *pre = col ? cpre : rpre;
+    const uint32_t lo = p[u], len = p[u + 1] - lo;
+    const uint32_t step = (len + 31) / 32;
+    uint32_t v = 0xffffffffu;
+    if ((uint32_t)i * step < len) {
+        const uint32_t end = ((uint32_t)i + 1) * step < len ? ((uint32_t)i + 1) * step : len;
+        v = pre[lo + end - 1];
+    }
+    (col ? cpc : rpc)[y] = v;
+}
+
 }  // namespace
 
 // The rebuild counts cells instead of sorting keys when the B x B key space
@@ -545,6 +568,8 @@ int ensure_sparse_capacity(sbp_model *m, int32_t B) {
         SBP_TRY(alloc(m, &S.cp, (int64_t)B + 1));
         SBP_TRY(alloc(m, &S.hoff, (int64_t)B + 1));
         SBP_TRY(alloc(m, &S.cnt, (int64_t)B + 1));
+        SBP_TRY(alloc(m, &S.rpc, (int64_t)B * 32));
+        SBP_TRY(alloc(m, &S.cpc, (int64_t)B * 32));
         S.cap_b = B;
     }
     return SBP_OK;
@@ -621,6 +646,9 @@ int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
         k_small_finish<<<1, kSmallThreads, 0, st>>>(m->dout, m->din, B, lpart, lfb, m->dsum, m->rcp, m->rcp32, E,
                                                     g->n, m->dl);
         SBP_LAUNCHED();
+        k_sparse_pivots<<<(int)((64 * (int64_t)B + kT - 1) / kT), kT, 0, st>>>(S.rp, S.rpre, S.cp, S.cpre, B, S.rpc,
+                                                                              S.cpc);
+        SBP_LAUNCHED();
         S.nnz = -1;  // on the device until someone asks
         *dl_done = true;
         return SBP_OK;
@@ -679,6 +707,8 @@ int rebuild_sparse(sbp_model *m, bool after_pass, bool *dl_done) {
     SBP_TRY(exclusive_scan_u32(S.cnt, S.cp, (int64_t)B + 1, nullptr, sscr, st));
     k_row_prefix<<<grid_of((int64_t)B * 32, cap), kT, 0, st>>>(S.cp, S.cv, B, S.cpre, m->din);
     SBP_LAUNCHED();
+    k_sparse_pivots<<<(int)((64 * (int64_t)B + kT - 1) / kT), kT, 0, st>>>(S.rp, S.rpre, S.cp, S.cpre, B, S.rpc, S.cpc);
+    SBP_LAUNCHED();
     // 5. per-row hash tables
     k_hash_caps<<<grid_of(B, cap), kT, 0, st>>>(S.rp, B, S.cnt);
     SBP_LAUNCHED();
@@ -710,7 +740,8 @@ int64_t sparse_nnz(sbp_model *m) {
 void free_sparse(sbp_model *m) {
     sbp_model::Sparse &S = m->sp;
     void *ps[] = {S.key0, S.key1, S.start, S.rc, S.rv, S.rowof, S.rpre, S.cr, S.cv, S.cpre, S.ckey0,
-                  S.ckey1, S.cval0, S.cval1, S.hkv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells, S.nnz_dev};
+                  S.ckey1, S.cval0, S.cval1, S.hkv, S.scratch, S.rp, S.cp, S.hoff, S.cnt, S.cells, S.nnz_dev,
+                  S.rpc,  S.cpc};
     for (void *p : ps) model_free(p, m->stream);
     S = sbp_model::Sparse();
 }
