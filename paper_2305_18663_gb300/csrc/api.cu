@@ -380,6 +380,7 @@ extern "C" int sbp_commit(sbp_model_t *m, sbp_sweep_stats *stats) {
     if (!m) return fail(SBP_EINVAL, "sbp_commit: NULL model");
     std::swap(m->b, m->bnew);
     SBP_CUDA(cudaMemcpyAsync(m->dl + 1, m->dl, 8, cudaMemcpyDeviceToDevice, m->stream));
+    m->nb_in_commit = false;
     int rc = commit_blockmodel(m);
     if (rc == SBP_OK) rc = nb_rows_after_commit(m);
     if (rc != SBP_OK) m->nb_ok = false;

@@ -199,13 +199,17 @@ __global__ void __launch_bounds__(kThreads) k_delta_dense(GraphDev g, const int3
 // kMoveChunk-edge slice of the concatenated (out, in) row of a moved vertex,
 // so hubs are spread over many warps and no warp scans unmoved vertices.
 // Lane j of the warp takes edges j, j + 32, ... of the slice, all loads in
-// flight together.
+// flight together.  With nbo (not NULL) it also brings the block-labelled
+// rows up to date (the twin of each edge takes v's new label), whatever the
+// plan; the count update runs only when the plan chose it.
 __global__ void __launch_bounds__(kThreads) k_delta_items(GraphDev g, const int2 *__restrict__ items,
                                                           const DevCounters *__restrict__ c, int64_t cap,
                                                           const int32_t *__restrict__ bnew,
                                                           const int32_t *__restrict__ bold, int32_t *__restrict__ M,
-                                                          int B, const int32_t *__restrict__ flag) {
-    if (*flag != 1) return;
+                                                          int B, const int32_t *__restrict__ flag,
+                                                          int32_t *__restrict__ nbo, int32_t *__restrict__ nbi) {
+    const bool counts = *flag == 1;
+    if (!counts && !nbo) return;
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)(c->items < (unsigned long long)cap ? c->items : (unsigned long long)cap);
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -224,6 +228,17 @@ __global__ void __launch_bounds__(kThreads) k_delta_items(GraphDev g, const int2
             const int idx = lo + j * 32 + lane;
             nb[j] = idx < k ? (idx < kout ? g.oc[o0 + idx] : g.ic[i0 + idx - kout]) : -1;
         }
+        if (nbo) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int idx = lo + j * 32 + lane;
+                if (nb[j] < 0) continue;
+                const int32_t x = s | (nb[j] == v ? kNbSelf : 0);
+                if (idx < kout) nbi[g.tw_oi[o0 + idx]] = x;  // v -> w: in w's in-row
+                else nbo[g.tw_io[i0 + idx - kout]] = x;     // w -> v: in w's out-row
+            }
+        }
+        if (!counts) continue;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             t[j] = nb[j] >= 0 ? bold[nb[j]] : 0;
@@ -405,9 +420,13 @@ int update_cells(sbp_model *m, int32_t *cells) {
                                                                                                   flag);
         SBP_LAUNCHED();
         if (m->list_ok && m->items) {
+            // the block-labelled rows follow in the same pass
+            const bool nb = m->nb_ok && m->nbo;
             k_delta_items<<<sms * 4, kThreads, 0, m->stream>>>(g->dev(), m->items, m->counters, m->cap_items, m->b,
-                                                               m->bnew, cells, B, flag);
+                                                               m->bnew, cells, B, flag, nb ? m->nbo : nullptr,
+                                                               nb ? m->nbi : nullptr);
             SBP_LAUNCHED();
+            m->nb_in_commit = nb;
         } else {
             const int64_t n_big = g->n - g->bin[3];
             const int64_t warps = n_big + (g->n + 31) / 32;
@@ -515,6 +534,10 @@ int nb_rows_rebuild(sbp_model *m) {
 // after a commit: the block-labelled rows follow the accepted moves, or are
 // marked stale when the list does not hold every change
 int nb_rows_after_commit(sbp_model *m) {
+    if (m->nb_in_commit) {  // updated by the apply step's kernel
+        m->nb_in_commit = false;
+        return SBP_OK;
+    }
     if (!m->nb_ok || !m->nbo) return SBP_OK;
     if (!m->list_ok || !m->items) {
         m->nb_ok = false;

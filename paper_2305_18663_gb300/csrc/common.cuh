@@ -214,6 +214,7 @@ struct sbp_model {
     // nb_ok: it matches m->b
     int32_t *nbo = nullptr, *nbi = nullptr;
     bool nb_ok = false;
+    bool nb_in_commit = false;  // the apply step's kernel updated them in this commit
     bool list_ok = true;
     std::vector<std::pair<int64_t, int64_t>> decided;  // decide ranges since the last commit
     // side streams of the decision pass: the three degree groups' kernels
