@@ -152,20 +152,34 @@ int read_stats(sbp_model *m, sbp_sweep_stats *out) {
     return SBP_OK;
 }
 
+// labels outside [0, B): the slot keeps INT32_MAX - (smallest such vertex)
+__global__ void k_check_labels(const int32_t *__restrict__ b, int64_t n, int32_t B, int32_t *__restrict__ slot) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (b[v] < 0 || b[v] >= B) atomicMax(slot, (int32_t)(INT32_MAX - v));
+}
+
+// The labels go to the pending buffer, are checked on the device (one read
+// back), and only then become the assignment: a bad label leaves the model
+// as it was.
 int upload_assignment(sbp_model *m, int32_t B, const int32_t *b) {
     const int64_t n = m->g->n;
     if (B < 1 || B > n) return fail(SBP_EINVAL, "B must be in [1, n]");
     if (!b) return fail(SBP_EINVAL, "assignment pointer is NULL");
-    // validate labels on the host copy
-    std::vector<int32_t> hb((size_t)n);
-    SBP_CUDA(cudaMemcpy(hb.data(), b, (size_t)n * 4, is_device_ptr(b) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-    for (int64_t v = 0; v < n; ++v)
-        if (hb[(size_t)v] < 0 || hb[(size_t)v] >= B)
-            return fail(SBP_EINVAL, "label out of [0, B) at vertex " + std::to_string(v));
+    int32_t *slot = m->status + 2;
+    SBP_CUDA(cudaMemcpyAsync(m->bnew, b, (size_t)n * 4, cudaMemcpyDefault, m->stream));
+    SBP_CUDA(cudaMemsetAsync(slot, 0, 4, m->stream));
+    k_check_labels<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, m->stream>>>(m->bnew, n, B, slot);
+    SBP_LAUNCHED();
+    int32_t *h = static_cast<int32_t *>(m->pinned);
+    SBP_CUDA(cudaMemcpyAsync(h, slot, 4, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    if (*h > 0) {
+        SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)n * 4, cudaMemcpyDeviceToDevice, m->stream));
+        return fail(SBP_EINVAL, "label out of [0, B) at vertex " + std::to_string((int64_t)INT32_MAX - *h));
+    }
     SBP_TRY(ensure_capacity(m, B));
     m->B = B;
-    SBP_CUDA(cudaMemcpyAsync(m->b, hb.data(), (size_t)n * 4, cudaMemcpyHostToDevice, m->stream));
-    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    std::swap(m->b, m->bnew);
     return rebuild_blockmodel(m);
 }
 
@@ -295,7 +309,7 @@ extern "C" int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32
         model_alloc((void **)&m->dl, 16, st) != cudaSuccess ||
         model_alloc((void **)&m->partials, (size_t)m->npartials * 32, st) != cudaSuccess ||
         model_alloc((void **)&m->counters, sizeof(DevCounters), st) != cudaSuccess ||
-        model_alloc((void **)&m->status, 8, st) != cudaSuccess || !m->pinned) {
+        model_alloc((void **)&m->status, 16, st) != cudaSuccess || !m->pinned) {
         cudaGetLastError();
         sbp_free_model(m);
         return fail(SBP_ENOMEM, "sbp_build_blockmodel: allocation failed");
