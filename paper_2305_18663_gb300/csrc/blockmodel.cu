@@ -145,13 +145,15 @@ __global__ void __launch_bounds__(kThreads) k_dl_final(const DlPartial *__restri
     }
 }
 
-// commit plan: 1 = update M from the moved vertices' rows, 0 = recount
-__global__ void k_commit_plan(const DevCounters *__restrict__ c, int64_t E, int32_t *__restrict__ flag) {
-    flag[0] = (c->acc_edges * 4ull <= (unsigned long long)E) ? 1 : 0;
-}
-
-__global__ void k_zero_if(int32_t *__restrict__ M, int64_t n, const int32_t *__restrict__ flag, int want) {
-    if (*flag != want) return;
+// commit plan (1 = update the counts from the moved vertices' rows, when
+// they hold at most a quarter of the edges; 0 = recount) and, for a recount,
+// the zeroed cells: every CTA derives the plan from the counters, CTA 0
+// stores it for the kernels that follow
+__global__ void k_commit_plan(const DevCounters *__restrict__ c, int64_t E, int32_t *__restrict__ flag,
+                              int32_t *__restrict__ M, int64_t n) {
+    const int plan = (c->acc_edges * 4ull <= (unsigned long long)E) ? 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag[0] = plan;
+    if (plan != 0) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) M[i] = 0;
 }
 
@@ -408,9 +410,7 @@ int update_cells(sbp_model *m, int32_t *cells) {
     const int sms = num_sms();
     const int64_t BB = (int64_t)B * B;
     int32_t *flag = m->status + 1;
-    k_commit_plan<<<1, 1, 0, m->stream>>>(m->counters, g->m, flag);
-    SBP_LAUNCHED();
-    k_zero_if<<<grid_for(BB, kThreads, sms * 8), kThreads, 0, m->stream>>>(cells, BB, flag, 0);
+    k_commit_plan<<<grid_for(BB, kThreads, sms * 8), kThreads, 0, m->stream>>>(m->counters, g->m, flag, cells, BB);
     SBP_LAUNCHED();
     if (g->m > 0) {
         const size_t smem = (size_t)B * 4;

@@ -239,10 +239,15 @@ __global__ void k_small_lengths(const int32_t *__restrict__ cells, int B, uint32
     const bool col = w >= B;
     const int i = col ? w - B : w;
     uint32_t c = 0;
-    for (int j0 = 0; j0 < B; j0 += 32) {
-        const int j = j0 + lane;
-        const bool nz = j < B && (col ? cells[j * B + i] : cells[i * B + j]) != 0;
-        c += (uint32_t)__popc(__ballot_sync(0xffffffffu, nz));
+    for (int j0 = 0; j0 < B; j0 += 32 * 8) {
+        int32_t x[8];  // eight chunks of the row (or column) in flight
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + 32 * q + lane;
+            x[q] = j < B ? (col ? cells[j * B + i] : cells[i * B + j]) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c += (uint32_t)__popc(__ballot_sync(0xffffffffu, x[q] != 0));
     }
     if (lane == 0) (col ? clen : rlen)[i] = c;
 }
@@ -301,44 +306,55 @@ __global__ void k_small_fill(const int32_t *__restrict__ cells, int B, const uin
     if (!col)
         for (uint32_t q = lane; q < cap; q += 32) hkv[off + q] = make_int2(-1, 0);
     __syncwarp();
-    for (int j0 = 0; j0 < B; j0 += 32) {
-        const int j = j0 + lane;
-        const uint32_t v = j < B ? (uint32_t)(col ? cells[j * B + i] : cells[i * B + j]) : 0u;
-        const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
-        uint32_t incl = v;
+    for (int j8 = 0; j8 < B; j8 += 32 * 8) {
+        uint32_t x8[8];  // eight chunks of the row (or column) in flight
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+        for (int cq = 0; cq < 8; ++cq) {
+            const int j = j8 + 32 * cq + lane;
+            x8[cq] = j < B ? (uint32_t)(col ? cells[j * B + i] : cells[i * B + j]) : 0u;
         }
-        if (v != 0) {
-            const uint32_t q = p + (uint32_t)__popc(nz & ((1u << lane) - 1u));
-            if (col) {
-                cr[q] = j;
-                cv[q] = (int32_t)v;
-                cpre[q] = carry + incl;
-            } else {
-                rc[q] = j;
-                rv[q] = (int32_t)v;
-                rowof[q] = i;
-                rpre[q] = carry + incl;
-                if ((int64_t)v < XT) f += T[v];
-                else fb += (double)v * log((double)v);
-                uint32_t h = sparse_hash(j) & (cap - 1);
-                bool done = false;
-                for (uint32_t t = 0; t < cap; ++t) {
-                    if (atomicCAS(&hkv[off + h].x, -1, j) == -1) {
-                        hkv[off + h].y = (int32_t)v;
-                        done = true;
-                        break;
-                    }
-                    h = (h + 1) & (cap - 1);
-                }
-                if (!done) record_status(status, SBP_EHASHFULL);
+#pragma unroll
+        for (int cq = 0; cq < 8; ++cq) {
+            const int j0 = j8 + 32 * cq;
+            if (j0 >= B) break;
+            const int j = j0 + lane;
+            const uint32_t v = x8[cq];
+            const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
+            if (v != 0) {
+                const uint32_t q = p + (uint32_t)__popc(nz & ((1u << lane) - 1u));
+                if (col) {
+                    cr[q] = j;
+                    cv[q] = (int32_t)v;
+                    cpre[q] = carry + incl;
+                } else {
+                    rc[q] = j;
+                    rv[q] = (int32_t)v;
+                    rowof[q] = i;
+                    rpre[q] = carry + incl;
+                    if ((int64_t)v < XT) f += T[v];
+                    else fb += (double)v * log((double)v);
+                    uint32_t h = sparse_hash(j) & (cap - 1);
+                    bool done = false;
+                    for (uint32_t t = 0; t < cap; ++t) {
+                        if (atomicCAS(&hkv[off + h].x, -1, j) == -1) {
+                            hkv[off + h].y = (int32_t)v;
+                            done = true;
+                            break;
+                        }
+                        h = (h + 1) & (cap - 1);
+                    }
+                    if (!done) record_status(status, SBP_EHASHFULL);
+                }
+            }
+            p += (uint32_t)__popc(nz);
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        p += (uint32_t)__popc(nz);
-        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
     f = warp_sum_128(f);
     fb = warp_sum(fb);
