@@ -44,25 +44,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# the translation unit of the decide-pass kernels (nodal.cu and what it includes)
+DECIDE_SOURCES = ["paper_2305_18663_gb300/csrc/nodal.cu", "paper_2305_18663_gb300/csrc/nodal_dev.cuh",
+                  "paper_2305_18663_gb300/csrc/common.cuh", "include/sbp.h"]
+
+
 def sources_sha256() -> str:
-    """Hash of the library's sources (kernels, host code, C header)."""
+    """Hash of the sources the decide-pass kernels are compiled from."""
     import hashlib
 
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2305_18663_gb300", "csrc")
-    names = [x for x in sorted(os.listdir(csrc)) if x.endswith((".cu", ".cuh", ".h"))]
-    for name in names + ["../../include/sbp.h"]:
-        path = os.path.normpath(os.path.join(csrc, name))
-        if os.path.isfile(path):
-            h.update(name.encode())
-            with open(path, "rb") as f:
-                h.update(f.read())
+    for name in DECIDE_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
 def decide_traffic(m_form: str):
     """DRAM bytes of one decide pass from the committed ncu summary, when it
-    was taken on the current sources and this M form; else None."""
+    was taken on the current decide-pass sources and this M form; else None."""
     path = os.path.join(ROOT, "profiles", "decide_traffic_dcsbm_1m.txt")
     try:
         kv = {}

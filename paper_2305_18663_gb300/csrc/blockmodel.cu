@@ -264,16 +264,23 @@ __global__ void __launch_bounds__(kThreads) k_delta_items(GraphDev g, const int2
     }
 }
 
-// block-labelled rows from scratch: out-entry e (u -> w) gets b[w], its twin
-// in w's in-row gets b[u]; bit 31 marks a self-loop
+// block-labelled rows from scratch, both CSRs in their own order (coalesced
+// writes): out-entry e (u -> w) gets b[w], in-entry j (w -> u) gets b[w];
+// bit 31 marks a self-loop (out-rows: from the edge's source; in-rows: set
+// afterwards at the graph's self-loop positions by k_nb_self)
 __global__ void k_nb_full(GraphDev g, const int32_t *__restrict__ b, int32_t *__restrict__ nbo,
                           int32_t *__restrict__ nbi) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int u = g.esrc[e], w = g.oc[e];
-        const int32_t self = u == w ? kNbSelf : 0;
-        nbo[e] = b[w] | self;
-        nbi[g.tw_oi[e]] = b[u] | self;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.m; e += stride) {
+        const int u = g.esrc[e], w = g.oc[e], x = g.ic[e];
+        nbo[e] = b[w] | (u == w ? kNbSelf : 0);
+        nbi[e] = b[x];
     }
+}
+
+__global__ void k_nb_self(const int32_t *__restrict__ self_in, int64_t n_self, int32_t *__restrict__ nbi) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_self; i += (int64_t)gridDim.x * blockDim.x)
+        nbi[self_in[i]] |= kNbSelf;
 }
 
 // the entries that name a moved vertex, after a pass: for every item of
@@ -525,6 +532,11 @@ int nb_rows_rebuild(sbp_model *m) {
     }
     if (g->m > 0) {
         k_nb_full<<<grid_for(g->m, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(g->dev(), m->b, m->nbo, m->nbi);
+        SBP_LAUNCHED();
+    }
+    if (g->n_self > 0) {
+        k_nb_self<<<grid_for(g->n_self, kThreads, num_sms() * 8), kThreads, 0, m->stream>>>(g->self_in, g->n_self,
+                                                                                           m->nbi);
         SBP_LAUNCHED();
     }
     m->nb_ok = true;

@@ -96,6 +96,8 @@ struct sbp_graph {
     int device = 0;
     int32_t *op = nullptr, *ip = nullptr, *oc = nullptr, *ic = nullptr, *esrc = nullptr;
     int32_t *tw_oi = nullptr, *tw_io = nullptr;  // twin positions of each edge in the other CSR
+    int32_t *self_in = nullptr;  // in-row positions of the self-loops
+    int64_t n_self = 0;
     int32_t *order = nullptr;  // vertices grouped: k=0 | 1..32 | 33..128 | >128
     int32_t *by_degree = nullptr;  // all vertices by degree, descending (ties: lower id first)
     int64_t bin[5] = {0, 0, 0, 0, 0};

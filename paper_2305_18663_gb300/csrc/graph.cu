@@ -87,12 +87,14 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     // entries (ascending source, duplicates adjacent) in their order, so a
     // cursor per in-row pairs the k-th copy of an edge with its k-th copy
     std::vector<int32_t> tw_oi((size_t)std::max<int64_t>(m, 1)), tw_io((size_t)std::max<int64_t>(m, 1));
+    std::vector<int32_t> self_in;
     {
         std::vector<int32_t> cur(ip.begin(), ip.end() - 1);
         for (int64_t e = 0; e < m; ++e) {
             const int32_t j = cur[(size_t)oc[(size_t)e]]++;
             tw_oi[(size_t)e] = j;
             tw_io[(size_t)j] = (int32_t)e;
+            if (oc[(size_t)e] == esrc[(size_t)e]) self_in.push_back(j);
         }
     }
 
@@ -132,6 +134,9 @@ extern "C" int sbp_load_graph(int64_t n, int64_t m, const int32_t *src, const in
     if (rc == SBP_OK) rc = upload(&g->esrc, esrc.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->tw_oi, tw_oi.data(), (size_t)m);
     if (rc == SBP_OK) rc = upload(&g->tw_io, tw_io.data(), (size_t)m);
+    g->n_self = (int64_t)self_in.size();
+    if (self_in.empty()) self_in.push_back(-1);  // the upload keeps one element at least
+    if (rc == SBP_OK) rc = upload(&g->self_in, self_in.data(), self_in.size());
     if (rc == SBP_OK) rc = upload(&g->order, order.data(), (size_t)n);
     if (rc == SBP_OK) rc = upload(&g->by_degree, by_degree.data(), (size_t)n);
     if (rc != SBP_OK) {
@@ -158,6 +163,7 @@ extern "C" void sbp_free_graph(sbp_graph_t *g) {
     cudaFree(g->esrc);
     cudaFree(g->tw_oi);
     cudaFree(g->tw_io);
+    cudaFree(g->self_in);
     cudaFree(g->order);
     cudaFree(g->by_degree);
     delete g;
