@@ -49,15 +49,25 @@ DECIDE_SOURCES = ["paper_2305_18663_gb300/csrc/nodal.cu", "paper_2305_18663_gb30
                   "paper_2305_18663_gb300/csrc/common.cuh", "include/sbp.h"]
 
 
+def code_only(text: str) -> str:
+    """C/C++ source without comments and whitespace (so that edits of the
+    documentation do not count as a change of the kernels)."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def sources_sha256() -> str:
-    """Hash of the sources the decide-pass kernels are compiled from."""
+    """Hash of the code the decide-pass kernels are compiled from."""
     import hashlib
 
     h = hashlib.sha256()
     for name in DECIDE_SOURCES:
         h.update(name.encode())
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, name)) as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()
 
 

@@ -145,14 +145,20 @@ void sbp_free_graph(sbp_graph_t *g);
 /* Creates a blockmodel handle for assignment b (n labels in [0, B), host or
  * device) and builds M, block degrees and DL (Eq. 1-2, Section II-A).
  * stream: a cudaStream_t (may be NULL) that every later call on this model
- * uses.  p may be NULL (defaults).  The graph must outlive the model.
+ * orders its work on (the decision pass of a graph with 2^22 edges or more
+ * runs part of its kernels on two side streams of the model, forked from and
+ * joined back into this stream within the call).  p may be NULL
+ * (defaults).  The graph must outlive the model.
  * Errors: SBP_EINVAL for B < 1, B > n or a label outside [0, B);
  * SBP_ENOMEM. */
 int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32_t *b, const sbp_params *p, void *stream,
                          sbp_model_t **out);
 
 /* Replaces the assignment of an existing model (labels in [0, B), host or
- * device) and rebuilds M and DL. Same errors as sbp_build_blockmodel. */
+ * device) and rebuilds M and DL.  The labels are checked on the device
+ * before they replace the current ones: on SBP_EINVAL (a label outside
+ * [0, B), the smallest such vertex named in the message) the model keeps its
+ * assignment.  Other errors as sbp_build_blockmodel. */
 int sbp_set_assignment(sbp_model_t *m, int32_t B, const int32_t *b);
 
 /* One asynchronous-Gibbs nodal pass restricted to the vertices of
