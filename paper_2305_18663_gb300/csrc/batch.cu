@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob 
                 x.Kin = kin;
                 x.self = self;
                 x.k = kk;
-                evaluate_group<DL32, G>(sa, md, x, mv.w2, [&](auto &&f) {
+                evaluate_group<DL32, G, true>(sa, md, x, mv.w2, [&](auto &&f) {
                     for (int e = gl; e < nl; e += G) {
                         const int t = list[e];
                         const unsigned cc = cnt[t];
@@ -334,7 +334,8 @@ int batch_enqueue(const std::vector<sbp_model *> &models, const std::vector<uint
         m->nb_ok = false;  // the persistent kernel moves labels without the block-labelled rows
         if (!m->movers) {
             // on this stream, which runs the kernel that first uses them
-            if (model_alloc(&m->movers, (size_t)(m->g->n > 0 ? m->g->n : 1) * sizeof(Mover), st) != cudaSuccess ||
+            // the degree groups' lists and the recheck list of the per-graph pass
+            if (model_alloc(&m->movers, (size_t)(m->g->n > 0 ? 2 * m->g->n : 1) * sizeof(Mover), st) != cudaSuccess ||
                 model_alloc((void **)&m->mcount, 4 * sizeof(unsigned), st) != cudaSuccess) {
                 cudaGetLastError();
                 cudaFreeAsync(buf, st);

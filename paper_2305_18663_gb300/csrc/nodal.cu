@@ -13,9 +13,14 @@
 
 #include "nodal_dev.cuh"
 
-// CTAs per SM the warp kernel is compiled for (register budget)
+// CTAs per SM the evaluation kernels are compiled for (register budget:
+// 80 registers at 3, 64 at 4; the direct-mapped kernel for the largest rows
+// fits 4 without spilling once the exact evaluation is a kernel of its own)
 #ifndef SBP_DECIDE_MIN_BLOCKS
 #define SBP_DECIDE_MIN_BLOCKS 3
+#endif
+#ifndef SBP_DIRECT_MIN_BLOCKS
+#define SBP_DIRECT_MIN_BLOCKS 4
 #endif
 
 namespace sbp {
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
 constexpr int kDirectChunks = 8;
 
 template <bool DL32>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_warp_direct(DecideArgs a, int bin,
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DIRECT_MIN_BLOCKS) k_eval_warp_direct(DecideArgs a, int bin,
                                                                                            int warp_words) {
     extern __shared__ unsigned dmw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
             sh.fb_tot = fbt;
             corner_hastings_fast(x, cv, md.B, pft, pbt);
             int dec = -1;
-            if (!a.trace_on) {
+            if (!a.trace_on && !a.force_exact) {
                 if (DL32)
                     dec = fast_decision_f(a.beta32, dlft, 0.0f, pft, pbt, mv.w2, k, dl32_error(amt, k));
                 else
@@ -821,31 +826,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
                 if (dec) accept_move(md, v, s, k);
                 count_result(c, dec != 0, false, k);
             } else {
-                double pf64 = 0.0, pb64 = 0.0;
-                __int128 dle = 0;
-                double fbe = 0.0;
-                for (int e = my_est; e < my_est + my_ecnt; ++e) {
-                    const int t = (int)((unsigned)W.key[e] & 0x3ffffffu);
-                    if (t == r || t == s) continue;
-                    const unsigned ec = W.ec[e];
-                    if (DL32)
-                        entry_exact_all(md, x, t, (int)(ec & 0xffu), (int)(ec >> 8), dle, fbe, pf64, pb64);
-                    else
-                        entry_exact(md, x, t, (int)(ec & 0xffu), (int)(ec >> 8), pf64, pb64);
-                }
-                double dL;
-                if (DL32) {
-#pragma unroll 1
-                    for (int jj = 0; jj < 8; ++jj) special_terms(md, x, jj, dle, fbe);
-                    dL = fix_to_double(dle) + fbe;
-                } else {
-                    dL = fix48_to_double(dl48) + (has_fb ? fb : 0.0);
-                }
-                corner_hastings_exact(x, cv, B, pf64, pb64);
-                const Exact ex = exact_decision_d(a.beta, dL, pf64, pb64, w2);
-                if (ex.accept) accept_move(md, v, s, k);
-                count_exact(c, ex.accept, ex.margin, k);
-                write_trace(a, v, s, 1 | (ex.accept ? 2 : 0) | (ex.margin ? 4 : 0), ex.dH, ex.logA);
+                push_recheck(a, v, s, w2);  // the exact evaluation follows the pass
             }
         }
         __syncwarp();
@@ -1242,13 +1223,36 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
     return SBP_OK;
 }
 
+// the movers the FP32 test left undecided (all of them when a trace is
+// asked for): a CTA each, aggregated again and decided by the exact
+// evaluation, after the three groups' kernels
+template <bool DL32>
+int launch_recheck(sbp_model *m, const DecideArgs &a0, int sms) {
+    const sbp_graph *g = m->g;
+    DecideArgs a = a0;
+    a.force_exact = 1;
+    const int64_t dmax = g->max_deg < m->B ? g->max_deg : m->B;
+    const int64_t need = dmax + dmax / 4 + 2;
+    int cap_log2 = 6;
+    while ((int64_t(1) << cap_log2) < need) ++cap_log2;
+    const int cap = 1 << cap_log2;
+    const size_t smem = (size_t)cap * (8 + 4 + 4);
+    if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
+    SBP_TRY(ensure_dyn_smem((const void *)k_eval_cta<DL32>, smem));
+    k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, m->stream>>>(a, 3, cap, cap_log2);
+    SBP_LAUNCHED();
+    return SBP_OK;
+}
+
 template <bool DL32>
 int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
     cudaStream_t st[3];
     SBP_TRY(fork_evals(m, st));
     const int rc = launch_groups<DL32>(m, a, sms, st);
     const int rj = join_evals(m);  // joined on every path
-    return rc != SBP_OK ? rc : rj;
+    if (rc != SBP_OK) return rc;
+    if (rj != SBP_OK) return rj;
+    return launch_recheck<DL32>(m, a, sms);
 }
 
 }  // namespace
@@ -1256,7 +1260,8 @@ int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
 int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_end, const sbp_vertex_trace *trace) {
     const sbp_graph *g = m->g;
     if (!m->movers) {
-        if (model_alloc(&m->movers, (size_t)(g->n > 0 ? g->n : 1) * sizeof(Mover), m->stream) != cudaSuccess ||
+        // the degree groups' lists (n entries) and the recheck list (n more)
+        if (model_alloc(&m->movers, (size_t)(g->n > 0 ? 2 * g->n : 1) * sizeof(Mover), m->stream) != cudaSuccess ||
             model_alloc((void **)&m->mcount, 4 * sizeof(unsigned), m->stream) != cudaSuccess) {
             cudaGetLastError();
             return fail(SBP_ENOMEM, "cudaMalloc failed for the mover lists");
@@ -1299,6 +1304,8 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
     a.mbase[0] = 0;
     a.mbase[1] = g->bin[2] - g->bin[1];
     a.mbase[2] = a.mbase[1] + (g->bin[3] - g->bin[2]);
+    a.mbase[3] = g->n;  // the recheck list
+    a.force_exact = 0;
     a.seed = m->p.seed;
     a.sweep_id = sweep_id;
     a.beta = m->p.beta;

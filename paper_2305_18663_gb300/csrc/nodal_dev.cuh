@@ -42,9 +42,11 @@ struct DecideArgs {
     GraphDev g;
     ModelDev md;
     int64_t v_begin, v_end;
-    Mover *movers;           // three lists: k <= 32, 33..128, > 128
+    Mover *movers;           // four lists: k <= 32, 33..128, > 128, and the movers
+                             // the FP32 test left to the exact evaluation
     unsigned *mcount;        // their lengths (device counters)
-    int64_t mbase[3];        // their offsets in movers
+    int64_t mbase[4];        // their offsets in movers
+    int force_exact;         // 1: decide every mover by the exact evaluation
     uint64_t seed, sweep_id;
     double beta;
     float beta32;
@@ -56,6 +58,18 @@ struct DecideArgs {
 struct Counts {
     unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0, recheck = 0;
 };
+
+// a mover the FP32 test could not settle (or any mover when a trace is
+// asked for), for the exact evaluation that follows the pass
+__device__ __forceinline__ void push_recheck(const DecideArgs &a, int v, int s, uint64_t w2) {
+    const unsigned i = atomicAdd(&a.mcount[3], 1u);
+    Mover m;
+    m.v = v;
+    m.s = s;
+    m.w2 = w2;
+    a.movers[a.mbase[3] + i] = m;
+}
+
 
 __device__ __forceinline__ void write_trace(const DecideArgs &a, int v, int s, int flags, double dH, double logA) {
     if (a.tr.s) a.tr.s[v] = s;
@@ -505,8 +519,9 @@ __device__ __forceinline__ Proposal propose_vertex(const GraphDev &g, const Mode
 // aligned group of G lanes (G = 32: the whole warp; 8 or 16: several movers
 // per warp).  each_entry(f) calls f(t, ko, ki) for each entry the calling
 // lane holds.  All G lanes call this; the result is written by the group's
-// first lane.
-template <bool DL32, int G, class EachEntry>
+// first lane.  A move the FP32 test cannot settle is decided here by the
+// exact evaluation (INLINE_EXACT) or handed to the recheck list.
+template <bool DL32, int G, bool INLINE_EXACT, class EachEntry>
 __device__ __forceinline__ void evaluate_group(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
                                                EachEntry each_entry, Counts &c) {
     static_assert(G == 8 || G == 16 || G == 32, "group of 8, 16 or 32 lanes");
@@ -571,18 +586,23 @@ __device__ __forceinline__ void evaluate_group(const DecideArgs &a, const ModelD
         dlf = group_sum<G>(dlf, gm);
         am = group_sum<G>(am, gm);
         // at most k / G entries per lane before the group tree
-        if (!a.trace_on) dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, x.k, dl32_error(am, x.k * (32 / G)));
+        if (!a.trace_on && !a.force_exact)
+            dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, x.k, dl32_error(am, x.k * (32 / G)));
     } else {
         dl = group_sum_128<G>(dl, gm);
         has_fb = __any_sync(gm, __double_as_longlong(fb) != 0);
         if (has_fb) fb = group_sum<G>(fb, gm);
-        if (!a.trace_on) dec = fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
+        if (!a.trace_on && !a.force_exact) dec = fast_decision(a.beta32, dl, has_fb, fb, pf, pb, w2, x.k);
     }
     if (dec >= 0) {
         if (gl == 0) {
             if (dec) accept_move(md, x.v, x.s, x.k);
             count_result(c, dec != 0, false, x.k);
         }
+        return;
+    }
+    if constexpr (!INLINE_EXACT) {
+        if (gl == 0) push_recheck(a, x.v, x.s, w2);
         return;
     }
     double pf64 = 0.0, pb64 = 0.0;
@@ -612,11 +632,11 @@ __device__ __forceinline__ void evaluate_group(const DecideArgs &a, const ModelD
     }
 }
 
-// the whole warp on one mover
+// the whole warp on one mover; unsettled moves go to the recheck list
 template <bool DL32, class EachEntry>
 __device__ __forceinline__ void evaluate_warp(const DecideArgs &a, const ModelDev &md, VertexCtx &x, uint64_t w2,
                                               EachEntry each_entry, Counts &c) {
-    evaluate_group<DL32, 32>(a, md, x, w2, each_entry, c);
+    evaluate_group<DL32, 32, false>(a, md, x, w2, each_entry, c);
 }
 
 }  // namespace
