@@ -495,21 +495,34 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
 //   P5 entry parallel: Delta L (table sums, per entry in 64-bit fixed point
 //      at 2^-48) and FP32 Hastings terms, summed per mover by a segmented
 //      warp scan (entries of a mover are contiguous);
-//   P6 lane per mover: corner and degree terms, FP32 test with its band, the
-//      FP64 recheck (sequential over the mover's entries) when needed.
+//   P6 lane per mover: corner and degree terms, FP32 test with its band;
+//      a move the band does not settle goes to the recheck list.
 
-constexpr int kBatchEdges = 32 * kSmallDeg;
+// rows of at most 32 edges: sub-batches of 512 edge ends keep a CTA's
+// shared memory at 38 KB, so that 4 CTAs (64 registers each) fit an SM
+#ifndef SBP_BATCH0_EDGES
+#define SBP_BATCH0_EDGES 512
+#endif
+#ifndef SBP_BATCH0_MIN_BLOCKS
+#define SBP_BATCH0_MIN_BLOCKS 4
+#endif
+constexpr int kBatchEdges = 32 * kSmallDeg;     // edge ends per sub-batch (33..128)
+constexpr int kBatchEdges0 = SBP_BATCH0_EDGES;  // ... for rows of at most 32
 constexpr int kDirectMaxB = 2048;  // direct-mapped per-warp counts up to this B
 
-struct BatchWarp {
-    int key[kBatchEdges];  // edge ends (q << 26 | self << 25 | t << 1 | in), then entries (q << 26 | t)
-    unsigned short ec[kBatchEdges];  // entry counts ko | ki << 8
+template <int EDGES>
+struct BatchWarpT {
+    int key[EDGES];  // edge ends (q << 26 | self << 25 | t << 1 | in), then entries (q << 26 | t)
+    unsigned short ec[EDGES];  // entry counts ko | ki << 8
     int r[32], s[32], rsr[32], rss[32], hasfb[32];
     long long dl[32];  // Delta L, fixed point 2^-48
     float pf[32], pb[32];
     float dlf[32], am[32];  // FP32 Delta L and its magnitude sum (precision form)
     double fb[32];
 };
+
+template <int MODE>
+using BatchWarp = BatchWarpT<MODE == 0 ? kBatchEdges0 : kBatchEdges>;
 
 
 __device__ __forceinline__ float fix48_to_float(long long v) {
@@ -525,12 +538,14 @@ __device__ __forceinline__ double fix48_to_double(long long v) {
 // memory).  Movers are processed in sub-batches of at most kBatchEdges
 // edge ends.
 template <int MODE, bool DL32>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_eval_batch(DecideArgs a, int bin,
-                                                                                     int warp_bytes) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, MODE == 0 ? SBP_BATCH0_MIN_BLOCKS : SBP_DECIDE_MIN_BLOCKS)
+    k_eval_batch(DecideArgs a, int bin, int warp_bytes) {
     extern __shared__ __align__(16) unsigned char bsm[];
+    constexpr int kEdges = MODE == 0 ? kBatchEdges0 : kBatchEdges;
+    using BW = BatchWarp<MODE>;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    BatchWarp &W = *reinterpret_cast<BatchWarp *>(bsm + (size_t)wid * warp_bytes);
-    unsigned *dcnt = reinterpret_cast<unsigned *>(bsm + (size_t)wid * warp_bytes + sizeof(BatchWarp));
+    BW &W = *reinterpret_cast<BW *>(bsm + (size_t)wid * warp_bytes);
+    unsigned *dcnt = reinterpret_cast<unsigned *>(bsm + (size_t)wid * warp_bytes + sizeof(BW));
     const GraphDev &g = a.g;
     const ModelDev &md = a.md;
     const int B = md.B;
@@ -571,7 +586,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
         // sub-batches of whole rows with at most kBatchEdges edge ends
         for (int sa = 0; sa < nv;) {
         const int fs = __shfl_sync(0xffffffffu, first, sa);
-        const unsigned fit = __ballot_sync(0xffffffffu, lane >= sa && lane < nv && incl - fs <= kBatchEdges);
+        const unsigned fit = __ballot_sync(0xffffffffu, lane >= sa && lane < nv && incl - fs <= kEdges);
         const int sb = 31 - __clz(fit);
         const int total = __shfl_sync(0xffffffffu, incl, sb) - fs;
         const bool act = lane >= sa && lane <= sb;
@@ -1197,17 +1212,17 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
     }
     // movers with k <= 32: batches of 32 per warp
     if (g->bin[2] > g->bin[1]) {
-        const int wb = (int)((sizeof(BatchWarp) + 15) / 16 * 16);
+        const int wb = (int)((sizeof(BatchWarp<0>) + 15) / 16 * 16);
         const size_t smem = (size_t)wb * kWarpsPerCta;
         SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<0, DL32>, smem));
-        k_eval_batch<0, DL32><<<sms * 3, kWarpsPerCta * 32, smem, st[0]>>>(a, 0, wb);
+        k_eval_batch<0, DL32><<<sms * SBP_BATCH0_MIN_BLOCKS, kWarpsPerCta * 32, smem, st[0]>>>(a, 0, wb);
         SBP_LAUNCHED();
     }
     // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
     // small, otherwise one warp each with a 256-slot table
     if (g->bin[3] > g->bin[2]) {
         if (B <= kDirectMaxB) {
-            const int wb = (int)((sizeof(BatchWarp) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
+            const int wb = (int)((sizeof(BatchWarp<1>) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
             const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
             const size_t smem = (size_t)wb * nwarps;
             SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32>, smem));
