@@ -150,3 +150,38 @@ def test_two_replicas_exchange_pending_labels_on_one_gpu():
         P.sbp_set_pending(reps[0].h, 0, 3, bad)
     for m in reps + [ref]:
         m.close()
+
+
+def _gather_main(rank, world, port, out_dir, ranges):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2305_18663_gb300.shard import allgather_slices
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        lo, hi = ranges[rank]
+        got = allgather_slices(torch.arange(lo, hi, dtype=torch.int32) * 3 + 1, ranges)
+        np.save(os.path.join(out_dir, f"g{rank}.npy"), got.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_three_gloo_ranks_gather_uneven_slices(tmp_path):
+    world = 3
+    ranges = [(0, 7), (7, 7), (7, 20)]  # the middle rank holds nothing
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_gather_main, args=(r, world, port, str(tmp_path), ranges)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    codes = [p.exitcode for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert codes == [0, 0, 0], codes
+    want = np.arange(0, 20, dtype=np.int32) * 3 + 1
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / f"g{r}.npy"), want)
