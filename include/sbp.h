@@ -343,10 +343,10 @@ int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const s
  * graphs (`sample` of them, evenly spaced in size order; all when sample <= 0
  * or >= count) under candidate options and returns the fastest in *best.
  * The search starts from *best when `start` is nonzero (else from the
- * defaults) and tunes one option at a time, in this order: movers_per_warp
- * {1, 2, 4}, ctas_per_sm {1, 2, 3, 4}, max_B {128, 256, 512, 1024}, max_n
- * {1024, 4096, 16384, 65536}, dense_max_B {1024, 4096}; workers and
- * mem_fraction are kept.  *graphs_per_s (may be NULL) receives the best
+ * defaults) and tunes one option at a time, in this order: workers {8, 16,
+ * 32}, movers_per_warp {1, 2, 4}, ctas_per_sm {1, 2, 3, 4}, max_B {128, 256,
+ * 512, 1024}, max_n {1024, 4096, 16384, 65536}, dense_max_B {1024, 4096};
+ * mem_fraction is kept.  *graphs_per_s (may be NULL) receives the best
  * rate on the sample, *trials (may be NULL) the number of timed runs.
  * Every run must give the same B and DL for every graph; SBP_ESTATE
  * otherwise.  p: NULL for the defaults. */

@@ -526,6 +526,7 @@ extern "C" int sbp_autotune_batch(const sbp_graph_t *const *graphs, int32_t coun
         std::vector<int32_t> values;
     };
     const Knob knobs[] = {
+        {&sbp_batch_options::workers, {8, 16, 32}},
         {&sbp_batch_options::movers_per_warp, {1, 2, 4}},
         {&sbp_batch_options::ctas_per_sm, {1, 2, 3, 4}},
         {&sbp_batch_options::max_B, {128, 256, 512, 1024}},
