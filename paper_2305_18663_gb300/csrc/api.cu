@@ -274,7 +274,7 @@ extern "C" void sbp_free_model(sbp_model_t *m) {
     void *ps[] = {m->b,        m->bnew,   m->M,        m->P,       m->Pc,     m->dout,  m->din,
                   m->rcp,      m->rcp32,  m->dsum,     m->dl,      m->partials, m->counters, m->status,
                   m->best_s,   m->best_d, m->map,      m->vcount,  m->movers, m->mcount, m->skip,
-                  m->items,    m->nbo,    m->nbi};
+                  m->items,    m->nbo,    m->nbi,      m->cta_tab};
     for (void *p : ps) model_free(p, st);
     for (int i = 0; i < 2; ++i) {
         if (m->side[i]) cudaStreamDestroy(m->side[i]);

@@ -224,6 +224,8 @@ struct sbp_model {
     cudaStream_t side[2] = {nullptr, nullptr};
     cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
     uint8_t *skip = nullptr;  // the hybrid pass's sequential vertices (n flags)
+    unsigned long long *cta_tab = nullptr;  // global neighbour tables of the CTA kernel
+    size_t cta_tab_bytes = 0;
     int32_t skip_h = -1;      // the h skip was built for
     // pinned host mirror for small read-backs
     void *pinned = nullptr;

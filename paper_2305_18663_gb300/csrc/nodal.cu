@@ -274,10 +274,13 @@ struct CtaScratch {
     int nlist, self, ok, dec;
 };
 
+// gtab: NULL, or a global scratch of 2 cap words per CTA for tables that do
+// not fit shared memory
 template <bool DL32>
-__global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin, int cap, int cap_log2) {
+__global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin, int cap, int cap_log2,
+                                                          unsigned long long *gtab) {
     extern __shared__ unsigned long long smem_u64[];
-    unsigned long long *cnt = smem_u64;
+    unsigned long long *cnt = gtab ? gtab + (size_t)blockIdx.x * 2 * (size_t)cap : smem_u64;
     int *keys = reinterpret_cast<int *>(cnt + cap);
     int *list = keys + cap;
     __shared__ CtaScratch sh;
@@ -1141,6 +1144,33 @@ ModelDev model_dev(sbp_model *m) {
 
 namespace {
 
+// The CTA kernel's neighbour table (cap slots of 16 bytes): in shared memory
+// while it fits, else a slice per CTA of a global scratch the model keeps
+// (at most 1 GB, fewer CTAs for very large tables).
+int cta_table(sbp_model *m, int cap, int sms, int *grid, size_t *smem, unsigned long long **gtab) {
+    const size_t bytes = (size_t)cap * 16;
+    *grid = sms * 4;
+    *gtab = nullptr;
+    *smem = bytes;
+    if (bytes <= 160 * 1024) return SBP_OK;
+    *smem = 0;
+    const size_t per_grid = std::max<size_t>(1, (size_t(1) << 30) / bytes);
+    if ((size_t)*grid > per_grid) *grid = (int)per_grid;
+    const size_t need = bytes * (size_t)*grid;
+    if (m->cta_tab_bytes < need) {
+        model_free(m->cta_tab, m->stream);
+        m->cta_tab = nullptr;
+        m->cta_tab_bytes = 0;
+        if (model_alloc((void **)&m->cta_tab, need, m->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SBP_ENOMEM, "nodal pass: no device memory for the neighbour tables");
+        }
+        m->cta_tab_bytes = need;
+    }
+    *gtab = m->cta_tab;
+    return SBP_OK;
+}
+
 // graphs with at least this many edges run the three degree groups'
 // kernels on three streams
 constexpr int64_t kSideStreamEdges = int64_t(1) << 22;
@@ -1203,10 +1233,12 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
             k_eval_warp<DL32><<<sms * 4, nwarps * 32, smem, st[2]>>>(a, 2, cap, cap_log2, 1);
             SBP_LAUNCHED();
         } else {
-            const size_t smem = (size_t)cap * (8 + 4 + 4);
-            if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
+            int grid;
+            size_t smem;
+            unsigned long long *gtab;
+            SBP_TRY(cta_table(m, cap, sms, &grid, &smem, &gtab));
             SBP_TRY(ensure_dyn_smem((const void *)k_eval_cta<DL32>, smem));
-            k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, st[2]>>>(a, 2, cap, cap_log2);
+            k_eval_cta<DL32><<<grid, kBigThreads, smem, st[2]>>>(a, 2, cap, cap_log2, gtab);
             SBP_LAUNCHED();
         }
     }
@@ -1251,10 +1283,12 @@ int launch_recheck(sbp_model *m, const DecideArgs &a0, int sms) {
     int cap_log2 = 6;
     while ((int64_t(1) << cap_log2) < need) ++cap_log2;
     const int cap = 1 << cap_log2;
-    const size_t smem = (size_t)cap * (8 + 4 + 4);
-    if (smem > 160 * 1024) return fail(SBP_ESTATE, "nodal pass: neighbour table does not fit shared memory");
+    int grid;
+    size_t smem;
+    unsigned long long *gtab;
+    SBP_TRY(cta_table(m, cap, sms, &grid, &smem, &gtab));
     SBP_TRY(ensure_dyn_smem((const void *)k_eval_cta<DL32>, smem));
-    k_eval_cta<DL32><<<sms * 4, kBigThreads, smem, m->stream>>>(a, 3, cap, cap_log2);
+    k_eval_cta<DL32><<<grid, kBigThreads, smem, m->stream>>>(a, 3, cap, cap_log2, gtab);
     SBP_LAUNCHED();
     return SBP_OK;
 }

@@ -225,6 +225,21 @@ def test_nodal_sweeps_large_B_hubs_cta_path():
     run_sweeps(g, 3000, random_labels(n, 3000, seed=2), sweeps=3)
 
 
+def test_nodal_sweeps_hub_table_beyond_shared_memory():
+    # B = 9500 and a hub with 18,000 edges: its neighbour table needs 16,384
+    # slots (256 KB), more than shared memory holds, so the CTA kernel keeps
+    # it in global memory
+    rng = np.random.default_rng(23)
+    n = 30000
+    src = rng.integers(0, n, 60000)
+    dst = rng.integers(0, n, 60000)
+    hub = 11
+    src = np.concatenate([src, np.full(9000, hub), rng.integers(0, n, 9000)])
+    dst = np.concatenate([dst, rng.integers(0, n, 9000), np.full(9000, hub)])
+    g = _G(n, src, dst)
+    run_sweeps(g, 9500, random_labels(n, 9500, seed=4), sweeps=2)
+
+
 def test_nodal_sweeps_degree_above_65535():
     # a hub with 70,000 edges: 16-bit packed counts no longer fit
     rng = np.random.default_rng(22)
