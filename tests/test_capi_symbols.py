@@ -53,3 +53,28 @@ def test_vertex_dealing_covers_each_vertex_once():
         # each rank gets both high- and low-degree vertices
         loads = [deg[p].sum() for p in parts]
         assert max(loads) - min(loads) <= deg.max() * 2
+
+
+def declared_arity():
+    """Parameter count of every function include/sbp.h declares."""
+    with open(os.path.join(ROOT, "include", "sbp.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(?:int|void|size_t)\s+\**(sbp_\w+)\s*\(([^)]*)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    # every ctypes prototype takes as many arguments as the C declaration
+    import paper_2305_18663_gb300 as P
+
+    lib = P.load()
+    arity = declared_arity()
+    assert arity, "no declarations parsed"
+    for name, n in arity.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
