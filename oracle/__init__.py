@@ -88,7 +88,10 @@ def lib():
         "og_bracket_free": (None, [vp]),
         "og_bracket_insert": (None, [vp, i64, f64]),
         "og_bracket_next": (ci, [vp, f64, i64p, f64p, C.POINTER(ci), C.POINTER(i64)]),
-        "og_partition": (ci, [vp, C.POINTER(_Params), i32p, C.POINTER(i64), C.POINTER(f64), C.POINTER(i64), ci]),
+        "og_partition": (ci, [vp, C.POINTER(_Params), i32p, C.POINTER(i64), C.POINTER(f64), C.POINTER(i64), ci, vp, i64,
+                              C.POINTER(i64)]),
+        "og_mcmc_phase": (i64, [vp, C.POINTER(_Params), u64, f64, ci, f64p]),
+        "og_merge_phase": (i64, [vp, C.POINTER(_Params), u64, i64, ci, C.POINTER(i64)]),
         "og_max_threads": (ci, []),
     }
     for name, (res, args) in sig.items():
@@ -246,6 +249,21 @@ class Model:
                                      _ptr(lnu), nthreads)
         return Decisions(b_new, s, flags, dH, logA, lnu, int(acc))
 
+    def mcmc_phase(self, p: "Params", sweep_id: int, t: float, nthreads: int = 1):
+        """One MCMC phase (Alg. 2) from the current state, sweep ids from
+        sweep_id on; the model ends in the phase's final state.  Returns
+        (sweeps run, DL after 0..sweeps sweeps)."""
+        hist = np.zeros(p.max_sweeps + 1, np.float64)
+        ns = lib().og_mcmc_phase(self._h, C.byref(_cparams(p)), sweep_id, t, nthreads, hist)
+        return int(ns), hist[: ns + 1]
+
+    def merge_phase(self, p: "Params", round_id: int, n_merges: int, nthreads: int = 1):
+        """One merge phase (Alg. 1) from the current state, round ids from
+        round_id on.  Returns (B after, proposal rounds taken)."""
+        rounds = C.c_int64()
+        Bn = lib().og_merge_phase(self._h, C.byref(_cparams(p)), round_id, n_merges, nthreads, C.byref(rounds))
+        return int(Bn), int(rounds.value)
+
     def merge_delta(self, r: int, s: int) -> float:
         return lib().og_merge_delta(self._h, r, s)
 
@@ -308,11 +326,24 @@ class Params:
     dense_max_B: int = 4096
 
 
-def partition(g: Graph, p: Params = Params(), nthreads: int = 1):
-    cp = _Params(p.seed, p.beta, p.merge_proposals, p.reduction, p.t_pre, p.t_post, p.max_sweeps, p.hybrid_h,
-                 p.dense_max_B)
+def _cparams(p: Params) -> _Params:
+    return _Params(p.seed, p.beta, p.merge_proposals, p.reduction, p.t_pre, p.t_post, p.max_sweeps, p.hybrid_h,
+                   p.dense_max_B)
+
+
+def partition(g: Graph, p: Params = Params(), nthreads: int = 1, phase_log: bool = False):
+    """Full run.  Returns (b, B, DL, sweeps), plus with phase_log a
+    (phases, 7) array: start B, target B, B after the merges, MCMC
+    threshold t, sweeps, compacted B and its DL."""
+    cp = _cparams(p)
     b = np.zeros(g.n, np.int32)
-    B, d, ns = C.c_int64(), C.c_double(), C.c_int64()
-    if lib().og_partition(g._h, C.byref(cp), b, C.byref(B), C.byref(d), C.byref(ns), nthreads) != 0:
+    B, d, ns, nl = C.c_int64(), C.c_double(), C.c_int64(), C.c_int64()
+    cap = 4096 if phase_log else 0
+    log = np.zeros((max(cap, 1), 7), np.float64)
+    if lib().og_partition(g._h, C.byref(cp), b, C.byref(B), C.byref(d), C.byref(ns), nthreads,
+                          _ptr(log) if phase_log else None, cap, C.byref(nl)) != 0:
         raise RuntimeError("partition failed")
-    return b, int(B.value), float(d.value), int(ns.value)
+    out = (b, int(B.value), float(d.value), int(ns.value))
+    if phase_log:
+        return out + (log[: min(int(nl.value), cap)].copy(),)
+    return out

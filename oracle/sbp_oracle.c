@@ -790,15 +790,19 @@ typedef struct {
 
 /* Merge phase: from state b with B blocks, reach B - n_merges blocks.  When
  * a round of proposals runs out before n_merges links, the merged model is
- * rebuilt and a new round (new round_id) proposes again. */
-static int64_t merge_phase(og_model *md, const og_params *p, uint64_t *round_id, int64_t n_merges, int nthreads) {
+ * rebuilt and a new round (new round_id) proposes again.  *rounds (may be
+ * NULL) receives the number of proposal rounds taken. */
+static int64_t merge_phase(og_model *md, const og_params *p, uint64_t *round_id, int64_t n_merges, int nthreads,
+                           int64_t *rounds) {
     const og_graph *g = md->g;
+    int64_t nr = 0;
     while (n_merges > 0) {
         int64_t B = md->B;
         int32_t *bs = (int32_t *)malloc(sizeof(int32_t) * (size_t)B);
         double *bd = (double *)malloc(sizeof(double) * (size_t)B);
         int32_t *map = (int32_t *)malloc(sizeof(int32_t) * (size_t)B);
         og_merge_proposals(md, p->seed, (*round_id)++, p->merge_proposals, bs, bd, nthreads);
+        nr++;
         int64_t Bn;
         int64_t done = og_merge_apply(B, bs, bd, n_merges, map, &Bn);
         int32_t *nb = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
@@ -808,13 +812,15 @@ static int64_t merge_phase(og_model *md, const og_params *p, uint64_t *round_id,
         n_merges -= done;
         if (done == 0) break;
     }
+    if (rounds) *rounds = nr;
     return md->B;
 }
 
 /* MCMC phase (Alg. 2 with the asynchronous-Gibbs pass, or the hybrid pass
  * while B <= dense_max_B when hybrid_h > 0): sweeps until
- * |DL_{k-3} - DL_k| < t DL_k (k >= 3) or max_sweeps. */
-static int64_t mcmc_phase(og_model *md, const og_params *p, uint64_t *sweep_id, double t, int nthreads) {
+ * |DL_{k-3} - DL_k| < t DL_k (k >= 3) or max_sweeps.  hist (may be NULL,
+ * else max_sweeps + 1 entries) receives DL_0 (the start) .. DL_k. */
+static int64_t mcmc_phase(og_model *md, const og_params *p, uint64_t *sweep_id, double t, int nthreads, double *hist_out) {
     const og_graph *g = md->g;
     double *hist = (double *)malloc(sizeof(double) * (size_t)(p->max_sweeps + 1));
     int32_t *bn = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n > 0 ? g->n : 1));
@@ -830,14 +836,31 @@ static int64_t mcmc_phase(og_model *md, const og_params *p, uint64_t *sweep_id, 
         hist[k] = og_model_dl(md);
         if (k >= 3 && fabs(hist[k - 3] - hist[k]) < t * hist[k]) break;
     }
+    int64_t done = k > p->max_sweeps ? p->max_sweeps : k;
+    if (hist_out) memcpy(hist_out, hist, sizeof(double) * (size_t)(done + 1));
     free(bn);
     free(hist);
-    return k > p->max_sweeps ? p->max_sweeps : k;
+    return done;
+}
+
+/* The two phases on their own, for the tests of their stopping rules. */
+int64_t og_mcmc_phase(og_model *md, const og_params *p, uint64_t sweep_id, double t, int nthreads, double *hist) {
+    return mcmc_phase(md, p, &sweep_id, t, nthreads, hist);
+}
+
+int64_t og_merge_phase(og_model *md, const og_params *p, uint64_t round_id, int64_t n_merges, int nthreads,
+                       int64_t *rounds) {
+    return merge_phase(md, p, &round_id, n_merges, nthreads, rounds);
 }
 
 /* Full run (Fig. 1, Section II-B): start from one block per vertex,
- * alternate merge and MCMC phases under the golden-ratio search. */
-int og_partition(const og_graph *g, const og_params *p, int32_t *b_out, int64_t *B_out, double *dl_out, int64_t *n_sweeps_out, int nthreads) {
+ * alternate merge and MCMC phases under the golden-ratio search.  log (may
+ * be NULL, else log_cap rows of 7 doubles) receives one row per phase:
+ * start B, target B, B after the merges, MCMC threshold t, sweeps, and the
+ * compacted B and its DL inserted into the bracket; *n_log the number of
+ * phases. */
+int og_partition(const og_graph *g, const og_params *p, int32_t *b_out, int64_t *B_out, double *dl_out, int64_t *n_sweeps_out,
+                 int nthreads, double *log, int64_t log_cap, int64_t *n_log) {
     const int64_t n = g->n;
     int32_t *b = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     for (int64_t v = 0; v < n; ++v) b[v] = (int32_t)v;
@@ -847,18 +870,30 @@ int og_partition(const og_graph *g, const og_params *p, int32_t *b_out, int64_t 
     memset(&k, 0, sizeof(k));
     bracket_insert(&k, n, og_model_dl(md), b, n);
     uint64_t sweep_id = 0, round_id = 0;
-    int64_t total_sweeps = 0;
+    int64_t total_sweeps = 0, phases = 0;
     int start;
     int64_t target;
     while (bracket_next(&k, p->reduction, &start, &target)) {
-        og_model_set_b(md, k.B[start], k.b[start]);
-        merge_phase(md, p, &round_id, k.B[start] - target, nthreads);
-        total_sweeps += mcmc_phase(md, p, &sweep_id, k.B[2] == 0 ? p->t_pre : p->t_post, nthreads);
+        int64_t B0 = k.B[start];
+        double t = k.B[2] == 0 ? p->t_pre : p->t_post;
+        og_model_set_b(md, B0, k.b[start]);
+        merge_phase(md, p, &round_id, B0 - target, nthreads, NULL);
+        int64_t Bm = md->B;
+        int64_t ns = mcmc_phase(md, p, &sweep_id, t, nthreads, NULL);
+        total_sweeps += ns;
         memcpy(b, md->b, sizeof(int32_t) * (size_t)n);
         int64_t Bc = og_compact(n, md->B, b);
         og_model_set_b(md, Bc, b);
-        bracket_insert(&k, Bc, og_model_dl(md), b, n);
+        double dlc = og_model_dl(md);
+        bracket_insert(&k, Bc, dlc, b, n);
+        if (log && phases < log_cap) {
+            double *row = log + 7 * phases;
+            row[0] = (double)B0; row[1] = (double)target; row[2] = (double)Bm;
+            row[3] = t; row[4] = (double)ns; row[5] = (double)Bc; row[6] = dlc;
+        }
+        phases++;
     }
+    if (n_log) *n_log = phases;
     memcpy(b_out, k.b[1], sizeof(int32_t) * (size_t)n);
     *B_out = k.B[1];
     *dl_out = k.dl[1];
