@@ -462,6 +462,23 @@ def test_merge_blocks_matches_oracle_application(dmax):
     check_blockmodel(pm, O.Model(G, Bn, mp[b]))
 
 
+@pytest.mark.parametrize("dmax", [4096, 2])
+def test_merge_blocks_second_round_matches_oracle(dmax):
+    # 6 blocks in 3 pairs with no edge between pairs: round 0 can make only
+    # 3 links, so 4 merges need a second proposal round on the merged model
+    from test_oracle_driver_pins import _paired_blocks_graph
+
+    n, src, dst, b = _paired_blocks_graph()
+    om = O.Model(O.Graph(n, src, dst), 6, b)
+    oB, orounds = om.merge_phase(O.Params(seed=5), 20, 4)
+    assert (oB, orounds) == (2, 2)
+    pm = P.Model(P.Graph(n, src, dst), 6, b, P.Params.default(seed=5, dense_max_B=dmax))
+    Bg, rounds = P.sbp_merge_blocks(pm.h, 20, 4)
+    assert (Bg, rounds) == (oB, orounds)
+    assert np.array_equal(pm.assignment(), om.assignment())
+    check_blockmodel(pm, om)
+
+
 def test_compact_drops_empty_blocks():
     g = make_config("plain_1k")
     b = (random_labels(g.n, 10, seed=1) * 3).astype(np.int32)  # labels 0,3,...,27 of 30
@@ -564,3 +581,73 @@ def test_full_size_sweep_in_benchmark_configuration(full_size, m_form):
     om.set_b(B, bg)
     check_blockmodel(pm, om)
     pm.close()
+
+
+# ---------------------------------------------------------------------------
+# the timed kernels themselves against the oracle: no per-vertex trace (a
+# trace sends every mover to the exact evaluation), FP32 terms with the
+# exact recheck, sweeps 0..4 from the perturbed start (the heavy-move sweeps
+# first), b bit for bit after every commit, then M, degrees and DL
+
+def untraced_sweeps_vs_oracle(g, B, b0, pg, G, m_form, sweeps, seed=0, min_moves=0):
+    dmax = 1 if m_form == "sparse" else 4096
+    params = P.Params.default(seed=seed, dense_max_B=dmax, dl_fp32=1)
+    pm = P.Model(pg, B, b0, params, torch.cuda.current_stream())
+    om = O.Model(G, B, b0)
+    total_margin = 0
+    moves = []
+    for sw in range(sweeps):
+        bcur = om.assignment()
+        P.sbp_nodal_decide(pm.h, sw, 0, g.n)  # the launch sequence bench.py times
+        st = P.sbp_commit(pm.h)
+        od = om.nodal_decide(seed, sw, 3.0, nthreads=NT)
+        # margin cases, by the oracle's own draw and log acceptance ratio
+        mv = (od.s != bcur) & ((od.flags & 1) != 0)
+        margin = mv & (np.abs(od.lnu - od.logA) <= TOL * np.maximum(np.abs(od.logA), 1.0))
+        bg = pm.assignment()
+        want = od.b_new.copy()
+        want[margin] = bg[margin]
+        bad = np.flatnonzero(bg != want)
+        assert bad.size == 0, f"sweep {sw}: {bad.size} labels differ from the oracle, first {bad[:5]}"
+        assert st.n_moves == int(mv.sum()), "movers differ"
+        acc_g = int((bg != bcur).sum())
+        assert acc_g == st.n_accepted
+        assert abs(st.n_accepted - od.accepted) <= int(margin.sum())
+        om.set_b(B, bg)
+        check_blockmodel(pm, om)
+        total_margin += int(margin.sum())
+        moves.append(int(mv.sum()))
+    pm.close()
+    assert max(moves) >= min_moves
+    return total_margin, moves
+
+
+@pytest.mark.parametrize("m_form", ["sparse", "dense"])
+def test_untraced_fp32_sweeps_full_size_match_oracle(full_size, m_form):
+    # 1M vertices, 20M edges, B = 316: E >= 2^22, so the decision pass forks
+    # its degree groups onto three streams, as in the timed run
+    g, b0, pg, G = full_size
+    margin, moves = untraced_sweeps_vs_oracle(g, 316, b0, pg, G, m_form, sweeps=5, min_moves=400_000)
+    assert margin <= 10
+
+
+@pytest.mark.parametrize("m_form", ["sparse", "dense"])
+def test_untraced_fp32_sweeps_just_above_fork_size_match_oracle(m_form):
+    # 220k vertices, about 4.4M edges: just above the 2^22-edge size at which
+    # the degree groups run on three streams
+    g = make_config("dcsbm_1m", seed=0, scale=0.22)
+    assert g.m >= 1 << 22
+    b0 = perturb(g.planted, 316, 0.3, seed=0)
+    margin, _ = untraced_sweeps_vs_oracle(g, 316, b0, P.Graph(g.n, g.src, g.dst), O.Graph(g.n, g.src, g.dst),
+                                          m_form, sweeps=4, min_moves=50_000)
+    assert margin <= 5
+
+
+@pytest.mark.parametrize("m_form", ["sparse", "dense"])
+def test_untraced_fp32_sweeps_below_fork_size_match_oracle(m_form):
+    # 50k vertices, 1M edges: one stream, every degree group and ragged tails
+    g = make_config("dcsbm_1m", seed=0, scale=0.05)
+    assert g.m < 1 << 22
+    b0 = perturb(g.planted, 316, 0.3, seed=0)
+    untraced_sweeps_vs_oracle(g, 316, b0, P.Graph(g.n, g.src, g.dst), O.Graph(g.n, g.src, g.dst), m_form,
+                              sweeps=5, min_moves=10_000)
