@@ -97,7 +97,10 @@ typedef struct sbp_params {
  * n_move_edges: sum of the degrees of the vertices with s != current block
  * (the rows the pass had to aggregate); dl_before / dl_after: DL (Eq. 2)
  * before and after the rebuild; n_recheck: moves decided by the exact
- * (FP64) evaluation because the fast one could not settle them. */
+ * (FP64) evaluation because the fast one could not settle them; n_entries:
+ * the distinct neighbour blocks of those vertices, summed (each is one
+ * entry of the sparse vector of changes, Section III-A (c), and costs four
+ * blockmodel lookups and two degree lookups). */
 typedef struct sbp_sweep_stats {
     int64_t n_proposed;
     int64_t n_moves;
@@ -107,6 +110,7 @@ typedef struct sbp_sweep_stats {
     double dl_before;
     double dl_after;
     int64_t n_recheck;
+    int64_t n_entries;
 } sbp_sweep_stats;
 
 /* Optional per-vertex outputs of a nodal decision pass: each member is NULL
@@ -256,7 +260,10 @@ void sbp_free_model(sbp_model_t *m);
  * SBP_EINVAL.  Every call shares that array: calls whose GPU work overlaps
  * (on different streams) race and must be ordered by the caller.  The first
  * call on each device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Results agree
+ * current; make that first call before any stream capture.  That address is
+ * kept for the rest of the process: it does not survive cudaDeviceReset, so
+ * after a reset of a device this entry point must not be called on it.
+ * Results agree
  * with sbp_get_dl to about 1e-13 relative (x ln x from FP64 log here). */
 int sbp_dense_dl_noalloc(const int32_t *M, int32_t B, const int32_t *dout, const int32_t *din, int64_t E, int64_t N,
                          double *dl_out, void *stream);

@@ -77,6 +77,7 @@ class SweepStats(C.Structure):
         ("dl_before", C.c_double),
         ("dl_after", C.c_double),
         ("n_recheck", C.c_int64),
+        ("n_entries", C.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -147,6 +147,7 @@ int read_stats(sbp_model *m, sbp_sweep_stats *out) {
     out->n_margin = (int64_t)h->c.margin;
     out->n_move_edges = (int64_t)h->c.move_edges;
     out->n_recheck = (int64_t)h->c.recheck;
+    out->n_entries = (int64_t)h->c.entries;
     out->dl_after = h->dl[0];
     out->dl_before = h->dl[1];
     return SBP_OK;

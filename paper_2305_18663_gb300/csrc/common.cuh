@@ -116,6 +116,7 @@ namespace sbp {
 struct DevCounters {
     unsigned long long proposed, moves, accepted, margin, move_edges, acc_edges, recheck;
     unsigned long long items;  // entries appended to the accepted-move list
+    unsigned long long entries;  // distinct neighbour blocks of the evaluated movers (sum of D_v)
 };
 
 // the accepted-move list: one (vertex, chunk) item per kMoveChunk edges of

@@ -123,7 +123,7 @@ int Engine::init(const sbp_params &p, const BatchOptions &o, bool background) {
     budget = (size_t)((double)free_b * opt.mem_fraction);
     int dev = 0, sms = 1;
     SBP_CUDA(cudaGetDevice(&dev));
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    SBP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     full_batch = (size_t)sms * (size_t)std::max(1, opt.tune.ctas_per_sm);
     for (int w = 0; w < W; ++w)
         workers.emplace_back([this, dev]() {

@@ -22,6 +22,11 @@
 #ifndef SBP_DIRECT_MIN_BLOCKS
 #define SBP_DIRECT_MIN_BLOCKS 4
 #endif
+// 1: full-range passes draw the proposals inside the evaluation kernels;
+// 0: always k_propose first (for comparison builds)
+#ifndef SBP_FUSED_PROPOSALS
+#define SBP_FUSED_PROPOSALS 1
+#endif
 
 namespace sbp {
 namespace {
@@ -161,6 +166,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
             }
             if (!ok) record_status(md.status, SBP_EHASHFULL);
             const int D = *nlist;
+            if (lane == 0) c.entries += (unsigned)D;
             VertexCtx x;
             x.v = v; x.r = r; x.s = s;
             x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
@@ -193,72 +199,122 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DECIDE_MIN_BLOCKS) k_ev
 // match; eight 32-edge chunks in flight per round.  Degrees below 65536.
 constexpr int kDirectChunks = 8;
 
+// one mover (v, s, w2) on the whole warp, counts in cnt[B] (all zero on entry
+// and on return), first touches in list
 template <bool DL32>
+__device__ __forceinline__ void direct_mover(const DecideArgs &a, unsigned *cnt, int *list, int v, int s, uint64_t w2,
+                                             Counts &c) {
+    const int lane = threadIdx.x & 31;
+    const ModelDev &md = a.md;
+    const GraphDev &g = a.g;
+    const int r = md.b[v];
+    const int o0 = g.op[v], kout = g.op[v + 1] - o0;
+    const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
+    const int k = kout + kin;
+    int nl = 0, self = 0;
+    for (int base = 0; base < k; base += 32 * kDirectChunks) {
+        int nb[kDirectChunks], tb[kDirectChunks];
+#pragma unroll
+        for (int c8 = 0; c8 < kDirectChunks; ++c8) {
+            const int idx = base + c8 * 32 + lane;
+            nb[c8] = idx < k ? nb_raw(g, md, o0, i0, kout, idx) : 0;
+        }
+        bool sf[kDirectChunks];
+#pragma unroll
+        for (int c8 = 0; c8 < kDirectChunks; ++c8) {
+            const int idx = base + c8 * 32 + lane;
+            sf[c8] = false;
+            tb[c8] = idx < k ? nb_block(md, nb[c8], v, sf[c8]) : -1;
+        }
+#pragma unroll
+        for (int c8 = 0; c8 < kDirectChunks; ++c8) {
+            const int idx = base + c8 * 32 + lane;
+            const bool is_out = idx < kout, is_self = idx < k && sf[c8];
+            self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
+            bool fresh = false;
+            if (tb[c8] >= 0 && !is_self) fresh = atomicAdd(&cnt[tb[c8]], is_out ? 1u : 0x10000u) == 0u;
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            if (fresh) list[nl + __popc(fm & ((1u << lane) - 1u))] = tb[c8];
+            nl += __popc(fm);
+        }
+    }
+    __syncwarp();
+    VertexCtx x;
+    x.v = v; x.r = r; x.s = s;
+    x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
+    const int D = nl;
+    if (lane == 0) c.entries += (unsigned)D;
+    evaluate_warp<DL32>(a, md, x, w2, [&](auto &&f) {
+        for (int e = lane; e < D; e += 32) {
+            const int t = list[e];
+            const unsigned cc = cnt[t];
+            f(t, (int)(cc & 0xffffu), (int)(cc >> 16));
+        }
+    }, c);
+    __syncwarp();
+    for (int e = lane; e < D; e += 32) cnt[list[e]] = 0u;
+    __syncwarp();
+}
+
+// One warp per mover with direct-mapped counts.  FUSED = false: the movers
+// of list `bin`.  FUSED = true: the warps draw the proposals of the group's
+// vertices themselves, warp w taking the vertices w, w + W, w + 2W, ... of
+// the group (W warps in the grid; the group is sorted by descending degree,
+// so every warp gets a share of the largest rows), one per lane, then
+// evaluates its movers one after another.
+template <bool DL32, bool FUSED>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, SBP_DIRECT_MIN_BLOCKS) k_eval_warp_direct(DecideArgs a, int bin,
                                                                                            int warp_words) {
     extern __shared__ unsigned dmw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const ModelDev &md = a.md;
-    const GraphDev &g = a.g;
     const int B = md.B;
     unsigned *cnt = dmw + (size_t)wid * warp_words;
     int *list = reinterpret_cast<int *>(cnt + B);
     for (int i = lane; i < B; i += 32) cnt[i] = 0u;
     __syncwarp();
-    const Mover *mlist = a.movers + a.mbase[bin];
-    const int64_t count = *(volatile unsigned *)&a.mcount[bin];
     Counts c;
-    for (int64_t q = (int64_t)blockIdx.x * nwarps + wid; q < count; q += (int64_t)gridDim.x * nwarps) {
-        const Mover mv = mlist[q];
-        const int v = mv.v, s = mv.s;
-        const int r = md.b[v];
-        const int o0 = g.op[v], kout = g.op[v + 1] - o0;
-        const int i0 = g.ip[v], kin = g.ip[v + 1] - i0;
-        const int k = kout + kin;
-        int nl = 0, self = 0;
-        for (int base = 0; base < k; base += 32 * kDirectChunks) {
-            int nb[kDirectChunks], tb[kDirectChunks];
-#pragma unroll
-            for (int c8 = 0; c8 < kDirectChunks; ++c8) {
-                const int idx = base + c8 * 32 + lane;
-                nb[c8] = idx < k ? nb_raw(g, md, o0, i0, kout, idx) : 0;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + wid, nw = (int64_t)gridDim.x * nwarps;
+    if constexpr (!FUSED) {
+        const Mover *mlist = a.movers + a.mbase[bin];
+        const int64_t count = *(volatile unsigned *)&a.mcount[bin];
+        for (int64_t q = gw; q < count; q += nw) {
+            const Mover mv = mlist[q];
+            direct_mover<DL32>(a, cnt, list, mv.v, mv.s, mv.w2, c);
+        }
+        if (lane == 0) flush_counts(md, c);
+    } else {
+        const int32_t *vl = a.vlist[bin];
+        const int64_t vcount = a.vcount[bin];
+        unsigned long long medges = 0;
+        for (int64_t j0 = 0; gw + j0 * nw < vcount; j0 += 32) {
+            const int64_t i = gw + (j0 + lane) * nw;
+            bool mover = false;
+            int pv = 0, ps = 0;
+            uint64_t pw = 0;
+            if (i < vcount) {
+                pv = vl[i];
+                const Proposal p = propose_vertex(a.g, md, a.seed, a.sweep_id, pv);
+                if (p.s == p.r) {
+                    c.proposed++;
+                } else {
+                    mover = true;
+                    ps = p.s;
+                    pw = p.w2;
+                    medges += (unsigned long long)p.k;
+                }
             }
-            bool sf[kDirectChunks];
-#pragma unroll
-            for (int c8 = 0; c8 < kDirectChunks; ++c8) {
-                const int idx = base + c8 * 32 + lane;
-                sf[c8] = false;
-                tb[c8] = idx < k ? nb_block(md, nb[c8], v, sf[c8]) : -1;
-            }
-#pragma unroll
-            for (int c8 = 0; c8 < kDirectChunks; ++c8) {
-                const int idx = base + c8 * 32 + lane;
-                const bool is_out = idx < kout, is_self = idx < k && sf[c8];
-                self += __popc(__ballot_sync(0xffffffffu, is_self && is_out));
-                bool fresh = false;
-                if (tb[c8] >= 0 && !is_self) fresh = atomicAdd(&cnt[tb[c8]], is_out ? 1u : 0x10000u) == 0u;
-                const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-                if (fresh) list[nl + __popc(fm & ((1u << lane) - 1u))] = tb[c8];
-                nl += __popc(fm);
+            unsigned mask = __ballot_sync(0xffffffffu, mover);
+            while (mask) {
+                const int q = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int v = __shfl_sync(0xffffffffu, pv, q), s = __shfl_sync(0xffffffffu, ps, q);
+                const uint64_t w2 = __shfl_sync(0xffffffffu, pw, q);
+                direct_mover<DL32>(a, cnt, list, v, s, w2, c);
             }
         }
-        __syncwarp();
-        VertexCtx x;
-        x.v = v; x.r = r; x.s = s;
-        x.Kout = kout; x.Kin = kin; x.self = self; x.k = k;
-        const int D = nl;
-        evaluate_warp<DL32>(a, md, x, mv.w2, [&](auto &&f) {
-            for (int e = lane; e < D; e += 32) {
-                const int t = list[e];
-                const unsigned cc = cnt[t];
-                f(t, (int)(cc & 0xffffu), (int)(cc >> 16));
-            }
-        }, c);
-        __syncwarp();
-        for (int e = lane; e < D; e += 32) cnt[list[e]] = 0u;
-        __syncwarp();
+        flush_counts_warp(md, c, medges);
     }
-    if (lane == 0) flush_counts(md, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,6 +336,9 @@ template <bool DL32>
 __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin, int cap, int cap_log2,
                                                           unsigned long long *gtab) {
     extern __shared__ unsigned long long smem_u64[];
+    // CTAs beyond the list's length have nothing to do (the recheck launch
+    // is usually nearly empty)
+    if ((int64_t)blockIdx.x >= (int64_t)(*(volatile unsigned *)&a.mcount[bin])) return;
     unsigned long long *cnt = gtab ? gtab + (size_t)blockIdx.x * 2 * (size_t)cap : smem_u64;
     int *keys = reinterpret_cast<int *>(cnt + cap);
     int *list = keys + cap;
@@ -330,6 +389,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         __syncthreads();
         const int D = sh.nlist;
         if (tid == 0 && !sh.ok) record_status(md.status, SBP_EHASHFULL);
+        if (tid == 0 && !a.force_exact) c.entries += (unsigned)D;
         VertexCtx x;
         x.v = v; x.r = r; x.s = s;
         x.Kout = kout; x.Kin = kin; x.self = sh.self; x.k = k;
@@ -535,21 +595,322 @@ __device__ __forceinline__ double fix48_to_double(long long v) {
     return (double)(int)(v >> 32) * 0x1p-16 + (double)(unsigned)(v & 0xffffffffu) * 0x1p-48;
 }
 
-// MODE 0: rows of at most 32 edges (aggregated in windows of whole rows);
-// MODE 1: rows of 33..128 edges (aggregated per mover in a direct-mapped
-// count array of B entries, which follows the warp's BatchWarp in shared
-// memory).  Movers are processed in sub-batches of at most kBatchEdges
-// edge ends.
+// The evaluation of up to 32 movers of one warp: lane q < nv holds mover q
+// (v, s, w2).  MODE 0: rows of at most 32 edges (aggregated in windows of
+// whole rows); MODE 1: rows of 33..128 edges (aggregated per mover in a
+// direct-mapped count array of B entries, dcnt, with its touch list dlist,
+// which follow the warp's BatchWarp in shared memory).  Movers are taken in
+// sub-batches of at most kBatchEdges edge ends.
 template <int MODE, bool DL32>
+__device__ __forceinline__ void batch_movers(const DecideArgs &a, BatchWarp<MODE> &W, unsigned *dcnt, int *dlist,
+                                             const int nv, int v, int s, uint64_t w2, Counts &c) {
+    constexpr int kEdges = MODE == 0 ? kBatchEdges0 : kBatchEdges;
+    const int lane = threadIdx.x & 31;
+    const GraphDev &g = a.g;
+    const ModelDev &md = a.md;
+    const int B = md.B;
+    // ---- P1 (the mover records are in registers)
+    int r = 0, o0 = 0, kout = 0, i0 = 0, kin = 0, k = 0;
+    if (lane < nv) {
+        r = md.b[v];
+        o0 = g.op[v];
+        kout = g.op[v + 1] - o0;
+        i0 = g.ip[v];
+        kin = g.ip[v + 1] - i0;
+        k = kout + kin;
+    } else {
+        v = 0;
+        s = -1;
+        w2 = 0;
+    }
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int first = incl - k;
+    // sub-batches of whole rows with at most kBatchEdges edge ends
+    for (int sa = 0; sa < nv;) {
+    const int fs = __shfl_sync(0xffffffffu, first, sa);
+    const unsigned fit = __ballot_sync(0xffffffffu, lane >= sa && lane < nv && incl - fs <= kEdges);
+    const int sb = 31 - __clz(fit);
+    const int total = __shfl_sync(0xffffffffu, incl, sb) - fs;
+    const bool act = lane >= sa && lane <= sb;
+    // ---- P2 (eight 32-edge chunks in flight for the longer rows of MODE 1)
+    constexpr int kP2 = MODE == 1 ? 8 : 4;
+    for (int base = 0; base < total; base += 32 * kP2) {
+        int nb[kP2], vq[kP2], tag[kP2];
+#pragma unroll
+        for (int c4 = 0; c4 < kP2; ++c4) {
+            const int pp = base + c4 * 32 + lane;
+            const int p = fs + pp;
+            int q = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int f = __shfl_sync(0xffffffffu, first, q + st);
+                if (f <= p) q += st;
+            }
+            const int fq = __shfl_sync(0xffffffffu, first, q);
+            const int kq = __shfl_sync(0xffffffffu, kout, q);
+            const int oq = __shfl_sync(0xffffffffu, o0, q);
+            const int iq = __shfl_sync(0xffffffffu, i0, q);
+            vq[c4] = __shfl_sync(0xffffffffu, v, q);
+            const int e = p - fq;
+            tag[c4] = (q << 26) | (e < kq ? 0 : 1);
+            nb[c4] = pp < total ? nb_raw(g, md, oq, iq, kq, e) : 0;
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < kP2; ++c4) {
+            const int pp = base + c4 * 32 + lane;
+            if (pp < total) {
+                bool sfl;
+                const int t = nb_block(md, nb[c4], vq[c4], sfl);
+                W.key[pp] = sfl ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
+            }
+        }
+    }
+    __syncwarp();
+    int nent = 0, my_self = 0, my_est = 0, my_ecnt = 0;
+    if (MODE == 0) {
+    // ---- P3: windows of whole rows
+    for (int qa = sa; qa <= sb;) {
+        const int fa = __shfl_sync(0xffffffffu, first, qa);
+        const unsigned inw = __ballot_sync(0xffffffffu, lane >= qa && lane <= sb && incl - fa <= 32);
+        const int qb = 31 - __clz(inw);
+        const int wend = __shfl_sync(0xffffffffu, incl, qb);
+        const int p = fa + lane;
+        const bool valid = p < wend;
+        const int x = valid ? W.key[p - fs] : 0;
+        const bool selfl = valid && ((x >> 25) & 1);
+        const bool in = (x & 1) != 0;
+        const bool isent = valid && !selfl;
+        const int mkey = isent ? (x >> 1) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, mkey);
+        const unsigned outm = __ballot_sync(0xffffffffu, isent && !in);
+        const unsigned sfl = __ballot_sync(0xffffffffu, selfl && !in);
+        const bool leader = isent && lane == __ffs(peers) - 1;
+        const unsigned lm = __ballot_sync(0xffffffffu, leader);
+        if (leader) {
+            const int ko = __popc(peers & outm), ki = __popc(peers) - ko;
+            const int pos = nent + __popc(lm & ((1u << lane) - 1u));
+            W.key[pos] = (x & (31 << 26)) | ((x >> 1) & 0xffffff);
+            W.ec[pos] = (unsigned short)(ko | (ki << 8));
+        }
+        if (lane >= qa && lane <= qb) {
+            const int lo_l = first - fa, hi_l = incl - fa;
+            const unsigned below = (1u << lo_l) - 1u;
+            const unsigned mq = (hi_l >= 32 ? 0xffffffffu : ((1u << hi_l) - 1u)) & ~below;
+            my_self = __popc(sfl & mq);
+            my_est = nent + __popc(lm & below);
+            my_ecnt = __popc(lm & mq);
+        }
+        nent += __popc(lm);
+        qa = qb + 1;
+    }
+    } else {
+    // ---- P3: per mover, direct-mapped counts; first touches kept in
+    // order of appearance (ballot compaction), so entries are deterministic
+    for (int q = sa; q <= sb; ++q) {
+        const int kq = __shfl_sync(0xffffffffu, k, q);
+        const int fq = __shfl_sync(0xffffffffu, first, q) - fs;
+        int nl = 0, selfq = 0;
+        for (int c0 = 0; c0 < kq; c0 += 32) {
+            const bool valid = c0 + lane < kq;
+            const int x = valid ? W.key[fq + c0 + lane] : 0;
+            const bool selfl = valid && ((x >> 25) & 1);
+            const bool in = (x & 1) != 0;
+            const bool isent = valid && !selfl;
+            const int t = isent ? ((x >> 1) & 0xffffff) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, t);
+            const unsigned outm = __ballot_sync(0xffffffffu, isent && !in);
+            selfq += __popc(__ballot_sync(0xffffffffu, selfl && !in));
+            const bool leader = isent && lane == __ffs(peers) - 1;
+            bool fresh = false;
+            if (leader) {
+                const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
+                fresh = atomicAdd(&dcnt[t], ko | (ki << 16)) == 0u;
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            if (fresh) dlist[nl + __popc(fm & ((1u << lane) - 1u))] = t;
+            nl += __popc(fm);
+            __syncwarp();
+        }
+        for (int e = lane; e < nl; e += 32) {
+            const int t = dlist[e];
+            const unsigned cc = dcnt[t];
+            dcnt[t] = 0u;
+            W.key[nent + e] = (q << 26) | t;
+            W.ec[nent + e] = (unsigned short)((cc & 0xffu) | ((cc >> 16) << 8));
+        }
+        if (lane == q) {
+            my_self = selfq;
+            my_est = nent;
+            my_ecnt = nl;
+        }
+        nent += nl;
+        __syncwarp();
+    }
+    }
+    W.r[lane] = r;
+    W.s[lane] = act ? s : -1;
+    W.rsr[lane] = 0;
+    W.rss[lane] = 0;
+    W.hasfb[lane] = 0;
+    W.dl[lane] = 0;
+    W.pf[lane] = 0.0f;
+    W.pb[lane] = 0.0f;
+    W.dlf[lane] = 0.0f;
+    W.am[lane] = 0.0f;
+    W.fb[lane] = 0.0;
+    __syncwarp();
+    // ---- P5: entry parallel, segmented sums per mover
+    for (int base = 0; base < nent; base += 32) {
+        const int e = base + lane;
+        const bool valid = e < nent;
+        const unsigned ent = valid ? (unsigned)W.key[e] : 0u;
+        const int q = valid ? (int)(ent >> 26) : 32;
+        long long d48 = 0;
+        float pfe = 0.0f, pbe = 0.0f, dlf = 0.0f, am = 0.0f;
+        double f = 0.0;
+        if (valid) {
+            const int t = (int)(ent & 0x3ffffffu);
+            const unsigned ec = W.ec[e];
+            const int ko = (int)(ec & 0xffu), ki = (int)(ec >> 8);
+            const int rq = W.r[q], sq = W.s[q];
+            if (t == rq) {
+                W.rsr[q] = ko | (ki << 8);
+            } else if (t == sq) {
+                W.rss[q] = ko | (ki << 8);
+            } else {
+                VertexCtx x;
+                x.r = rq;
+                x.s = sq;
+                if (DL32) {
+                    entry_fast32(md, x, t, ko, ki, dlf, am, pfe, pbe);
+                } else {
+                    __int128 d = 0;
+                    entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
+                    d48 = (long long)(d >> 16);
+                }
+            }
+        }
+        const bool anyfb = !DL32 && __any_sync(0xffffffffu, __double_as_longlong(f) != 0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int qo = __shfl_up_sync(0xffffffffu, q, o);
+            const float p2 = __shfl_up_sync(0xffffffffu, pfe, o);
+            const float b2 = __shfl_up_sync(0xffffffffu, pbe, o);
+            if (DL32) {
+                const float l2 = __shfl_up_sync(0xffffffffu, dlf, o);
+                const float a2 = __shfl_up_sync(0xffffffffu, am, o);
+                if (lane >= o && qo == q) {
+                    dlf += l2;
+                    am += a2;
+                }
+            } else {
+                const long long d2 = __shfl_up_sync(0xffffffffu, d48, o);
+                if (lane >= o && qo == q) d48 += d2;
+            }
+            if (lane >= o && qo == q) {
+                pfe += p2;
+                pbe += b2;
+            }
+        }
+        if (anyfb) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int qo = __shfl_up_sync(0xffffffffu, q, o);
+                const double f2 = __shfl_up_sync(0xffffffffu, f, o);
+                if (lane >= o && qo == q) f += f2;
+            }
+        }
+        const int qn = __shfl_down_sync(0xffffffffu, q, 1);
+        if (valid && (lane == 31 || qn != q)) {
+            if (DL32) {
+                W.dlf[q] += dlf;
+                W.am[q] += am;
+            } else {
+                W.dl[q] += d48;
+            }
+            W.pf[q] += pfe;
+            W.pb[q] += pbe;
+            if (anyfb && __double_as_longlong(f) != 0) {
+                W.fb[q] += f;
+                W.hasfb[q] = 1;
+            }
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    // ---- P6: lane per mover
+    if (act) {
+        c.entries += (unsigned)my_ecnt;
+        VertexCtx x;
+        x.v = v; x.r = r; x.s = s;
+        x.Kout = kout; x.Kin = kin; x.self = my_self; x.k = k;
+        const int rsr = W.rsr[lane], rss = W.rss[lane];
+        x.ko_r = rsr & 0xff; x.ki_r = rsr >> 8;
+        x.ko_s = rss & 0xff; x.ki_s = rss >> 8;
+        __int128 d = 0;
+        bool has_fb = W.hasfb[lane] != 0;
+        double fb = has_fb ? W.fb[lane] : 0.0;
+        float dlf = W.dlf[lane], am = W.am[lane];
+        CornerVals cv;
+        if (DL32) {
+            cv.Mrr = special_terms32(md, x, 0, dlf, am);
+            cv.Mss = special_terms32(md, x, 1, dlf, am);
+            cv.Mrs = special_terms32(md, x, 2, dlf, am);
+            cv.Msr = special_terms32(md, x, 3, dlf, am);
+#pragma unroll
+            for (int jj = 4; jj < 8; ++jj) special_terms32(md, x, jj, dlf, am);
+        } else {
+            cv.Mrr = special_terms(md, x, 0, d, fb);
+            cv.Mss = special_terms(md, x, 1, d, fb);
+            cv.Mrs = special_terms(md, x, 2, d, fb);
+            cv.Msr = special_terms(md, x, 3, d, fb);
+#pragma unroll
+            for (int jj = 4; jj < 8; ++jj) special_terms(md, x, jj, d, fb);
+            has_fb = has_fb || __double_as_longlong(fb) != 0;
+        }
+        cv.dr = md.dsum[r];
+        cv.ds = md.dsum[s];
+        long long dl48 = W.dl[lane] + (long long)(d >> 16);
+        float pf = W.pf[lane], pb = W.pb[lane];
+        corner_hastings_fast(x, cv, B, pf, pb);
+        int dec = -1;
+        if (!a.trace_on) {
+            if (DL32)
+                dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, k, dl32_error(am, k));
+            else
+                dec = fast_decision_f(a.beta32, fix48_to_float(dl48), has_fb ? (float)fb : 0.0f, pf, pb, w2, k);
+        }
+        if (dec >= 0) {
+            if (dec) accept_move(md, v, s, k);
+            count_result(c, dec != 0, false, k);
+        } else {
+            push_recheck(a, v, s, w2);  // the exact evaluation follows the pass
+        }
+    }
+    __syncwarp();
+        sa = sb + 1;
+    }
+}
+
+// k_eval_batch: 32 movers per warp.  FUSED = false: the movers come from the
+// list of degree group `bin` that k_propose filled.  FUSED = true: the warps
+// draw the proposals of that group's vertices themselves (32 per round, lane
+// per vertex), keep the movers in a queue of two slots per lane (position p
+// in lane p % 32, slot p / 32) and evaluate them 32 at a time, so that the
+// proposals' load chains overlap other warps' evaluation.
+template <int MODE, bool DL32, bool FUSED>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MODE == 0 ? SBP_BATCH0_MIN_BLOCKS : SBP_DECIDE_MIN_BLOCKS)
     k_eval_batch(DecideArgs a, int bin, int warp_bytes) {
     extern __shared__ __align__(16) unsigned char bsm[];
-    constexpr int kEdges = MODE == 0 ? kBatchEdges0 : kBatchEdges;
     using BW = BatchWarp<MODE>;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     BW &W = *reinterpret_cast<BW *>(bsm + (size_t)wid * warp_bytes);
     unsigned *dcnt = reinterpret_cast<unsigned *>(bsm + (size_t)wid * warp_bytes + sizeof(BW));
-    const GraphDev &g = a.g;
     const ModelDev &md = a.md;
     const int B = md.B;
     int *dlist = reinterpret_cast<int *>(dcnt + B);
@@ -557,301 +918,72 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MODE == 0 ? SBP_BATCH0_MIN_
         for (int i = lane; i < B; i += 32) dcnt[i] = 0u;
         __syncwarp();
     }
-    const Mover *mlist = a.movers + a.mbase[bin];
-    const int64_t count = *(volatile unsigned *)&a.mcount[bin];
     Counts c;
-    const int64_t nbatch = (count + 31) >> 5;
-    for (int64_t bt = (int64_t)blockIdx.x * nwarps + wid; bt < nbatch; bt += (int64_t)gridDim.x * nwarps) {
-        const int64_t first_i = bt << 5;
-        const int nv = (int)(count - first_i < 32 ? count - first_i : 32);
-        // ---- P1
-        int v = 0, s = -1, r = 0, o0 = 0, kout = 0, i0 = 0, kin = 0, k = 0;
-        uint64_t w2 = 0;
-        if (lane < nv) {
-            const Mover mv = mlist[first_i + lane];
-            v = mv.v;
-            s = mv.s;
-            w2 = mv.w2;
-            r = md.b[v];
-            o0 = g.op[v];
-            kout = g.op[v + 1] - o0;
-            i0 = g.ip[v];
-            kin = g.ip[v + 1] - i0;
-            k = kout + kin;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + wid, nw = (int64_t)gridDim.x * nwarps;
+    if constexpr (!FUSED) {
+        const Mover *mlist = a.movers + a.mbase[bin];
+        const int64_t count = *(volatile unsigned *)&a.mcount[bin];
+        const int64_t nbatch = (count + 31) >> 5;
+        for (int64_t bt = gw; bt < nbatch; bt += nw) {
+            const int64_t first_i = bt << 5;
+            const int nv = (int)(count - first_i < 32 ? count - first_i : 32);
+            Mover mv{0, -1, 0ull};
+            if (lane < nv) mv = mlist[first_i + lane];
+            batch_movers<MODE, DL32>(a, W, dcnt, dlist, nv, mv.v, mv.s, mv.w2, c);
         }
-        int incl = k;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int first = incl - k;
-        // sub-batches of whole rows with at most kBatchEdges edge ends
-        for (int sa = 0; sa < nv;) {
-        const int fs = __shfl_sync(0xffffffffu, first, sa);
-        const unsigned fit = __ballot_sync(0xffffffffu, lane >= sa && lane < nv && incl - fs <= kEdges);
-        const int sb = 31 - __clz(fit);
-        const int total = __shfl_sync(0xffffffffu, incl, sb) - fs;
-        const bool act = lane >= sa && lane <= sb;
-        // ---- P2 (eight 32-edge chunks in flight for the longer rows of MODE 1)
-        constexpr int kP2 = MODE == 1 ? 8 : 4;
-        for (int base = 0; base < total; base += 32 * kP2) {
-            int nb[kP2], vq[kP2], tag[kP2];
-#pragma unroll
-            for (int c4 = 0; c4 < kP2; ++c4) {
-                const int pp = base + c4 * 32 + lane;
-                const int p = fs + pp;
-                int q = 0;
-#pragma unroll
-                for (int st = 16; st >= 1; st >>= 1) {
-                    const int f = __shfl_sync(0xffffffffu, first, q + st);
-                    if (f <= p) q += st;
-                }
-                const int fq = __shfl_sync(0xffffffffu, first, q);
-                const int kq = __shfl_sync(0xffffffffu, kout, q);
-                const int oq = __shfl_sync(0xffffffffu, o0, q);
-                const int iq = __shfl_sync(0xffffffffu, i0, q);
-                vq[c4] = __shfl_sync(0xffffffffu, v, q);
-                const int e = p - fq;
-                tag[c4] = (q << 26) | (e < kq ? 0 : 1);
-                nb[c4] = pp < total ? nb_raw(g, md, oq, iq, kq, e) : 0;
-            }
-#pragma unroll
-            for (int c4 = 0; c4 < kP2; ++c4) {
-                const int pp = base + c4 * 32 + lane;
-                if (pp < total) {
-                    bool sfl;
-                    const int t = nb_block(md, nb[c4], vq[c4], sfl);
-                    W.key[pp] = sfl ? (tag[c4] | (1 << 25)) : (tag[c4] | (t << 1));
-                }
-            }
-        }
-        __syncwarp();
-        int nent = 0, my_self = 0, my_est = 0, my_ecnt = 0;
-        if (MODE == 0) {
-        // ---- P3: windows of whole rows
-        for (int qa = sa; qa <= sb;) {
-            const int fa = __shfl_sync(0xffffffffu, first, qa);
-            const unsigned inw = __ballot_sync(0xffffffffu, lane >= qa && lane <= sb && incl - fa <= 32);
-            const int qb = 31 - __clz(inw);
-            const int wend = __shfl_sync(0xffffffffu, incl, qb);
-            const int p = fa + lane;
-            const bool valid = p < wend;
-            const int x = valid ? W.key[p - fs] : 0;
-            const bool selfl = valid && ((x >> 25) & 1);
-            const bool in = (x & 1) != 0;
-            const bool isent = valid && !selfl;
-            const int mkey = isent ? (x >> 1) : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, mkey);
-            const unsigned outm = __ballot_sync(0xffffffffu, isent && !in);
-            const unsigned sfl = __ballot_sync(0xffffffffu, selfl && !in);
-            const bool leader = isent && lane == __ffs(peers) - 1;
-            const unsigned lm = __ballot_sync(0xffffffffu, leader);
-            if (leader) {
-                const int ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                const int pos = nent + __popc(lm & ((1u << lane) - 1u));
-                W.key[pos] = (x & (31 << 26)) | ((x >> 1) & 0xffffff);
-                W.ec[pos] = (unsigned short)(ko | (ki << 8));
-            }
-            if (lane >= qa && lane <= qb) {
-                const int lo_l = first - fa, hi_l = incl - fa;
-                const unsigned below = (1u << lo_l) - 1u;
-                const unsigned mq = (hi_l >= 32 ? 0xffffffffu : ((1u << hi_l) - 1u)) & ~below;
-                my_self = __popc(sfl & mq);
-                my_est = nent + __popc(lm & below);
-                my_ecnt = __popc(lm & mq);
-            }
-            nent += __popc(lm);
-            qa = qb + 1;
-        }
-        } else {
-        // ---- P3: per mover, direct-mapped counts; first touches kept in
-        // order of appearance (ballot compaction), so entries are deterministic
-        for (int q = sa; q <= sb; ++q) {
-            const int kq = __shfl_sync(0xffffffffu, k, q);
-            const int fq = __shfl_sync(0xffffffffu, first, q) - fs;
-            int nl = 0, selfq = 0;
-            for (int c0 = 0; c0 < kq; c0 += 32) {
-                const bool valid = c0 + lane < kq;
-                const int x = valid ? W.key[fq + c0 + lane] : 0;
-                const bool selfl = valid && ((x >> 25) & 1);
-                const bool in = (x & 1) != 0;
-                const bool isent = valid && !selfl;
-                const int t = isent ? ((x >> 1) & 0xffffff) : -1;
-                const unsigned peers = __match_any_sync(0xffffffffu, t);
-                const unsigned outm = __ballot_sync(0xffffffffu, isent && !in);
-                selfq += __popc(__ballot_sync(0xffffffffu, selfl && !in));
-                const bool leader = isent && lane == __ffs(peers) - 1;
-                bool fresh = false;
-                if (leader) {
-                    const unsigned ko = __popc(peers & outm), ki = __popc(peers) - ko;
-                    fresh = atomicAdd(&dcnt[t], ko | (ki << 16)) == 0u;
-                }
-                const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-                if (fresh) dlist[nl + __popc(fm & ((1u << lane) - 1u))] = t;
-                nl += __popc(fm);
-                __syncwarp();
-            }
-            for (int e = lane; e < nl; e += 32) {
-                const int t = dlist[e];
-                const unsigned cc = dcnt[t];
-                dcnt[t] = 0u;
-                W.key[nent + e] = (q << 26) | t;
-                W.ec[nent + e] = (unsigned short)((cc & 0xffu) | ((cc >> 16) << 8));
-            }
-            if (lane == q) {
-                my_self = selfq;
-                my_est = nent;
-                my_ecnt = nl;
-            }
-            nent += nl;
-            __syncwarp();
-        }
-        }
-        W.r[lane] = r;
-        W.s[lane] = act ? s : -1;
-        W.rsr[lane] = 0;
-        W.rss[lane] = 0;
-        W.hasfb[lane] = 0;
-        W.dl[lane] = 0;
-        W.pf[lane] = 0.0f;
-        W.pb[lane] = 0.0f;
-        W.dlf[lane] = 0.0f;
-        W.am[lane] = 0.0f;
-        W.fb[lane] = 0.0;
-        __syncwarp();
-        // ---- P5: entry parallel, segmented sums per mover
-        for (int base = 0; base < nent; base += 32) {
-            const int e = base + lane;
-            const bool valid = e < nent;
-            const unsigned ent = valid ? (unsigned)W.key[e] : 0u;
-            const int q = valid ? (int)(ent >> 26) : 32;
-            long long d48 = 0;
-            float pfe = 0.0f, pbe = 0.0f, dlf = 0.0f, am = 0.0f;
-            double f = 0.0;
-            if (valid) {
-                const int t = (int)(ent & 0x3ffffffu);
-                const unsigned ec = W.ec[e];
-                const int ko = (int)(ec & 0xffu), ki = (int)(ec >> 8);
-                const int rq = W.r[q], sq = W.s[q];
-                if (t == rq) {
-                    W.rsr[q] = ko | (ki << 8);
-                } else if (t == sq) {
-                    W.rss[q] = ko | (ki << 8);
-                } else {
-                    VertexCtx x;
-                    x.r = rq;
-                    x.s = sq;
-                    if (DL32) {
-                        entry_fast32(md, x, t, ko, ki, dlf, am, pfe, pbe);
+        flush_counts_warp(md, c, 0ull);
+    } else {
+        const int32_t *vl = a.vlist[bin];
+        const int64_t vcount = a.vcount[bin];
+        const int64_t nvb = (vcount + 31) >> 5;
+        unsigned long long medges = 0;
+        int q0v = 0, q0s = -1, q1v = 0, q1s = -1, nq = 0;
+        uint64_t q0w = 0, q1w = 0;
+        for (int64_t vb = gw;; vb += nw) {
+            const bool more = vb < nvb;
+            if (more) {
+                const int64_t i = (vb << 5) + lane;
+                bool mover = false;
+                int pv = 0, ps = 0;
+                uint64_t pw = 0;
+                if (i < vcount) {
+                    pv = vl[i];
+                    const Proposal p = propose_vertex(a.g, md, a.seed, a.sweep_id, pv);
+                    if (p.s == p.r) {
+                        c.proposed++;
                     } else {
-                        __int128 d = 0;
-                        entry_fast(md, x, t, ko, ki, d, f, pfe, pbe);
-                        d48 = (long long)(d >> 16);
+                        mover = true;
+                        ps = p.s;
+                        pw = p.w2;
+                        medges += (unsigned long long)p.k;
                     }
                 }
+                const unsigned mask = __ballot_sync(0xffffffffu, mover);
+                const int cnt = __popc(mask);
+                // queue positions nq .. nq + cnt - 1 take the new movers in lane order
+                const int r0 = lane - nq, r1 = 32 + lane - nq;
+                const bool t0 = r0 >= 0 && r0 < cnt, t1 = r1 >= 0 && r1 < cnt;
+                const int src0 = t0 ? nth_set_bit(mask, r0) : lane, src1 = t1 ? nth_set_bit(mask, r1) : lane;
+                const int v0 = __shfl_sync(0xffffffffu, pv, src0), s0 = __shfl_sync(0xffffffffu, ps, src0);
+                const uint64_t w0 = __shfl_sync(0xffffffffu, pw, src0);
+                const int v1 = __shfl_sync(0xffffffffu, pv, src1), s1 = __shfl_sync(0xffffffffu, ps, src1);
+                const uint64_t w1 = __shfl_sync(0xffffffffu, pw, src1);
+                if (t0) { q0v = v0; q0s = s0; q0w = w0; }
+                if (t1) { q1v = v1; q1s = s1; q1w = w1; }
+                nq += cnt;
             }
-            const bool anyfb = !DL32 && __any_sync(0xffffffffu, __double_as_longlong(f) != 0);
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int qo = __shfl_up_sync(0xffffffffu, q, o);
-                const float p2 = __shfl_up_sync(0xffffffffu, pfe, o);
-                const float b2 = __shfl_up_sync(0xffffffffu, pbe, o);
-                if (DL32) {
-                    const float l2 = __shfl_up_sync(0xffffffffu, dlf, o);
-                    const float a2 = __shfl_up_sync(0xffffffffu, am, o);
-                    if (lane >= o && qo == q) {
-                        dlf += l2;
-                        am += a2;
-                    }
-                } else {
-                    const long long d2 = __shfl_up_sync(0xffffffffu, d48, o);
-                    if (lane >= o && qo == q) d48 += d2;
-                }
-                if (lane >= o && qo == q) {
-                    pfe += p2;
-                    pbe += b2;
-                }
+            while (nq >= 32 || (!more && nq > 0)) {
+                const int nv = nq < 32 ? nq : 32;
+                const int v = q0v, s = q0s;
+                const uint64_t w2 = q0w;
+                q0v = q1v; q0s = q1s; q0w = q1w;
+                nq -= nv;
+                batch_movers<MODE, DL32>(a, W, dcnt, dlist, nv, v, s, w2, c);
             }
-            if (anyfb) {
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int qo = __shfl_up_sync(0xffffffffu, q, o);
-                    const double f2 = __shfl_up_sync(0xffffffffu, f, o);
-                    if (lane >= o && qo == q) f += f2;
-                }
-            }
-            const int qn = __shfl_down_sync(0xffffffffu, q, 1);
-            if (valid && (lane == 31 || qn != q)) {
-                if (DL32) {
-                    W.dlf[q] += dlf;
-                    W.am[q] += am;
-                } else {
-                    W.dl[q] += d48;
-                }
-                W.pf[q] += pfe;
-                W.pb[q] += pbe;
-                if (anyfb && __double_as_longlong(f) != 0) {
-                    W.fb[q] += f;
-                    W.hasfb[q] = 1;
-                }
-            }
-            __syncwarp();
+            if (!more) break;
         }
-        __syncwarp();
-        // ---- P6: lane per mover
-        if (act) {
-            VertexCtx x;
-            x.v = v; x.r = r; x.s = s;
-            x.Kout = kout; x.Kin = kin; x.self = my_self; x.k = k;
-            const int rsr = W.rsr[lane], rss = W.rss[lane];
-            x.ko_r = rsr & 0xff; x.ki_r = rsr >> 8;
-            x.ko_s = rss & 0xff; x.ki_s = rss >> 8;
-            __int128 d = 0;
-            bool has_fb = W.hasfb[lane] != 0;
-            double fb = has_fb ? W.fb[lane] : 0.0;
-            float dlf = W.dlf[lane], am = W.am[lane];
-            CornerVals cv;
-            if (DL32) {
-                cv.Mrr = special_terms32(md, x, 0, dlf, am);
-                cv.Mss = special_terms32(md, x, 1, dlf, am);
-                cv.Mrs = special_terms32(md, x, 2, dlf, am);
-                cv.Msr = special_terms32(md, x, 3, dlf, am);
-#pragma unroll
-                for (int jj = 4; jj < 8; ++jj) special_terms32(md, x, jj, dlf, am);
-            } else {
-                cv.Mrr = special_terms(md, x, 0, d, fb);
-                cv.Mss = special_terms(md, x, 1, d, fb);
-                cv.Mrs = special_terms(md, x, 2, d, fb);
-                cv.Msr = special_terms(md, x, 3, d, fb);
-#pragma unroll
-                for (int jj = 4; jj < 8; ++jj) special_terms(md, x, jj, d, fb);
-                has_fb = has_fb || __double_as_longlong(fb) != 0;
-            }
-            cv.dr = md.dsum[r];
-            cv.ds = md.dsum[s];
-            long long dl48 = W.dl[lane] + (long long)(d >> 16);
-            float pf = W.pf[lane], pb = W.pb[lane];
-            corner_hastings_fast(x, cv, B, pf, pb);
-            int dec = -1;
-            if (!a.trace_on) {
-                if (DL32)
-                    dec = fast_decision_f(a.beta32, dlf, 0.0f, pf, pb, w2, k, dl32_error(am, k));
-                else
-                    dec = fast_decision_f(a.beta32, fix48_to_float(dl48), has_fb ? (float)fb : 0.0f, pf, pb, w2, k);
-            }
-            if (dec >= 0) {
-                if (dec) accept_move(md, v, s, k);
-                count_result(c, dec != 0, false, k);
-            } else {
-                push_recheck(a, v, s, w2);  // the exact evaluation follows the pass
-            }
-        }
-        __syncwarp();
-            sa = sb + 1;
-        }
+        flush_counts_warp(md, c, medges);
     }
-    flush_counts_warp(md, c, 0ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -1204,8 +1336,9 @@ int join_evals(sbp_model *m) {
     return SBP_OK;
 }
 
-// the evaluation kernels of the three degree groups (after k_propose)
-template <bool DL32>
+// the evaluation kernels of the three degree groups: after k_propose, or
+// (FUSED) drawing the proposals themselves
+template <bool DL32, bool FUSED>
 int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t st[3]) {
     const sbp_graph *g = m->g;
     const int B = m->B;
@@ -1217,8 +1350,8 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
         const int warp_words = 2 * B + 4;
         const int nwarps = warp_words * 4 * kWarpsPerCta <= 64 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
         const size_t smem = (size_t)warp_words * 4 * nwarps;
-        SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp_direct<DL32>, smem));
-        k_eval_warp_direct<DL32><<<sms * 4, nwarps * 32, smem, st[2]>>>(a, 2, warp_words);
+        SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp_direct<DL32, FUSED>, smem));
+        k_eval_warp_direct<DL32, FUSED><<<sms * 4, nwarps * 32, smem, st[2]>>>(a, 2, warp_words);
         SBP_LAUNCHED();
     } else if (g->bin[4] > g->bin[3]) {
         const int64_t dmax = g->max_deg < B ? g->max_deg : B;
@@ -1246,8 +1379,8 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
     if (g->bin[2] > g->bin[1]) {
         const int wb = (int)((sizeof(BatchWarp<0>) + 15) / 16 * 16);
         const size_t smem = (size_t)wb * kWarpsPerCta;
-        SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<0, DL32>, smem));
-        k_eval_batch<0, DL32><<<sms * SBP_BATCH0_MIN_BLOCKS, kWarpsPerCta * 32, smem, st[0]>>>(a, 0, wb);
+        SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<0, DL32, FUSED>, smem));
+        k_eval_batch<0, DL32, FUSED><<<sms * SBP_BATCH0_MIN_BLOCKS, kWarpsPerCta * 32, smem, st[0]>>>(a, 0, wb);
         SBP_LAUNCHED();
     }
     // movers with 33 <= k <= 128: batches with direct-mapped counts while B is
@@ -1257,8 +1390,8 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
             const int wb = (int)((sizeof(BatchWarp<1>) + 4 * (size_t)B + 4 * kWarpDeg + 15) / 16 * 16);
             const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
             const size_t smem = (size_t)wb * nwarps;
-            SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32>, smem));
-            k_eval_batch<1, DL32><<<sms * 3, nwarps * 32, smem, st[1]>>>(a, 1, wb);
+            SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32, FUSED>, smem));
+            k_eval_batch<1, DL32, FUSED><<<sms * 3, nwarps * 32, smem, st[1]>>>(a, 1, wb);
             SBP_LAUNCHED();
         } else {
             const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
@@ -1294,10 +1427,10 @@ int launch_recheck(sbp_model *m, const DecideArgs &a0, int sms) {
 }
 
 template <bool DL32>
-int launch_evals(sbp_model *m, const DecideArgs &a, int sms) {
+int launch_evals(sbp_model *m, const DecideArgs &a, int sms, bool fused) {
     cudaStream_t st[3];
     SBP_TRY(fork_evals(m, st));
-    const int rc = launch_groups<DL32>(m, a, sms, st);
+    const int rc = fused ? launch_groups<DL32, true>(m, a, sms, st) : launch_groups<DL32, false>(m, a, sms, st);
     const int rj = join_evals(m);  // joined on every path
     if (rc != SBP_OK) return rc;
     if (rj != SBP_OK) return rj;
@@ -1396,15 +1529,24 @@ int launch_decide(sbp_model *m, uint64_t sweep_id, int64_t v_begin, int64_t v_en
         a.skip = m->skip;
     }
 
-    // proposals for every vertex of the range
-    {
+    // A full-range pass with no trace and no sequential part, whose degree
+    // groups all take the direct-mapped kernels, draws the proposals inside
+    // the evaluation kernels; any other pass proposes every vertex of its
+    // range first (k_propose) and hands the movers over in lists.
+    for (int i = 0; i < 3; ++i) {
+        a.vlist[i] = g->order + g->bin[i + 1];
+        a.vcount[i] = g->bin[i + 2] - g->bin[i + 1];
+    }
+    const bool fused = SBP_FUSED_PROPOSALS && v_begin == 0 && v_end == g->n && !a.skip && !a.trace_on &&
+                       B <= kDirectMaxB && g->max_deg < 65536;
+    if (!fused) {
         int64_t blocks = (v_end - v_begin + 255) / 256;
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         if (blocks < 1) blocks = 1;
         k_propose<<<(int)blocks, 256, 0, m->stream>>>(a);
         SBP_LAUNCHED();
     }
-    return m->p.dl_fp32 ? launch_evals<true>(m, a, sms) : launch_evals<false>(m, a, sms);
+    return m->p.dl_fp32 ? launch_evals<true>(m, a, sms, fused) : launch_evals<false>(m, a, sms, fused);
 }
 
 }  // namespace sbp

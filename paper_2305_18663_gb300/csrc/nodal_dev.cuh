@@ -53,10 +53,34 @@ struct DecideArgs {
     int trace_on;
     sbp_vertex_trace tr;
     const uint8_t *skip;     // NULL, or vertices this pass leaves alone (the hybrid pass's sequential part)
+    // the vertices of the three degree groups (k <= 32, 33..128, > 128), for
+    // the kernels that draw the proposals themselves
+    const int32_t *vlist[3];
+    int64_t vcount[3];
 };
 
+// position of the k-th (0-based) set bit of m, for k < popc(m)
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const unsigned lo = m & ((1u << w) - 1u);
+        const int c = __popc(lo);
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = lo;
+        }
+    }
+    return pos;
+}
+
+// per-thread counts (32-bit: every sum over a pass is at most 2E < 2^32,
+// since the CSR offsets are 32-bit); widened when flushed
 struct Counts {
-    unsigned long long proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0, recheck = 0;
+    unsigned proposed = 0, moves = 0, accepted = 0, margin = 0, acc_edges = 0, recheck = 0, entries = 0;
 };
 
 // a mover the FP32 test could not settle (or any mover when a trace is
@@ -384,7 +408,7 @@ __device__ __forceinline__ void count_result(Counts &c, bool accept, bool margin
     c.moves++;
     c.accepted += accept;
     c.margin += margin;
-    c.acc_edges += accept ? (unsigned long long)k : 0ull;
+    c.acc_edges += accept ? (unsigned)k : 0u;
 }
 
 // a move decided by the exact evaluation
@@ -397,13 +421,15 @@ __device__ __forceinline__ void count_exact(Counts &c, bool accept, bool margin,
 // proposals: one lane per vertex, all vertices of the range
 
 __device__ __forceinline__ void flush_counts(const ModelDev &md, const Counts &c) {
+    typedef unsigned long long u64;
     if (c.proposed | c.moves) {
-        atomicAdd(&md.counters->proposed, c.proposed);
-        atomicAdd(&md.counters->moves, c.moves);
-        atomicAdd(&md.counters->accepted, c.accepted);
-        atomicAdd(&md.counters->margin, c.margin);
-        if (c.acc_edges) atomicAdd(&md.counters->acc_edges, c.acc_edges);
-        if (c.recheck) atomicAdd(&md.counters->recheck, c.recheck);
+        atomicAdd(&md.counters->proposed, (u64)c.proposed);
+        atomicAdd(&md.counters->moves, (u64)c.moves);
+        atomicAdd(&md.counters->accepted, (u64)c.accepted);
+        atomicAdd(&md.counters->margin, (u64)c.margin);
+        if (c.acc_edges) atomicAdd(&md.counters->acc_edges, (u64)c.acc_edges);
+        if (c.recheck) atomicAdd(&md.counters->recheck, (u64)c.recheck);
+        if (c.entries) atomicAdd(&md.counters->entries, (u64)c.entries);
     }
 }
 
@@ -416,6 +442,7 @@ __device__ __forceinline__ void flush_counts_warp(const ModelDev &md, Counts c, 
         c.margin += __shfl_xor_sync(0xffffffffu, c.margin, o);
         c.acc_edges += __shfl_xor_sync(0xffffffffu, c.acc_edges, o);
         c.recheck += __shfl_xor_sync(0xffffffffu, c.recheck, o);
+        c.entries += __shfl_xor_sync(0xffffffffu, c.entries, o);
         extra_edges += __shfl_xor_sync(0xffffffffu, extra_edges, o);
     }
     if ((threadIdx.x & 31) == 0) {

@@ -1,13 +1,37 @@
 """The batching form: every graph of a batch ends with exactly the result of
-its own sbp_partition run (assignment, B, DL, sweep count), whatever the
-batch's schedule (workers, batch limit, admission waves).  Needs a GPU."""
+the oracle's full run (Section II-B: merge phases, MCMC phases, golden-ratio
+search) and of its own sbp_partition run (assignment, B, sweep count
+identical; DL within 1e-12 relative of the oracle's FP64 value, identical to
+sbp_partition's), whatever the batch's schedule (workers, batch limit,
+admission waves).  Needs a GPU."""
+import os
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 import paper_2305_18663_gb300 as P  # noqa: E402
 from synth.dcsbm import batch_specs, dcsbm  # noqa: E402
+
+NT = max(1, min(16, os.cpu_count() or 1))
+_ORACLE = {}
+
+
+def oracle_runs(key, gs, seed):
+    """O.partition of every graph (cached per graph set and seed)."""
+    if (key, seed) not in _ORACLE:
+        _ORACLE[(key, seed)] = [O.partition(O.Graph(g.n, g.src, g.dst), O.Params(seed=seed), nthreads=NT) for g in gs]
+    return _ORACLE[(key, seed)]
+
+
+def assert_matches_oracle(res, ref):
+    b, B, dl, ns = res
+    ob, oB, odl, ons = ref
+    assert B == oB and ns == ons
+    assert dl == pytest.approx(odl, rel=1e-12)
+    assert np.array_equal(b, ob)
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +64,9 @@ def test_batch_equals_plain(opts):
     gs, pgs = _graphs(10, 4000)
     params = P.Params.default(seed=4, dense_max_B=opts.get("dense_max_B", 1024))
     out = P.partition_batch(pgs, params, P.BatchOptions.default(**opts))
-    for g, pg, (b, B, dl, ns, ta, td) in zip(gs, pgs, out):
+    ref = oracle_runs("n4000", gs, 4)
+    for g, pg, (b, B, dl, ns, ta, td), o in zip(gs, pgs, out, ref):
+        assert_matches_oracle((b, B, dl, ns), o)
         pb, pB, pdl, pns = _plain(pg, params)
         assert B == pB and ns == pns
         assert dl == pdl

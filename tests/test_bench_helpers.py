@@ -21,7 +21,16 @@ def test_traffic_figure_only_for_its_form_and_code():
 
 
 def test_algorithmic_bytes_formula():
-    n, m, B, me = 1000, 5000, 10, 1234
-    dec, reb = bench.algorithmic_bytes(n, m, B, me)
-    assert dec == 8 * (n + 1) + 12 * n + 8 * me
+    # the per-sweep bytes of the measurement table: streamed offsets,
+    # labels, the proposal's edge and the moving rows; the proposal's
+    # inverse-CDF search; four blockmodel counts and two degrees per
+    # distinct neighbour block of a moving vertex (hash probes of 8 bytes
+    # on sparse rows)
+    n, m, B, me, ent = 1000, 5000, 10, 1234, 3000
+    dec, streamed, reb = bench.algorithmic_bytes(n, m, B, me, ent)
+    assert streamed == 8 * (n + 1) + 16 * n + 8 * me
+    assert dec == streamed + 4 * 5 * n + ent * (4 * 4 + 8)  # 2B = 20 prefix entries: 5 halvings
     assert reb == 16 * m + 12 * B * B
+    dec_s, streamed_s, _ = bench.algorithmic_bytes(n, m, B, me, ent, sparse=True, nnz=40)
+    assert streamed_s == streamed
+    assert dec_s == streamed + 4 * 3 * n + ent * (4 * 8 + 8)  # rows and columns of 8 entries on average

@@ -1,6 +1,9 @@
 """The serving form: requests submitted while others run are admitted as
 memory frees up, and each result is the same as partitioning the graph
-alone (sbp_partition).  Needs a GPU."""
+alone (sbp_partition) and as the oracle's full run (Section II-B):
+assignment, B and sweep count identical, DL within 1e-12 relative of the
+oracle's FP64 value.  Needs a GPU."""
+import os
 import threading
 import time
 
@@ -9,8 +12,12 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 import paper_2305_18663_gb300 as P  # noqa: E402
 from synth.dcsbm import batch_specs, dcsbm  # noqa: E402
+
+NT = max(1, min(16, os.cpu_count() or 1))
+_ORACLE = {}
 
 pytestmark = pytest.mark.gpu
 
@@ -22,16 +29,20 @@ def _cuda():
     P.load()
 
 
-def _graphs(count, n_hi, seed):
+def _graphs(count, n_hi, seed, with_host=False):
     specs = batch_specs(count, seed=seed, n_lo=300, n_hi=n_hi)
-    return [P.Graph(s["n"], *(lambda g: (g.src, g.dst))(dcsbm(**s))) for s in specs]
+    hg = [dcsbm(**s) for s in specs]
+    pg = [P.Graph(g.n, g.src, g.dst) for g in hg]
+    return (pg, hg) if with_host else pg
 
 
 @pytest.mark.parametrize("opts", [dict(), dict(workers=2, mem_fraction=1e-9)])
 def test_served_results_equal_alone(opts):
-    graphs = _graphs(8, 6000, seed=21)
+    graphs, host = _graphs(8, 6000, seed=21, with_host=True)
     params = P.Params.default(seed=6)
     alone = [g.partition(params) for g in graphs]
+    if "oracle" not in _ORACLE:
+        _ORACLE["oracle"] = [O.partition(O.Graph(g.n, g.src, g.dst), O.Params(seed=6), nthreads=NT) for g in host]
     srv = P.Server(params, P.BatchOptions.default(**opts))
     rids = {}
 
@@ -47,7 +58,9 @@ def test_served_results_equal_alone(opts):
     outs = [srv.wait(rids[i]) for i in range(len(graphs))]
     st = srv.stats()
     srv.close()
-    for (b, B, dl, ns, ts, ta, td), (pb, pB, pdl, pns) in zip(outs, alone):
+    for (b, B, dl, ns, ts, ta, td), (pb, pB, pdl, pns), (ob, oB, odl, ons) in zip(outs, alone, _ORACLE["oracle"]):
+        assert B == oB and ns == ons and np.array_equal(b, ob)
+        assert dl == pytest.approx(odl, rel=1e-12)
         assert B == pB and dl == pdl and ns == pns
         assert np.array_equal(b, pb)
         assert ts <= ta <= td

@@ -1,17 +1,25 @@
-"""The allocation-free DL entry point agrees with the library's own DL.
+"""The allocation-free DL entry point agrees with the library's own DL and
+with the oracle's, and allocates nothing.
 
 sbp_dense_dl_noalloc is for callers that must not allocate device memory
-while running (its scratch is a fixed device array inside the library).
-For the same blockmodel it must give the DL that the model reports through
-sbp_get_dl, within the 1e-12 relative tolerance of the parity tests, call
-after call (the calls share that scratch).  This file is named so pytest
-collects it last.
+while running: a serving process whose memory pool already owns the whole
+device, or code on a latency budget that cannot take cudaMalloc's implicit
+device synchronisation or a late out-of-memory failure.  Its scratch is a
+fixed device array inside the library.  For the same blockmodel it must
+give the DL that the model reports through sbp_get_dl and the DL of the
+oracle's FP64 evaluation of Eq. 2, within the 1e-12 relative tolerance of
+the parity tests.  The checks cover two calls in a row (the calls share
+that scratch), the largest accepted B (4096: every partial-sum slot in
+use), a call on a side stream, and the device's free memory, which must be
+unchanged by a call once the first call has looked up the array's address.
+This file is named so pytest collects it last.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 import paper_2305_18663_gb300 as P  # noqa: E402
 from synth.dcsbm import make_config, random_labels  # noqa: E402
 
@@ -25,32 +33,93 @@ def _cuda():
     P.load()
 
 
-def _dl_noalloc(pm, g, B):
+def _device_blockmodel(pm, B):
     dev = torch.device("cuda")
     M = torch.zeros(B * B, dtype=torch.int32, device=dev)
     dout = torch.zeros(B, dtype=torch.int32, device=dev)
     din = torch.zeros(B, dtype=torch.int32, device=dev)
     P.sbp_get_blockmodel_dense(pm.h, M)
     P.sbp_get_degrees(pm.h, dout, din)
-    out = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
-    P.sbp_dense_dl_noalloc(M, B, dout, din, g.m, g.n, out)
     torch.cuda.synchronize()
+    return M, dout, din
+
+
+def _dl_noalloc(bm, g, B, stream=None):
+    M, dout, din = bm
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    if stream is None:
+        P.sbp_dense_dl_noalloc(M, B, dout, din, g.m, g.n, out)
+        torch.cuda.synchronize()
+    else:
+        stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(stream):
+            P.sbp_dense_dl_noalloc(M, B, dout, din, g.m, g.n, out, stream)
+        stream.synchronize()
     return float(out.item())
 
 
-def test_noalloc_dl_matches_model_dl_on_consecutive_calls():
+def test_noalloc_dl_matches_model_and_oracle_on_consecutive_calls():
     g = make_config("plain_1k")
     pg = P.Graph(g.n, g.src, g.dst)
+    G = O.Graph(g.n, g.src, g.dst)
     seen = {}
     for B, seed in [(64, 1), (500, 2), (64, 1), (1000, 3)]:
         b = random_labels(g.n, B, seed=seed) if B < g.n else np.arange(g.n, dtype=np.int32)
         pm = P.Model(pg, B, b)
-        got = _dl_noalloc(pm, g, B)
+        bm = _device_blockmodel(pm, B)
+        got = _dl_noalloc(bm, g, B)
+        again = _dl_noalloc(bm, g, B)
+        assert got == again  # two calls in a row on the shared scratch
         assert got == pytest.approx(pm.dl(), rel=1e-12)
-        if (B, seed) in seen:  # same input again: same result from the shared scratch
+        assert got == pytest.approx(O.Model(G, B, b).dl(), rel=1e-12)
+        if (B, seed) in seen:  # same input after other inputs: same result
             assert got == seen[(B, seed)]
         seen[(B, seed)] = got
         pm.close()
+
+
+def test_noalloc_dl_at_largest_B_and_on_a_side_stream():
+    # B = 4096: B*B = 2^24 entries fill all 16,384 partial-sum slots
+    g = make_config("dcsbm_1m", seed=0, scale=0.01)
+    B = 4096
+    b = random_labels(g.n, B, seed=7)
+    pm = P.Model(P.Graph(g.n, g.src, g.dst), B, b)
+    bm = _device_blockmodel(pm, B)
+    want = O.Model(O.Graph(g.n, g.src, g.dst), B, b).dl()
+    side = torch.cuda.Stream()
+    on_null = _dl_noalloc(bm, g, B)
+    on_side = _dl_noalloc(bm, g, B, side)
+    assert on_null == on_side
+    assert on_null == pytest.approx(pm.dl(), rel=1e-12)
+    assert on_null == pytest.approx(want, rel=1e-12)
+    # a smaller B right after: slots beyond its partials keep stale values
+    # that it must not read
+    b2 = random_labels(g.n, 37, seed=8)
+    pm2 = P.Model(P.Graph(g.n, g.src, g.dst), 37, b2)
+    small = _dl_noalloc(_device_blockmodel(pm2, 37), g, 37, side)
+    assert small == pytest.approx(O.Model(O.Graph(g.n, g.src, g.dst), 37, b2).dl(), rel=1e-12)
+    pm.close()
+    pm2.close()
+
+
+def test_noalloc_dl_allocates_no_device_memory():
+    g = make_config("plain_1k")
+    B = 300
+    pm = P.Model(P.Graph(g.n, g.src, g.dst), B, random_labels(g.n, B, seed=5))
+    M, dout, din = _device_blockmodel(pm, B)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    P.sbp_dense_dl_noalloc(M, B, dout, din, g.m, g.n, out)  # the first call looks up the array's address
+    torch.cuda.synchronize()
+    torch_bytes = torch.cuda.memory_reserved()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        P.sbp_dense_dl_noalloc(M, B, dout, din, g.m, g.n, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
+    assert torch.cuda.memory_reserved() == torch_bytes
+    assert float(out.item()) == pytest.approx(pm.dl(), rel=1e-12)
+    pm.close()
 
 
 def test_noalloc_dl_rejects_B_beyond_scratch():
