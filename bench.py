@@ -85,7 +85,8 @@ def decide_traffic(m_form: str):
         if kv.get("sources_sha256") != sources_sha256() or kv.get("m_form") != m_form:
             return None
         return {"bytes": float(kv["dram_bytes_per_pass"]), "sweep": kv["sweep"],
-                "algorithmic_bytes": float(kv["algorithmic_bytes_of_that_sweep"])}
+                "algorithmic_bytes": float(kv["algorithmic_bytes_of_that_sweep"]),
+                "streamed_bytes": float(kv["streamed_bytes_of_that_sweep"])}
     except (OSError, KeyError, ValueError):
         return None
 
@@ -401,7 +402,7 @@ def run_ours(args, rank, world, local_rank):
                                                     "blockmodel and degree lookups of every distinct neighbour block "
                                                     "of a moving vertex"),
                          "streamed_bytes": dec_streamed, "streamed_frac": achieved_streamed / hbm,
-                         "sum_D_v": entries, "move_edge_ends": move_edges,
+                         "sum_D_v": entries, "move_edge_ends": move_edges, "nnz": nnz or None,
                          "traffic": traffic["bytes"] if traffic else None,
                          "traffic_note": (f"ncu DRAM bytes of the decide pass of {traffic['sweep']}, whose "
                                           f"algorithmic bytes are {traffic['algorithmic_bytes']:.4g}") if traffic else None},

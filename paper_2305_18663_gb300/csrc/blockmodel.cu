@@ -197,6 +197,22 @@ __global__ void __launch_bounds__(kThreads) k_delta_dense(GraphDev g, const int3
     }
 }
 
+// Adds d to cells[key] for every lane with key >= 0.  The lanes whose key
+// equals that of the first lane holding one add together with one atomic
+// (most edges of a moved vertex land on the same (block, block) cell); the
+// other lanes add their own.  All lanes of the warp call it.
+__device__ __forceinline__ void warp_cell_add(int32_t *cells, int key, int d) {
+    const unsigned act = __ballot_sync(0xffffffffu, key >= 0);
+    if (!act) return;
+    const int lead = __ffs(act) - 1;
+    const int k0 = __shfl_sync(0xffffffffu, key, lead);
+    const unsigned same = __ballot_sync(0xffffffffu, key == k0);
+    if ((int)(threadIdx.x & 31) == lead)
+        atomicAdd(&cells[k0], d * __popc(same));
+    else if (key >= 0 && key != k0)
+        atomicAdd(&cells[key], d);
+}
+
 // The same apply step driven by the accepted-move list: an item is one
 // kMoveChunk-edge slice of the concatenated (out, in) row of a moved vertex,
 // so hubs are spread over many warps and no warp scans unmoved vertices.
@@ -249,17 +265,21 @@ __global__ void __launch_bounds__(kThreads) k_delta_items(GraphDev g, const int2
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const int idx = lo + j * 32 + lane;
-            if (nb[j] < 0) continue;
-            if (idx < kout) {
-                // out-edge v -> w: leaves (r, t), enters (s, u)
-                atomicAdd(&M[(size_t)r * B + t[j]], -1);
-                atomicAdd(&M[(size_t)s * B + u[j]], 1);
-            } else if (u[j] == t[j]) {
-                // in-edge w -> v from a vertex that stayed (a moved source
-                // applies it through its own out-row)
-                atomicAdd(&M[(size_t)t[j] * B + r], -1);
-                atomicAdd(&M[(size_t)t[j] * B + s], 1);
+            int leave = -1, enter = -1;  // cells (B * B <= 2^26) the edge leaves and enters
+            if (nb[j] >= 0) {
+                if (idx < kout) {
+                    // out-edge v -> w: leaves (r, t), enters (s, u)
+                    leave = r * B + t[j];
+                    enter = s * B + u[j];
+                } else if (u[j] == t[j]) {
+                    // in-edge w -> v from a vertex that stayed (a moved
+                    // source applies it through its own out-row)
+                    leave = t[j] * B + r;
+                    enter = t[j] * B + s;
+                }
             }
+            warp_cell_add(M, leave, -1);
+            warp_cell_add(M, enter, 1);
         }
     }
 }

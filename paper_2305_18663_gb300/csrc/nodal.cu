@@ -858,12 +858,7 @@ __device__ __forceinline__ void batch_movers(const DecideArgs &a, BatchWarp<MODE
         float dlf = W.dlf[lane], am = W.am[lane];
         CornerVals cv;
         if (DL32) {
-            cv.Mrr = special_terms32(md, x, 0, dlf, am);
-            cv.Mss = special_terms32(md, x, 1, dlf, am);
-            cv.Mrs = special_terms32(md, x, 2, dlf, am);
-            cv.Msr = special_terms32(md, x, 3, dlf, am);
-#pragma unroll
-            for (int jj = 4; jj < 8; ++jj) special_terms32(md, x, jj, dlf, am);
+            cv = special_terms32_lane(md, x, dlf, am);
         } else {
             cv.Mrr = special_terms(md, x, 0, d, fb);
             cv.Mss = special_terms(md, x, 1, d, fb);
@@ -1391,12 +1386,12 @@ int launch_groups(sbp_model *m, const DecideArgs &a, int sms, const cudaStream_t
             const int nwarps = wb <= 10 * 1024 ? kWarpsPerCta : kWarpsPerCta / 2;
             const size_t smem = (size_t)wb * nwarps;
             SBP_TRY(ensure_dyn_smem((const void *)k_eval_batch<1, DL32, FUSED>, smem));
-            k_eval_batch<1, DL32, FUSED><<<sms * 3, nwarps * 32, smem, st[1]>>>(a, 1, wb);
+            k_eval_batch<1, DL32, FUSED><<<sms * SBP_DECIDE_MIN_BLOCKS, nwarps * 32, smem, st[1]>>>(a, 1, wb);
             SBP_LAUNCHED();
         } else {
             const size_t smem = warp_smem(kWarpCap, kWarpsPerCta);
             SBP_TRY(ensure_dyn_smem((const void *)k_eval_warp<DL32>, smem));
-            k_eval_warp<DL32><<<sms * 3, kWarpsPerCta * 32, smem, st[1]>>>(a, 1, kWarpCap, 8, 32);
+            k_eval_warp<DL32><<<sms * SBP_DECIDE_MIN_BLOCKS, kWarpsPerCta * 32, smem, st[1]>>>(a, 1, kWarpCap, 8, 32);
             SBP_LAUNCHED();
         }
     }

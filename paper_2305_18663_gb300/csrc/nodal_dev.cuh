@@ -175,23 +175,23 @@ __device__ __forceinline__ float log1p_atanh(float z) {
 // ln y for an integer count y >= 1 (exactly 0 at 1)
 __device__ __forceinline__ float ln_count(int y) { return y > 1 ? __logf((float)y) : 0.0f; }
 
+// Both forms, and both evaluations of ln(1 + z), are computed and the one
+// that applies is selected: no branches, so that the independent terms of a
+// move interleave and lanes with different counts do not diverge.
 __device__ __forceinline__ float dxlogx32(int x, int k, float &am) {
-    if (k == 0) return 0.0f;
     const int y = x + k;
-    const float xf = (float)x, yf = (float)y;
-    if (x == 0 || 2 * y < x) {
-        const float fy = yf * ln_count(y > 0 ? y : 1);
-        const float fx = xf * ln_count(x > 0 ? x : 1);
-        am += fabsf(fy) + fabsf(fx);
-        return fy - fx;
-    }
-    const float kf = (float)k;
-    const float t1 = kf * ln_count(y);
-    const float z = __fdividef(kf, xf);
-    const float l1 = fabsf(z) <= 0.5f ? log1p_atanh(z) : __logf(1.0f + z);
-    const float t2 = xf * l1;
-    am += fabsf(t1) + fabsf(t2);
-    return t1 + t2;
+    const float xf = (float)x, yf = (float)y, kf = (float)k;
+    const float ly = ln_count(y > 0 ? y : 1), lx = ln_count(x > 0 ? x : 1);
+    const float fy = yf * ly, fx = xf * lx;  // (x+k) ln(x+k) - x ln x
+    const float z = __fdividef(kf, x > 0 ? xf : 1.0f);
+    const bool series = fabsf(z) <= 0.5f;
+    const float la = log1p_atanh(series ? z : 0.0f), lb = __logf(1.0f + fmaxf(z, -0.5f));
+    const float t1 = kf * ly, t2 = xf * (series ? la : lb);  // k ln(x+k) + x ln(1 + k/x)
+    const bool direct = x == 0 || 2 * y < x;
+    const float val = direct ? fy - fx : t1 + t2;
+    const float mag = direct ? fabsf(fy) + fabsf(fx) : fabsf(t1) + fabsf(t2);
+    am += k != 0 ? mag : 0.0f;
+    return k != 0 ? val : 0.0f;
 }
 
 // bound on |Delta L (FP32) - Delta L| for a move of a degree-k vertex
@@ -277,11 +277,54 @@ __device__ __forceinline__ int special_terms32(const ModelDev &md, const VertexC
     return val;
 }
 
+
 // Hastings terms of v's neighbours in r and in s (forward and backward),
 // from the corner entries and the block degrees; FP32 and FP64 versions.
 struct CornerVals {
     int Mrr, Mss, Mrs, Msr, dr, ds;
 };
+
+// the four corner entries M[r][r], M[s][s], M[r][s], M[s][r]; on sparse rows
+// the two row offsets and then the four first probe slots are loaded
+// together (collisions continue one slot at a time)
+__device__ __forceinline__ void Mat4corner(const ModelDev &md, int r, int s, int &Mrr, int &Mss, int &Mrs, int &Msr) {
+    if (!md.sparse) {
+        const size_t B = (size_t)md.B;
+        Mrr = md.M[(size_t)r * B + r];
+        Mss = md.M[(size_t)s * B + s];
+        Mrs = md.M[(size_t)r * B + s];
+        Msr = md.M[(size_t)s * B + r];
+        return;
+    }
+    const uint32_t o_r = md.hoff[r], c_r = md.hoff[r + 1] - o_r;
+    const uint32_t o_s = md.hoff[s], c_s = md.hoff[s + 1] - o_s;
+    const uint32_t hr = sparse_hash(r), hs = sparse_hash(s);
+    const uint32_t h1 = hr & (c_r - 1), h2 = hs & (c_s - 1), h3 = hs & (c_r - 1), h4 = hr & (c_s - 1);
+    const int2 k1 = md.hkv[o_r + h1], k2 = md.hkv[o_s + h2], k3 = md.hkv[o_r + h3], k4 = md.hkv[o_s + h4];
+    Mrr = sparse_probe_from(md, o_r, c_r, h1, r, k1);
+    Mss = sparse_probe_from(md, o_s, c_s, h2, s, k2);
+    Mrs = sparse_probe_from(md, o_r, c_r, h3, s, k3);
+    Msr = sparse_probe_from(md, o_s, c_s, h4, r, k4);
+}
+
+// the eight corner and degree terms of one move on one lane (the lane per
+// mover of the batch kernels), all loads issued together and the terms
+// summed as a tree: returns the corner entries, adds to dl and am
+__device__ __forceinline__ CornerVals special_terms32_lane(const ModelDev &md, const VertexCtx &x, float &dl, float &am) {
+    const int r = x.r, s = x.s;
+    const int cr = x.ko_r + x.ki_r, cs = x.ko_s + x.ki_s;
+    CornerVals cv;
+    Mat4corner(md, r, s, cv.Mrr, cv.Mss, cv.Mrs, cv.Msr);
+    const int dor = md.dout[r], dos = md.dout[s], dir = md.din[r], dis = md.din[s];
+    cv.dr = md.dsum[r];
+    cv.ds = md.dsum[s];
+    const float c0 = dxlogx32(cv.Mrr, -(cr + x.self), am), c1 = dxlogx32(cv.Mss, cs + x.self, am);
+    const float c2 = dxlogx32(cv.Mrs, x.ki_r - x.ko_s, am), c3 = dxlogx32(cv.Msr, x.ko_r - x.ki_s, am);
+    const float d0 = dxlogx32(dor, -x.Kout, am), d1 = dxlogx32(dos, x.Kout, am);
+    const float d2 = dxlogx32(dir, -x.Kin, am), d3 = dxlogx32(dis, x.Kin, am);
+    dl += ((c0 + c1) + (c2 + c3)) - ((d0 + d1) + (d2 + d3));
+    return cv;
+}
 
 __device__ __forceinline__ void corner_hastings_fast(const VertexCtx &x, const CornerVals &c, int B, float &pf,
                                                      float &pb) {

@@ -17,7 +17,9 @@ def test_traffic_figure_only_for_its_form_and_code():
     # the committed figure belongs to the sparse-row form; the dense form has none
     assert bench.decide_traffic("dense") is None
     if t is not None:  # present exactly while the decide-pass code is unchanged
-        assert t["bytes"] > t["algorithmic_bytes"] > 0
+        # the pass must at least stream the movers' rows from DRAM, and the
+        # lookups it adds to the algorithmic bytes are served from L2
+        assert 0.9 * t["streamed_bytes"] <= t["bytes"] <= t["algorithmic_bytes"]
 
 
 def test_algorithmic_bytes_formula():
