@@ -546,6 +546,7 @@ def run_batch(args):
            "unit": "graphs/s", "n_gpus": 1, "higher_is_better": True, "impl": "ours",
            "plain": {"value": len(graphs) / t_plain, "unit": "graphs/s", "seconds": t_plain},
            "batched_seconds": t_batch, "speedup_vs_plain": t_plain / t_batch, "batch_stats": bstats.as_dict(),
+           "phases_batched_share": bstats.phases_batched / max(1, bstats.phases_batched + bstats.phases_per_graph),
            "autotune": tuned,
            "results_equal": mismatch == 0, "mismatches": mismatch,
            "completion_s": {"p50": float(np.percentile(done, 50)), "p99": float(np.percentile(done, 99))},
@@ -659,7 +660,8 @@ def main():
     ap.add_argument("--serve-n-hi", type=int, default=2_000_000)
     ap.add_argument("--serve-rates", default="2,20,200")
     ap.add_argument("--batch-total", type=int, default=4096, help="graphs of the batching workload")
-    ap.add_argument("--batch-count", type=int, default=256, help="graphs actually run (an evenly strided subset)")
+    ap.add_argument("--batch-count", type=int, default=4096,
+                    help="graphs actually run (all of them by default; fewer: an evenly strided subset)")
     ap.add_argument("--batch-workers", type=int, default=16)
     ap.add_argument("--autotune", type=int, default=32,
                     help="batch mode: graphs in the autotuner's sample (0: default options)")

@@ -365,7 +365,10 @@ int sbp_autotune_batch(const sbp_graph_t *const *graphs, int32_t count, const sb
  * sbp_server_create starts the engine (host worker threads and a launcher
  * thread); requests submitted while others run are admitted as their
  * memory fits (memory freed by finished requests admits the next), and
- * their work overlaps on the device with the others'.  Every request's
+ * their work overlaps on the device with the others'.  Free host workers
+ * take the oldest admitted request's next step first (a batch call takes
+ * the largest graph's), so requests finish close to arrival order.  Every
+ * request's
  * result equals sbp_partition of its graph alone.  A graph and its b_out
  * buffer (host or device, n labels, or NULL) must stay valid until the
  * request is done.  sbp_server_wait blocks until the request is done and

@@ -84,6 +84,11 @@ struct Engine {
     std::atomic<int64_t> per_graph_phases{0};
     std::vector<std::thread> workers;
     std::thread launcher;
+    // which queued graph a free worker takes: the largest (a batch call:
+    // the longest runs start first, which shortens the whole call) or the
+    // oldest request (the server: requests finish closer to arrival order,
+    // which keeps the median latency down when the device is saturated)
+    bool oldest_first = false;
 
     int init(const sbp_params &p, const BatchOptions &o, bool background);
     int64_t submit(const sbp_graph *g, int32_t *b_out);
@@ -113,6 +118,7 @@ void Engine::admit() {
 int Engine::init(const sbp_params &p, const BatchOptions &o, bool background) {
     prm = p;
     opt = o;
+    oldest_first = background;  // the server
     prm.dense_max_B = opt.tune.dense_max_B;
     W = std::max(1, opt.workers);
     t0 = now_s();
@@ -194,9 +200,11 @@ void Engine::worker() {
     for (;;) {
         cv.wait(lk, [&]() { return aborting || (closing && running == 0) || !cpu_q.empty(); });
         if (aborting || (cpu_q.empty() && closing && running == 0)) return;
-        size_t pick = 0;  // the largest graph first
-        for (size_t q = 1; q < cpu_q.size(); ++q)
-            if (items[(size_t)cpu_q[q]]->g->m > items[(size_t)cpu_q[pick]]->g->m) pick = q;
+        size_t pick = 0;
+        for (size_t q = 1; q < cpu_q.size(); ++q) {
+            const int64_t a = cpu_q[q], b = cpu_q[pick];
+            if (oldest_first ? a < b : items[(size_t)a]->g->m > items[(size_t)b]->g->m) pick = q;
+        }
         const int64_t idx = cpu_q[pick];
         cpu_q.erase(cpu_q.begin() + (long)pick);
         Item &it = *items[(size_t)idx];

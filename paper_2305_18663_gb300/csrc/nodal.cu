@@ -405,7 +405,11 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         __int128 dl = 0;
         double fb = 0.0;
         float pf = 0.0f, pb = 0.0f, dlf = 0.0f, am = 0.0f;
-        for (int e = tid; e < D; e += blockDim.x) {
+        // the FP32 pass only feeds the FP32 test; when the exact evaluation
+        // decides anyway (the recheck launch, a trace) it is skipped (the
+        // exact form's pass also yields the exact Delta L, so it stays)
+        const bool fast_pass = !DL32 || (!a.trace_on && !a.force_exact);
+        for (int e = tid; fast_pass && e < D; e += blockDim.x) {
             const int slot = list[e];
             const int t = keys[slot];
             const unsigned long long cc = cnt[slot];
@@ -416,7 +420,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
                     entry_fast(md, x, t, (int)(cc & 0xffffffffu), (int)(cc >> 32), dl, fb, pf, pb);
             }
         }
-        if (tid < 32) {
+        if (fast_pass && tid < 32) {
             if (DL32)
                 special_terms32(md, x, tid, dlf, am);
             else

@@ -105,9 +105,12 @@ def sharded_sweep(model, sweep_id: int, ranges: list[tuple[int, int]], group=Non
         raise ValueError("ranges must cover the graph")
     dev = torch.device("cuda", torch.cuda.current_device())
     sbp_nodal_decide(model.h, sweep_id, lo, hi)
-    mine = torch.empty(hi - lo, dtype=torch.int32, device=dev)
-    sbp_get_pending(model.h, lo, hi, mine)
+    # gloo gathers host tensors, NCCL device tensors
+    host = dist.get_backend(group) == "gloo"
+    mine = torch.empty(hi - lo, dtype=torch.int32, device="cpu" if host else dev)
+    sbp_get_pending(model.h, lo, hi, mine)  # synchronous: the labels are in place on return
     full = allgather_slices(mine, ranges, group)
-    torch.cuda.current_stream(dev).synchronize()  # the model may run on another stream
+    if not host:
+        torch.cuda.current_stream(dev).synchronize()  # the model may run on another stream
     sbp_set_pending(model.h, 0, n, full)
     return sbp_commit(model.h, stats=stats)

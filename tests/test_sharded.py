@@ -4,7 +4,10 @@ CPU: two gloo ranks, each deciding its dealt range with the oracle, exchange
 the new labels through `allgather_slices` and apply them; the result equals
 the single-rank sweeps bit for bit.  GPU: two model replicas on one device
 decide their ranges, trade them through sbp_get_pending / sbp_set_pending and
-commit; the result equals sbp_nodal_sweep over the whole graph."""
+commit; and two gloo ranks, each with its own replica on the same device, run
+`sharded_sweep` (decide, exchange on the host, commit).  Both equal
+sbp_nodal_sweep over the whole graph.  The ranks' kernels never wait on one
+another: the exchange is a host collective between whole sweeps."""
 
 import multiprocessing as mp
 import os
@@ -185,3 +188,63 @@ def test_three_gloo_ranks_gather_uneven_slices(tmp_path):
     want = np.arange(0, 20, dtype=np.int32) * 3 + 1
     for r in range(world):
         assert np.array_equal(np.load(tmp_path / f"g{r}.npy"), want)
+
+
+def _sharded_gpu_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2305_18663_gb300 as P
+    from paper_2305_18663_gb300.shard import sharded_sweep
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        P.load()
+        n, B, src, dst, b0, ranges = _relabelled(world)
+        m = P.Model(P.Graph(n, src, dst), B, b0, P.Params.default(seed=SEED, beta=BETA))
+        accepted = 0
+        for k in range(SWEEPS):
+            accepted += sharded_sweep(m, k, ranges, stats=True).n_accepted
+        np.save(os.path.join(out_dir, f"s{rank}.npy"), m.assignment())
+        np.save(os.path.join(out_dir, f"dl{rank}.npy"), np.array([m.dl(), accepted], np.float64))
+        m.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_sharded_sweep_two_gloo_ranks_on_one_gpu(tmp_path):
+    import torch
+
+    import paper_2305_18663_gb300 as P
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_sharded_gpu_main, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+    codes = [p.exitcode for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert codes == [0, 0], codes
+    n, B, src, dst, b0, _ = _relabelled(world)
+    ref = P.Model(P.Graph(n, src, dst), B, b0, P.Params.default(seed=SEED, beta=BETA))
+    accepted = 0
+    for k in range(SWEEPS):
+        accepted += P.sbp_nodal_sweep(ref.h, k, 0, n).n_accepted
+    assert accepted > 0
+    rank_accepted = 0
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / f"s{r}.npy"), ref.assignment())
+        dl, acc = np.load(tmp_path / f"dl{r}.npy")
+        assert dl == ref.dl()
+        rank_accepted += int(acc)  # each rank counts the moves of the range it decided
+    assert rank_accepted == accepted
+    ref.close()
