@@ -162,7 +162,12 @@ int sbp_build_blockmodel(const sbp_graph_t *g, int32_t B, const int32_t *b, cons
  * device) and rebuilds M and DL.  The labels are checked on the device
  * before they replace the current ones: on SBP_EINVAL (a label outside
  * [0, B), the smallest such vertex named in the message) the model keeps its
- * assignment.  Other errors as sbp_build_blockmodel. */
+ * assignment.  With the model's own B (after its first nodal pass, unless
+ * full_rebuild is set) the change is applied like the moves of a pass: the
+ * counts are updated from the changed vertices' rows when those hold at most
+ * a quarter of the edges, else recounted; either way M, the degrees and DL
+ * are those of a rebuild from scratch.  Discards pending decisions.  Other
+ * errors as sbp_build_blockmodel. */
 int sbp_set_assignment(sbp_model_t *m, int32_t B, const int32_t *b);
 
 /* One asynchronous-Gibbs nodal pass restricted to the vertices of

@@ -159,6 +159,84 @@ __global__ void k_check_labels(const int32_t *__restrict__ b, int64_t n, int32_t
         if (b[v] < 0 || b[v] >= B) atomicMax(slot, (int32_t)(INT32_MAX - v));
 }
 
+// Labels set from outside against the current ones, with the same block
+// count: the range check of k_check_labels, and every changed vertex listed
+// the way the decision kernels list an accepted move (its kMoveChunk-edge
+// items, its degree in acc_edges), so that the commit of a pass can apply
+// the change.  Counters and item slots are taken once per warp.
+__global__ void k_diff_labels(const int32_t *__restrict__ bnew, const int32_t *__restrict__ b, int64_t n, int32_t B,
+                              const int32_t *__restrict__ op, const int32_t *__restrict__ ip, int2 *__restrict__ items,
+                              int64_t cap, DevCounters *__restrict__ c, int32_t *__restrict__ slot) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        int k = 0, nch = 0;
+        if (v < n) {
+            const int32_t lab = bnew[v];
+            if (lab < 0 || lab >= B) {
+                atomicMax(slot, (int32_t)(INT32_MAX - v));
+            } else if (lab != b[v]) {
+                k = (op[v + 1] - op[v]) + (ip[v + 1] - ip[v]);
+                nch = (k + kMoveChunk - 1) / kMoveChunk;
+            }
+        }
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned wk = __reduce_add_sync(0xffffffffu, (unsigned)k);
+        unsigned long long first = 0;
+        if (lane == 0 && wtotal > 0) {
+            first = atomicAdd(&c->items, (unsigned long long)wtotal);
+            atomicAdd(&c->acc_edges, (unsigned long long)wk);
+        }
+        first = __shfl_sync(0xffffffffu, first, 0);
+        for (int q = 0; q < nch; ++q) {
+            const unsigned long long at = first + (unsigned long long)(incl - nch + q);
+            if (at < (unsigned long long)cap) items[at] = make_int2((int)v, q);
+        }
+    }
+}
+
+// Labels with the block count the model already has, once it has its
+// accepted-move list: the change against the current labels is applied like
+// the moves of a pass (the commit's plan, on the device, updates the counts
+// from the changed vertices' rows when they hold at most a quarter of the
+// edges, else recounts; the block-labelled rows follow the changed vertices).
+// Same counts and DL as a rebuild from scratch.
+int upload_incremental(sbp_model *m, const int32_t *b) {
+    const int64_t n = m->g->n;
+    int32_t *slot = m->status + 2;
+    SBP_CUDA(cudaMemcpyAsync(m->bnew, b, (size_t)n * 4, cudaMemcpyDefault, m->stream));
+    SBP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream));
+    SBP_CUDA(cudaMemsetAsync(slot, 0, 4, m->stream));
+    k_diff_labels<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, m->stream>>>(
+        m->bnew, m->b, n, m->B, m->g->op, m->g->ip, m->items, m->cap_items, m->counters, slot);
+    SBP_LAUNCHED();
+    int32_t *h = static_cast<int32_t *>(m->pinned);
+    SBP_CUDA(cudaMemcpyAsync(h, slot, 4, cudaMemcpyDeviceToHost, m->stream));
+    SBP_CUDA(cudaStreamSynchronize(m->stream));
+    if (*h > 0) {
+        SBP_CUDA(cudaMemcpyAsync(m->bnew, m->b, (size_t)n * 4, cudaMemcpyDeviceToDevice, m->stream));
+        SBP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream));
+        return fail(SBP_EINVAL, "label out of [0, B) at vertex " + std::to_string((int64_t)INT32_MAX - *h));
+    }
+    std::swap(m->b, m->bnew);
+    SBP_CUDA(cudaMemcpyAsync(m->dl + 1, m->dl, 8, cudaMemcpyDeviceToDevice, m->stream));
+    m->list_ok = true;  // the items list every change, once
+    m->decided.clear();
+    m->nb_in_commit = false;
+    int rc = commit_blockmodel(m);
+    if (rc == SBP_OK) rc = nb_rows_after_commit(m);
+    if (rc != SBP_OK) m->nb_ok = false;
+    SBP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), m->stream));
+    return rc;
+}
+
 // The labels go to the pending buffer, are checked on the device (one read
 // back), and only then become the assignment: a bad label leaves the model
 // as it was.
@@ -166,6 +244,7 @@ int upload_assignment(sbp_model *m, int32_t B, const int32_t *b) {
     const int64_t n = m->g->n;
     if (B < 1 || B > n) return fail(SBP_EINVAL, "B must be in [1, n]");
     if (!b) return fail(SBP_EINVAL, "assignment pointer is NULL");
+    if (B == m->B && m->items && !m->p.full_rebuild) return upload_incremental(m, b);
     int32_t *slot = m->status + 2;
     SBP_CUDA(cudaMemcpyAsync(m->bnew, b, (size_t)n * 4, cudaMemcpyDefault, m->stream));
     SBP_CUDA(cudaMemsetAsync(slot, 0, 4, m->stream));

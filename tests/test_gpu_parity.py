@@ -651,3 +651,55 @@ def test_untraced_fp32_sweeps_below_fork_size_match_oracle(m_form):
     b0 = perturb(g.planted, 316, 0.3, seed=0)
     untraced_sweeps_vs_oracle(g, 316, b0, P.Graph(g.n, g.src, g.dst), O.Graph(g.n, g.src, g.dst), m_form,
                               sweeps=5, min_moves=10_000)
+
+
+@pytest.mark.parametrize("dmax", [4096, 1])
+def test_set_assignment_of_a_nearby_state_equals_a_rebuild(dmax):
+    # labels set with the model's block count are applied like a pass's
+    # moves (incremental counts for a few changes, a recount for many); the
+    # result must be the model built from those labels from scratch, and the
+    # block-labelled rows must follow (later sweeps agree)
+    g = make_config("dcsbm_1m", seed=0, scale=0.05)
+    B = 316
+    b0 = perturb(g.planted, B, 0.3, seed=0)
+    pg = P.Graph(g.n, g.src, g.dst)
+    prm = P.Params.default(seed=5, dense_max_B=dmax)
+    pm = P.Model(pg, B, b0, prm)
+    for sw in range(2):
+        pm.sweep(sw)
+    rng = np.random.default_rng(1)
+    cur = pm.assignment()
+    G = O.Graph(g.n, g.src, g.dst)
+    for step, frac in enumerate((0.001, 0.02, 0.6)):
+        x = cur.copy()
+        idx = rng.choice(g.n, int(frac * g.n), replace=False)
+        x[idx] = rng.integers(0, B, idx.size).astype(np.int32)
+        if step == 1:
+            P.sbp_set_assignment(pm.h, B, torch.from_numpy(x).cuda())  # device input
+        else:
+            P.sbp_set_assignment(pm.h, B, x)
+        fresh = P.Model(pg, B, x, prm)
+        assert np.array_equal(pm.assignment(), x)
+        k1, c1 = pm.coo()
+        k2, c2 = fresh.coo()
+        assert np.array_equal(k1, k2) and np.array_equal(c1, c2)
+        assert np.array_equal(pm.degrees()[0], fresh.degrees()[0]) and np.array_equal(pm.degrees()[1], fresh.degrees()[1])
+        assert pm.dl() == fresh.dl()
+        if step == 0:
+            check_blockmodel(pm, O.Model(G, B, x))
+        for sw in (10 + 2 * step, 11 + 2 * step):
+            pm.sweep(sw)
+            fresh.sweep(sw)
+            assert np.array_equal(pm.assignment(), fresh.assignment())
+            assert np.array_equal(pm.coo()[1], fresh.coo()[1]) and pm.dl() == fresh.dl()
+        fresh.close()
+        cur = pm.assignment()
+    # a label out of range is refused and leaves the model as it was
+    bad = cur.copy()
+    bad[7] = B
+    dl = pm.dl()
+    with pytest.raises(P.SbpError):
+        P.sbp_set_assignment(pm.h, B, bad)
+    assert np.array_equal(pm.assignment(), cur) and pm.dl() == dl
+    check_blockmodel(pm, O.Model(G, B, cur))
+    pm.close()
