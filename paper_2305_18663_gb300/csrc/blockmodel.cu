@@ -1,15 +1,19 @@
-// blockmodel.cu -- rebuild of the blockmodel from the assignment.
+// blockmodel.cu -- the blockmodel from the assignment, and its update after
+// a pass.
 //
 // Section II-A: M[r][s] counts the edges from block r to block s; the block
 // degrees are its row and column sums.  Alg. 5: after every pass the moves
-// are applied and the blockmodel is made consistent again -- here by a full
-// recount from the new assignment, so the result is exact by construction.
+// are applied and the blockmodel is made consistent again: each edge with a
+// moved end leaves its old (block, block) cell and enters the new one when
+// the moved rows hold at most a quarter of the edges (a plan taken on the
+// device), else M is recounted from the new assignment.  Both give the same
+// integers.  The same kernels keep the block-labelled rows in step.
 //
-// Dense form (B <= dense_max_B): M is B x B int32, counted by a
-// warp-aggregated atomic histogram over the out-edges.  P holds, per block
-// u, the inclusive prefix of row u followed by dout_u plus the inclusive
-// prefix of column u; the nodal and merge proposals search it.  DL (Eq. 2)
-// is reduced in a fixed order so it is reproducible bit for bit.
+// Dense form (B <= dense_max_B): M is B x B int32, counted by an atomic
+// histogram over the out-edges with the diagonal privatised per CTA.  P
+// holds, per block u, the inclusive prefix of row u followed by dout_u plus
+// the inclusive prefix of column u; the nodal and merge proposals search it.
+// DL (Eq. 2) is reduced in a fixed order so it is reproducible bit for bit.
 #include <cmath>
 
 #include "apply.cuh"

@@ -1,13 +1,19 @@
 // nodal.cu -- the asynchronous-Gibbs nodal decision pass of one graph.
 //
-// Kernels: k_propose (one lane per vertex) draws every proposal and sends
-// those with s != r to three lists by degree; k_eval_batch (32 movers per
-// warp, k <= 32, and k <= 128 with direct-mapped counts while B is small),
-// k_eval_warp (one warp per mover with a shared-memory table) and k_eval_cta
-// (one CTA per mover, very large tables) aggregate the rows of the movers
-// only and run the test.  The decision goes to the pending assignment; M is
-// untouched until commit.  The steps and their numerics are described in
-// nodal_dev.cuh.
+// Vertices are split by total degree into three groups (k <= 32, 33..128,
+// above 128), each with its own evaluation kernel: k_eval_batch (32 movers
+// per warp; for 33..128 with direct-mapped counts while B is small),
+// k_eval_warp_direct (one warp per mover, direct-mapped counts) or, at
+// larger B, k_eval_warp (one warp per mover with a shared-memory table) and
+// k_eval_cta (one CTA per mover, very large tables).  In a pass over all
+// vertices without a trace the first two kinds draw the proposals of their
+// group's vertices themselves; otherwise k_propose (one lane per vertex)
+// draws every proposal first and hands the moving ones (s != r) over in
+// lists by group.  Only movers' rows are aggregated.  Moves the FP32 test
+// cannot settle are decided after the pass by the exact evaluation
+// (k_eval_cta in recheck mode).  The decision goes to the pending
+// assignment; M is untouched until commit.  The steps and their numerics
+// are described in nodal_dev.cuh.
 #include <algorithm>
 #include <cmath>
 
@@ -445,10 +451,7 @@ __global__ void __launch_bounds__(kBigThreads) k_eval_cta(DecideArgs a, int bin,
         }
         __syncthreads();
         CornerVals cv;
-        cv.Mrr = Mat(md, r, r);
-        cv.Mss = Mat(md, s, s);
-        cv.Mrs = Mat(md, r, s);
-        cv.Msr = Mat(md, s, r);
+        Mat4corner(md, r, s, cv.Mrr, cv.Mss, cv.Mrs, cv.Msr);
         cv.dr = md.dsum[r];
         cv.ds = md.dsum[s];
         if (tid == 0) {

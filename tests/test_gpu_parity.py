@@ -703,3 +703,29 @@ def test_set_assignment_of_a_nearby_state_equals_a_rebuild(dmax):
     assert np.array_equal(pm.assignment(), cur) and pm.dl() == dl
     check_blockmodel(pm, O.Model(G, B, cur))
     pm.close()
+
+
+def _loops_dups_isolated_graph():
+    # self-loops, duplicate edges, 20 isolated vertices and a hub of ~400
+    # edges (the group above 128 edges), as in the traced test above
+    rng = np.random.default_rng(11)
+    n = 300
+    src = rng.integers(0, n - 20, 3000).astype(np.int32)
+    dst = rng.integers(0, n - 20, 3000).astype(np.int32)
+    src[:200] = dst[:200]
+    src[200:400] = src[400:600]
+    dst[200:400] = dst[400:600]
+    hub = 5
+    src = np.concatenate([src, np.full(400, hub, np.int32), np.full(3, hub, np.int32)])
+    dst = np.concatenate([dst, rng.integers(0, n - 20, 400).astype(np.int32), np.full(3, hub, np.int32)])
+    return _G(n, src, dst)
+
+
+@pytest.mark.parametrize("m_form", ["dense", "sparse"])
+def test_untraced_sweeps_self_loops_duplicates_isolated(m_form):
+    # the kernels that draw their own proposals (full-range pass, no trace)
+    # on self-loops, duplicates, isolated vertices and a hub, against the
+    # oracle sweep by sweep
+    g = _loops_dups_isolated_graph()
+    untraced_sweeps_vs_oracle(g, 12, random_labels(g.n, 12, seed=1), P.Graph(g.n, g.src, g.dst),
+                              O.Graph(g.n, g.src, g.dst), m_form, sweeps=8, seed=3, min_moves=50)
