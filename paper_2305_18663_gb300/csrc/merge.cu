@@ -1,6 +1,6 @@
 // merge.cu -- block-merge proposals and merge Delta DL (Alg. 1, Alg. 4).
 //
-// One warp per block r runs the x proposals of r in order.  Proposal i
+// One warp per block r; its lanes draw up to 32 proposals of r at once.  Proposal i
 // (Philox counter (round_id, r, i), key (seed, 1)): u is the block at the
 // far end of a uniformly chosen edge of block r (row r then column r of M);
 // s != r is drawn with probability proportional to 1 + M[u][s] + M[s][u]
@@ -21,7 +21,9 @@
 namespace sbp {
 namespace {
 
-__device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1) {
+// Proposal of block r on one lane (every search a single-lane one, so the
+// lanes of a warp can draw different proposals of r at once).
+__device__ __forceinline__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1) {
     const int B = md.B;
     const int64_t dr = (int64_t)md.dout[r] + md.din[r];
     if (dr == 0) {
@@ -33,7 +35,7 @@ __device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1
     if (md.sparse) {
         u = sparse_cdf_block(md, r, (uint32_t)t0, (uint32_t)md.dout[r]);
     } else {
-        u = warp_cdf_search(md.P + (size_t)r * 2 * B, md.Pc + (size_t)r * 32, 2 * B, md.pstep, (uint32_t)t0);
+        u = (int)pivot_upper(md.P + (size_t)r * 2 * B, md.Pc + (size_t)r * 32, 0, 2 * B, (uint32_t)t0);
         if (u >= B) u -= B;
     }
     const int64_t Mur = Mat(md, u, r), Mru = Mat(md, r, u);
@@ -64,16 +66,33 @@ __device__ int merge_propose(const ModelDev &md, int r, uint64_t w0, uint64_t w1
         // row u with column r left out
         const int64_t pre = r > 0 ? (int64_t)Pu[r - 1] : 0;
         const int64_t tt = t >= pre ? t + Mur : t;
-        return warp_upper_bound(Pu, B, (uint32_t)tt);
+        return (int)lane_upper(Pu, 0, (uint32_t)B, (uint32_t)tt);
     }
     // column u with row r left out; Pu[B + c] = dout_u + column prefix
     const int64_t pre = r > 0 ? (int64_t)Pu[B + r - 1] : du_out;
     int64_t target = du_out + (t - row_w);
     if (target >= pre) target += Mru;
-    return warp_upper_bound(Pu + B, B, (uint32_t)target);
+    return (int)lane_upper(Pu + B, 0, (uint32_t)B, (uint32_t)target);
 }
 
-__device__ double merge_delta(const ModelDev &md, int r, int s) {
+// The terms of merging r into s that do not come from row or column r's
+// other entries, on one lane: the 2x2 corner collapsing into M[s][s]
+// (added) and the block degrees of s absorbing those of r (subtracted).
+struct MergeCorner {
+    double add, sub;
+};
+
+__device__ __forceinline__ MergeCorner merge_corner(const ModelDev &md, int r, int s) {
+    const int64_t a = Mat(md, r, r), b = Mat(md, r, s), c = Mat(md, s, r), d = Mat(md, s, s);
+    MergeCorner m;
+    m.add = gmerge(a, b) + gmerge(a + b, c) + gmerge(a + b + c, d);
+    m.sub = gmerge(md.dout[s], md.dout[r]) + gmerge(md.din[s], md.din[r]);
+    return m;
+}
+
+// the entries of row r and column r other than r and s, merged into row and
+// column s: the whole warp, one sum per lane then the warp total
+__device__ __forceinline__ double merge_entries(const ModelDev &md, int r, int s) {
     const int B = md.B, lane = threadIdx.x & 31;
     double acc = 0.0;
     if (md.sparse) {
@@ -96,15 +115,17 @@ __device__ double merge_delta(const ModelDev &md, int r, int s) {
             if (Mtr) acc += gmerge(Mat(md, t, s), Mtr);
         }
     }
-    acc = warp_sum(acc);
-    const int64_t a = Mat(md, r, r), b = Mat(md, r, s), c = Mat(md, s, r), d = Mat(md, s, s);
-    acc += gmerge(a, b) + gmerge(a + b, c) + gmerge(a + b + c, d);
-    acc -= gmerge(md.dout[s], md.dout[r]) + gmerge(md.din[s], md.din[r]);
-    return -acc;
+    return warp_sum(acc);
 }
 
 __device__ __forceinline__ long long score_key(double d) { return (long long)floor(d * 1048576.0 + 0.5); }
 
+// One warp per block r.  Up to 32 proposals at a time, one per lane: each
+// lane draws its proposal s_i and computes its corner and degree terms, so
+// the proposals' dependent lookups and FP64 terms overlap; then the warp
+// sums the row and column entries of each proposal in turn.  Delta DL of
+// proposal i: -((entries + corner) - degrees), the best being the smallest
+// score on the grid, the earliest i on a tie.
 __global__ void __launch_bounds__(256) k_merge_proposals(ModelDev md, uint64_t seed, uint64_t round_id, int x,
                                                          int32_t *__restrict__ best_s, double *__restrict__ best_d) {
     const int lane = threadIdx.x & 31;
@@ -113,15 +134,27 @@ __global__ void __launch_bounds__(256) k_merge_proposals(ModelDev md, uint64_t s
         int bs = -1;
         double bd = 0.0;
         long long bk = 0;
-        for (int i = 0; i < x; ++i) {
-            const U64x4 w = philox4x64_10(round_id, (uint64_t)r, (uint64_t)i, 0, seed, 1);
-            const int s = merge_propose(md, r, w.x, w.y);
-            const double d = merge_delta(md, r, s);
-            const long long key = score_key(d);
-            if (bs < 0 || key < bk) {
-                bs = s;
-                bd = d;
-                bk = key;
+        for (int i0 = 0; i0 < x; i0 += 32) {
+            const int nq = x - i0 < 32 ? x - i0 : 32;
+            int si = 0;
+            MergeCorner ci{0.0, 0.0};
+            if (lane < nq) {
+                const U64x4 w = philox4x64_10(round_id, (uint64_t)r, (uint64_t)(i0 + lane), 0, seed, 1);
+                si = merge_propose(md, r, w.x, w.y);
+                ci = merge_corner(md, r, si);
+            }
+            for (int q = 0; q < nq; ++q) {
+                const int s = __shfl_sync(0xffffffffu, si, q);
+                double acc = merge_entries(md, r, s);
+                acc += __shfl_sync(0xffffffffu, ci.add, q);
+                acc -= __shfl_sync(0xffffffffu, ci.sub, q);
+                const double d = -acc;
+                const long long key = score_key(d);
+                if (bs < 0 || key < bk) {
+                    bs = s;
+                    bd = d;
+                    bk = key;
+                }
             }
         }
         if (lane == 0) {

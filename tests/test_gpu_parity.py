@@ -518,6 +518,22 @@ def test_partition_sparse_start_dcsbm_5k_matches_oracle():
     assert ns == ons
 
 
+@pytest.mark.slow
+def test_partition_plain_200k_matches_oracle():
+    # the full run (golden-ratio search from B = N = 200,000, sparse rows
+    # above 4096 blocks) of the 200k-vertex / 4M-edge configuration: the
+    # same B, assignment, sweep count and DL as the oracle's run
+    g = make_config("plain_200k")
+    G = O.Graph(g.n, g.src, g.dst)
+    ob, oB, odl, ons = O.partition(G, O.Params(), nthreads=NT)
+    pg = P.Graph(g.n, g.src, g.dst)
+    b, B, dl, ns = pg.partition(P.Params.default())
+    assert B == oB
+    assert ns == ons
+    assert dl == pytest.approx(odl, rel=1e-12)
+    assert np.array_equal(b, ob)
+
+
 @pytest.mark.parametrize("dmax", [4096, 1])
 def test_incremental_commit_equals_full_rebuild(dmax):
     # the apply step updates the counts (dense M, or the cell counts of the
@@ -729,3 +745,24 @@ def test_untraced_sweeps_self_loops_duplicates_isolated(m_form):
     g = _loops_dups_isolated_graph()
     untraced_sweeps_vs_oracle(g, 12, random_labels(g.n, 12, seed=1), P.Graph(g.n, g.src, g.dst),
                               O.Graph(g.n, g.src, g.dst), m_form, sweeps=8, seed=3, min_moves=50)
+
+
+@pytest.mark.parametrize("case", ["hubs_B3000", "hub_table_global_B9500"])
+def test_untraced_sweeps_large_B_table_kernels(case):
+    # B above the direct-mapped limit: k_propose hands the movers to the
+    # hash-table kernels (k_eval_warp, and k_eval_cta for the hubs, its
+    # table in global memory at B = 9500), FP32 terms without a trace,
+    # against the oracle sweep by sweep
+    if case == "hubs_B3000":
+        g, B = _hub_graph(), 3000
+    else:
+        rng = np.random.default_rng(23)
+        n = 30000
+        src = rng.integers(0, n, 60000)
+        dst = rng.integers(0, n, 60000)
+        hub = 11
+        src = np.concatenate([src, np.full(9000, hub), rng.integers(0, n, 9000)])
+        dst = np.concatenate([dst, rng.integers(0, n, 9000), np.full(9000, hub)])
+        g, B = _G(n, src, dst), 9500
+    untraced_sweeps_vs_oracle(g, B, random_labels(g.n, B, seed=2), P.Graph(g.n, g.src, g.dst),
+                              O.Graph(g.n, g.src, g.dst), "dense", sweeps=3, seed=4, min_moves=100)
