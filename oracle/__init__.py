@@ -7,9 +7,10 @@ C compiler into ``oracle/_build/``.
 
 Parity status per step (details in ``sbp_oracle.c``): the blockmodel and
 description length (Eq. 1-2), Philox, the nodal proposal / Delta DL /
-Hastings, the merge Delta DL and the merge application are pinned by the
-tests; the driver's constants are readings and are pinned only through
-determinism and a unimodal-search check.
+Hastings and the acceptance draw, the merge Delta DL and the merge
+application (with its further rounds), the MCMC stop rule and the phase
+sequence of a full run are pinned by the tests; the driver's constants are
+readings of the paper, not values it gives.
 """
 from __future__ import annotations
 

@@ -13,10 +13,13 @@
  * oracle and the CUDA path follow the same readings.
  *
  * Parity status: P1 (blockmodel, Eq. 1-2), P2 (Philox), P3-P5 (proposal,
- * move Delta-DL, Hastings), P7 (merge Delta-DL) and P8 (merge application)
- * are pinned by the tests against brute force, closed forms and numpy.
- * P9 (driver constants) is pinned only through determinism and a unimodal
- * search check; its constants are readings, not values from the paper.
+ * move Delta-DL, Hastings, and the acceptance draw re-derived from numpy's
+ * Philox words), P7 (merge Delta-DL) and P8 (merge application, including
+ * its further proposal rounds) are pinned by the tests against brute force,
+ * closed forms and numpy.  P9: the MCMC stop rule is pinned against DL
+ * histories recomputed by numpy, and the phase sequence of a full run
+ * against the bracket rule alone (itself pinned on unimodal curves); the
+ * driver's constants are readings, not values from the paper.
  */
 #include <math.h>
 #include <stdint.h>
