@@ -525,7 +525,7 @@ def run_batch(args):
     raw = gen_graphs(chosen)
     t_gen = time.perf_counter() - t0
     graphs = [P.Graph(n, src, dst) for n, src, dst in raw]
-    opts = P.BatchOptions.default(workers=args.batch_workers)
+    opts = P.BatchOptions.default(**{"workers": args.batch_workers, **json.loads(args.options)})
     tuned = None
     if args.autotune > 0:
         # the autotuner on a sample of the same graphs, before the timed call
@@ -560,7 +560,7 @@ def run_batch(args):
            "config": {"workload": f"{len(graphs)} of {args.batch_total} directed DCSBM graphs (every {stride}th), "
                                   "N log-uniform [500, 50000], mean out-degree uniform [8, 32], "
                                   "planted B = round(sqrt(N)/2), degree exponent 2.5 on [1, 100], intra:inter 4:1",
-                      "graphs": len(graphs), "vertices": nv, "edges": ne, "workers": args.batch_workers,
+                      "graphs": len(graphs), "vertices": nv, "edges": ne, "workers": opts.workers,
                       "max_B": opts.max_B, "max_n": opts.max_n, "dense_max_B": opts.dense_max_B,
                       "generation_s": t_gen}}
     print(json.dumps(res))
@@ -600,7 +600,7 @@ def run_serve(args):
     for rate in rates:
         gaps = rng.exponential(1.0 / rate, len(graphs))
         arrive = np.cumsum(gaps) - gaps[0]
-        srv = P.Server(params, P.BatchOptions.default())
+        srv = P.Server(params, P.BatchOptions.default(**json.loads(args.options)))
         rids = [None] * len(graphs)
         base = time.perf_counter()
 
@@ -668,8 +668,10 @@ def main():
     ap.add_argument("--batch-total", type=int, default=4096, help="graphs of the batching workload")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="graphs actually run (all of them by default; fewer: an evenly strided subset)")
-    ap.add_argument("--batch-workers", type=int, default=16)
-    ap.add_argument("--autotune", type=int, default=32,
+    ap.add_argument("--batch-workers", type=int, default=32)
+    ap.add_argument("--options", default="{}",
+                    help="batch and serve modes: batch options over the defaults, as JSON (e.g. '{\"max_n\": 4096}')")
+    ap.add_argument("--autotune", type=int, default=0,
                     help="batch mode: graphs in the autotuner's sample (0: default options)")
     ap.add_argument("--m-form", default="sparse", choices=["dense", "sparse", "auto"],
                     help="sparse: hashed sparse rows at every B (the M form of the 1M-vertex precision "

@@ -284,17 +284,20 @@ int sbp_philox_check(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_
  *
  * Every graph runs the same golden-ratio search as sbp_partition (Section
  * II-B; Alg. 1, 2) and ends with the same assignment, B, DL and sweep count.
- * MCMC phases at B <= max_B run in persistent launches over all waiting
- * graphs (a CTA per graph phase, sweeps and the convergence test on the
- * device), overlapped with the per-graph work (merge phases, larger-B
- * phases) that `workers` host threads drive on their graphs' streams.  Graphs are admitted in input order while their
- * estimated device memory fits mem_fraction of the free memory, and each
- * model is freed when its graph finishes.
+ * A graph whose next phase starts at B <= 1024 on a dense model and merges
+ * to B <= max_B hands its search to a persistent launch over all waiting
+ * graphs: a CTA runs that graph's phases (start state, merge rounds, sweeps
+ * with the convergence test, compaction, bracket update) until the search
+ * ends or a phase is out of those bounds.  This overlaps with the
+ * per-graph work (set-up, larger-B phases) that `workers` host threads
+ * drive on their graphs' streams.  Graphs are admitted in input order
+ * while their estimated device memory fits mem_fraction of the free
+ * memory, and each model is freed when its graph finishes.
  *
- * workers: host threads (1..256); max_B: largest B of a batched MCMC phase
- * (1..1024); max_n: largest graph (vertices) whose phases are batched (a CTA
- * takes a whole phase, so big graphs are better served by the per-graph
- * kernels); dense_max_B: dense/sparse switch of the batch's models
+ * workers: host threads (1..256); max_B: largest B a batched phase merges
+ * to (1..1024); max_n: largest graph (vertices) whose searches are batched
+ * (a CTA runs a whole search, so the biggest graphs can be better served by
+ * the per-graph kernels); dense_max_B: dense/sparse switch of the batch's models
  * (max_B..16384); ctas_per_sm: persistent CTAs per SM (1..8);
  * movers_per_warp: movers a warp of the persistent kernel evaluates at once
  * (1, 2 or 4: 32, 16 or 8 lanes each; fewer when their per-mover count rows
@@ -327,7 +330,10 @@ typedef struct sbp_batch_result {
  * s_per_graph: worker-seconds of per-graph work (summed over the workers),
  * of which s_merge in set-up, merge phases and compaction and s_sweeps in
  * per-graph MCMC sweeps; s_batched: wall seconds of the persistent launches;
- * MCMC phases run batched and per graph. */
+ * phases_batched: phases run in the persistent launches, of which
+ * merges_batched with their merge phase (the others had theirs run per
+ * graph) and starts_batched from a search state the model no longer held;
+ * phases_per_graph: MCMC phases run per graph. */
 typedef struct sbp_batch_stats {
     int64_t rounds;
     double s_per_graph;
@@ -336,10 +342,12 @@ typedef struct sbp_batch_stats {
     int64_t phases_per_graph;
     double s_merge;
     double s_sweeps;
+    int64_t merges_batched;
+    int64_t starts_batched;
 } sbp_batch_stats;
 
-/* Fills o with the defaults: 16 workers, max_B 512, max_n 4096, dense_max_B
- * 4096, 2 CTAs per SM, 2 movers per warp, mem_fraction 0.5. */
+/* Fills o with the defaults: 32 workers, max_B 512, max_n 65536, dense_max_B
+ * 1024, 2 CTAs per SM, 2 movers per warp, mem_fraction 0.5. */
 int sbp_default_batch_options(sbp_batch_options *o);
 
 /* Partitions graphs[0..count).  p: NULL for the defaults (shared by every
@@ -355,11 +363,14 @@ int sbp_partition_batch(const sbp_graph_t *const *graphs, int32_t count, const s
  * graphs (`sample` of them, evenly spaced in size order; all when sample <= 0
  * or >= count) under candidate options and returns the fastest in *best.
  * The search starts from *best when `start` is nonzero (else from the
- * defaults) and tunes one option at a time, in this order: workers {8, 16,
- * 32}, movers_per_warp {1, 2, 4}, ctas_per_sm {1, 2, 3, 4}, max_B {128, 256,
+ * defaults) and tunes one option at a time, in this order:
+ * movers_per_warp {1, 2, 4}, ctas_per_sm {1, 2, 3, 4}, max_B {128, 256,
  * 512, 1024}, max_n {1024, 4096, 16384, 65536}, dense_max_B {1024, 4096};
- * mem_fraction is kept.  *graphs_per_s (may be NULL) receives the best
- * rate on the sample, *trials (may be NULL) the number of timed runs.
+ * workers (the caller's host threads) and mem_fraction are kept.  A
+ * sample runs far from the full batch's load (its host workers are mostly
+ * idle), so options that favour per-graph work can win on it and lose on
+ * the whole batch.  *graphs_per_s (may be NULL) receives the best rate on
+ * the sample, *trials (may be NULL) the number of timed runs.
  * Every run must give the same B and DL for every graph; SBP_ESTATE
  * otherwise.  p: NULL for the defaults. */
 int sbp_autotune_batch(const sbp_graph_t *const *graphs, int32_t count, const sbp_params *p, int32_t sample,

@@ -125,6 +125,8 @@ class BatchStats(C.Structure):
         ("phases_per_graph", C.c_int64),
         ("s_merge", C.c_double),
         ("s_sweeps", C.c_double),
+        ("merges_batched", C.c_int64),
+        ("starts_batched", C.c_int64),
     ]
 
     def as_dict(self) -> dict:

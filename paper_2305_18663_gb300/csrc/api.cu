@@ -576,16 +576,20 @@ int PartitionRun::begin(sbp_model *model) {
     SBP_TRY(read_assignment(m, init.b));
     model_holds = init.id;
     br.insert(std::move(init));
-    return next_phase();
+    plan();
+    return SBP_OK;
 }
 
-int PartitionRun::next_phase() {
-    int start;
-    int32_t target;
+void PartitionRun::plan() {
     if (!br.next(m->p.reduction, start, target)) {
         done = true;
-        return SBP_OK;
+        return;
     }
+    t = br.s[2].B == 0 ? m->p.t_pre : m->p.t_post;
+    k = 0;
+}
+
+int PartitionRun::start_phase() {
     const State &from = br.s[start];
     // the model already holds that state (labels, counts, DL) when it is the
     // one the last phase ended in; uploading it again would rebuild the same
@@ -594,7 +598,6 @@ int PartitionRun::next_phase() {
     int32_t Bm = m->B, rounds = 0;
     SBP_TRY(sbp_merge_blocks(m, round_id, from.B - target, &Bm, &rounds));
     round_id += (uint64_t)rounds;
-    t = br.s[2].B == 0 ? m->p.t_pre : m->p.t_post;
     SBP_TRY(read_dl(m, hist[0]));
     k = 0;
     return SBP_OK;
@@ -613,13 +616,6 @@ int PartitionRun::sweep() {
     return SBP_OK;
 }
 
-int PartitionRun::after_sweeps(int k_done, double dl_last) {
-    sweep_id += (uint64_t)k_done;
-    k = k_done;
-    if (k > 0) hist[(size_t)k] = dl_last;
-    return SBP_OK;
-}
-
 int PartitionRun::end_phase() {
     total += k;
     int32_t Bc = m->B;
@@ -631,7 +627,53 @@ int PartitionRun::end_phase() {
     SBP_TRY(read_assignment(m, x.b));
     model_holds = x.id;
     br.insert(std::move(x));
-    return next_phase();
+    plan();
+    return SBP_OK;
+}
+
+void PartitionRun::export_search(SearchRec &rec, int32_t *slots, bool started) const {
+    const size_t n = (size_t)m->g->n;
+    for (int p = 0; p < 3; ++p) {
+        const State &x = br.s[p];
+        rec.s[p].B = x.B;
+        rec.s[p].slot = p;
+        rec.s[p].dl = x.dl;
+        rec.s[p].id = x.id;
+        if (x.B != 0) std::memcpy(slots + (size_t)p * n, x.b.data(), n * 4);
+    }
+    rec.sweep_id = sweep_id;
+    rec.round_id = round_id;
+    rec.last_id = last_id;
+    rec.holds = model_holds;
+    rec.total = total;
+    rec.started = started ? 1 : 0;
+    rec.B_model = m->B;
+    rec.done = rec.phases = rec.merged = rec.starts = rec.ok = 0;
+}
+
+void PartitionRun::import_search(const SearchRec &rec, const int32_t *slots) {
+    const size_t n = (size_t)m->g->n;
+    for (int p = 0; p < 3; ++p) {
+        State &x = br.s[p];
+        x.B = rec.s[p].B;
+        x.dl = rec.s[p].dl;
+        x.id = rec.s[p].id;
+        if (x.B != 0) x.b.assign(slots + (size_t)rec.s[p].slot * n, slots + (size_t)rec.s[p].slot * n + n);
+        else x.b.clear();
+    }
+    sweep_id = rec.sweep_id;
+    round_id = rec.round_id;
+    last_id = rec.last_id;
+    model_holds = rec.holds;
+    total = rec.total;
+    // the model's host-side view of what the kernel left: B, and the
+    // derived state a rebuild resets
+    m->B = rec.B_model;
+    m->nb_ok = false;
+    m->list_ok = true;
+    m->decided.clear();
+    if (rec.done) done = true;
+    else plan();
 }
 
 int PartitionRun::finish(int32_t *b_out, int32_t *B_out, double *dl_out, int64_t *n_sweeps) const {
@@ -651,6 +693,7 @@ int run_partition(sbp_model *m, int32_t *b_out, int32_t *B_out, double *dl_out, 
     PartitionRun r;
     SBP_TRY(r.begin(m));
     while (!r.done) {
+        SBP_TRY(r.start_phase());
         while (!r.phase_over()) SBP_TRY(r.sweep());
         SBP_TRY(r.end_phase());
     }

@@ -4,16 +4,28 @@
 // Alg. 1 merge phases, Alg. 2 MCMC phases), with the same result as
 // sbp_partition.  Graphs can be submitted at any time.  Two kinds of work
 // overlap on the device:
-//   - per-graph work, driven by host worker threads: model set-up, merge
-//     phases, compaction, and the MCMC phases the persistent kernel does not
-//     take (B above its limit, big graphs, sparse rows).  Workers take graphs
-//     from a shared queue, largest first; a graph's work goes to its model's
-//     stream;
-//   - persistent launches (batch.cu), driven by the launcher: every graph whose
-//     next MCMC phase is batchable waits until a GPU's worth is ready or the
-//     workers have nothing else to do; up to four launches are in flight on
-//     their own streams, each completing by event, with results in host-mapped
-//     memory; their graphs then go back to the workers.
+//   - per-graph work, driven by host worker threads: model set-up, and the
+//     phases the persistent kernel does not take (merges from B above its
+//     limit, big graphs, sparse rows), each with its merges, sweeps and
+//     compaction on the per-graph kernels.  Workers take graphs from a
+//     shared queue: first the short steps (a finished search's result, the
+//     set-up of a graph whose search the persistent kernel will take), then
+//     the largest (the server: the oldest); a graph's work goes to its
+//     model's stream;
+//   - persistent launches (batch.cu), driven by the launcher: a graph whose
+//     next phase the kernel can run whole (start state, merges, sweeps,
+//     compaction) hands it its search from that phase on, as does a graph
+//     whose merges ran per graph and whose sweeps it can run.  The kernel
+//     runs the search's phases and bracket updates until the search ends or
+//     a phase is out of its bounds.  A launch starts when a GPU's worth of
+//     searches is ready, when the workers have nothing else to do, or 2 ms
+//     after the oldest ready search joined; up to 16 are in flight on their
+//     own streams, with the searches in host-mapped memory.  A search that
+//     ends is taken back as soon as its record says so (a launch can hold
+//     searches of very different lengths); one whose next phase is out of
+//     the kernel's bounds once its launch is over (its model's device state
+//     is then complete for the per-graph kernels).  Either goes back to the
+//     workers.
 // Admission: graphs are admitted in submission order while their estimated
 // device memory fits the budget (one is always admitted when none is
 // running); a finished graph's model is freed at once, so the next request
@@ -22,7 +34,9 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <numeric>
@@ -40,10 +54,12 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// device bytes of a graph's model at its largest (sparse rows at B = N)
+// device bytes of a graph's model at its largest: sparse rows at B = N, or
+// the dense counts and prefix rows at the first dense B, min(N, dense_max_B)
 size_t model_bytes(const sbp_graph *g, int dense_max_B) {
     const size_t n = (size_t)g->n, m = (size_t)std::max<int64_t>(g->m, 1);
-    return 152 * m + 128 * n + 12 * (size_t)dense_max_B * (size_t)dense_max_B + (1u << 20);
+    const size_t bd = std::min(n, (size_t)dense_max_B);
+    return 152 * m + 128 * n + 12 * bd * bd + (1u << 20);
 }
 
 }  // namespace
@@ -53,7 +69,19 @@ struct Item {
     int32_t *b_out = nullptr;
     sbp_model *m = nullptr;
     PartitionRun run;
-    bool admitted = false, started = false, after_batch = false, finished = false;
+    bool admitted = false, started = false, finished = false;
+    // the persistent kernel it waits for: 1 to run the started phase's
+    // sweeps and the search after it, 2 the search from the planned phase on
+    int job = 0;
+    bool bounced = false;  // the kernel gave the search back without a phase
+    double t_ready = 0;    // when it last joined the persistent kernel's queue
+    // host-mapped search record and its four label slots (4 n), and their
+    // device view
+    unsigned char *xfer = nullptr, *xfer_dev = nullptr;
+    size_t xfer_bytes = 0;
+    SearchRec *rec() const { return reinterpret_cast<SearchRec *>(xfer); }
+    int32_t *slots() const { return reinterpret_cast<int32_t *>(xfer + kRecBytes); }
+    static constexpr size_t kRecBytes = (sizeof(SearchRec) + 255) / 256 * 256;
     int rc = SBP_OK;
     std::string msg;
     size_t bytes = 0;
@@ -89,6 +117,10 @@ struct Engine {
     // oldest request (the server: requests finish closer to arrival order,
     // which keeps the median latency down when the device is saturated)
     bool oldest_first = false;
+    // host-mapped label buffers, reused by size once their graph is done
+    std::mutex xfer_mu;
+    std::multimap<size_t, unsigned char *> xfer_free;
+    std::vector<unsigned char *> xfer_all;
 
     int init(const sbp_params &p, const BatchOptions &o, bool background);
     int64_t submit(const sbp_graph *g, int32_t *b_out);
@@ -99,7 +131,55 @@ struct Engine {
     void admit();  // under mu
     int work(Item &it, cudaStream_t s);
     void worker();
+    bool whole_phase_ok(const Item &it) const;
+    int ensure_xfer(Item &it);
+    void release_xfer(Item &it);
 };
+
+// the planned phase can run whole in the persistent kernel
+bool Engine::whole_phase_ok(const Item &it) const {
+    if (it.run.done) return false;
+    return batch_phase_eligible(it.m, it.run.start_state().B, it.run.target, opt.tune.max_B, opt.tune.max_n);
+}
+
+int Engine::ensure_xfer(Item &it) {
+    const size_t need = Item::kRecBytes + (size_t)std::max<int64_t>(it.g->n, 1) * 16;
+    if (it.xfer_bytes >= need) return SBP_OK;
+    release_xfer(it);
+    size_t cls = 4096;
+    while (cls < need) cls <<= 1;
+    unsigned char *h = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(xfer_mu);
+        auto f = xfer_free.find(cls);
+        if (f != xfer_free.end()) {
+            h = f->second;
+            xfer_free.erase(f);
+        }
+    }
+    if (!h) {
+        if (cudaHostAlloc((void **)&h, cls, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SBP_ENOMEM, "batch engine: mapped host memory for a search");
+        }
+        std::lock_guard<std::mutex> lk(xfer_mu);
+        xfer_all.push_back(h);
+    }
+    unsigned char *d = nullptr;
+    SBP_CUDA(cudaHostGetDevicePointer((void **)&d, h, 0));
+    it.xfer = h;
+    it.xfer_dev = d;
+    it.xfer_bytes = cls;
+    return SBP_OK;
+}
+
+void Engine::release_xfer(Item &it) {
+    if (!it.xfer) return;
+    std::lock_guard<std::mutex> lk(xfer_mu);
+    xfer_free.emplace(it.xfer_bytes, it.xfer);
+    it.xfer = it.xfer_dev = nullptr;
+    it.xfer_bytes = 0;
+}
 
 void Engine::admit() {
     while (next_admit < items.size()) {
@@ -166,12 +246,22 @@ int Engine::work(Item &it, cudaStream_t s) {
         r = sbp_build_blockmodel(it.g, (int32_t)it.g->n, ident.data(), &prm, s, &it.m);
         if (r == SBP_OK) r = it.run.begin(it.m);
         it.started = true;
-    } else if (it.after_batch) {
-        r = it.run.end_phase();
-        it.after_batch = false;
     }
     double t_merge = now_s() - tm, t_sweeps = 0.0;
-    while (r == SBP_OK && !it.run.done && !batch_eligible(it.m, opt.tune.max_B, opt.tune.max_n)) {
+    while (r == SBP_OK && !it.run.done) {
+        if (!it.bounced && whole_phase_ok(it)) {
+            it.job = 2;
+            break;
+        }
+        it.bounced = false;
+        tm = now_s();
+        r = it.run.start_phase();
+        t_merge += now_s() - tm;
+        if (r != SBP_OK) break;
+        if (batch_eligible(it.m, opt.tune.max_B, opt.tune.max_n)) {
+            it.job = 1;
+            break;
+        }
         tm = now_s();
         while (r == SBP_OK && !it.run.phase_over()) r = it.run.sweep();
         const double t1 = now_s();
@@ -180,10 +270,13 @@ int Engine::work(Item &it, cudaStream_t s) {
         t_merge += now_s() - t1;
         per_graph_phases.fetch_add(1, std::memory_order_relaxed);
     }
+    if (r == SBP_OK && it.job) r = ensure_xfer(it);
     if (r == SBP_OK && it.run.done) r = it.run.finish(it.b_out, &it.res.B, &it.res.dl, &it.res.n_sweeps);
     if (r != SBP_OK || it.run.done) {
         if (it.m) sbp_free_model(it.m);
         it.m = nullptr;
+        release_xfer(it);
+        it.job = 0;
         it.finished = true;
         it.res.t_done = now_s() - t0;
     }
@@ -200,9 +293,22 @@ void Engine::worker() {
     for (;;) {
         cv.wait(lk, [&]() { return aborting || (closing && running == 0) || !cpu_q.empty(); });
         if (aborting || (cpu_q.empty() && closing && running == 0)) return;
+        // first the short steps: graphs whose search has ended (their result
+        // is out and their memory freed at once) and graphs not yet set up
+        // whose searches the persistent kernel will take (the set-up hands
+        // the device work that overlaps the rest); then by the engine's order
+        auto rank = [&](int64_t i) {
+            const Item &c = *items[(size_t)i];
+            return (c.started && c.run.done) || (!c.started && c.g->n <= opt.tune.max_n) ? 0 : 1;
+        };
         size_t pick = 0;
         for (size_t q = 1; q < cpu_q.size(); ++q) {
             const int64_t a = cpu_q[q], b = cpu_q[pick];
+            const int ra = rank(a), rb = rank(b);
+            if (ra != rb) {
+                if (ra < rb) pick = q;
+                continue;
+            }
             if (oldest_first ? a < b : items[(size_t)a]->g->m > items[(size_t)b]->g->m) pick = q;
         }
         const int64_t idx = cpu_q[pick];
@@ -228,6 +334,7 @@ void Engine::worker() {
             used -= it.bytes;
             admit();
         } else {
+            it.t_ready = now_s();
             ready.push_back(idx);
         }
         cv.notify_all();
@@ -238,15 +345,16 @@ int Engine::loop() {
     struct Launch {
         cudaStream_t st = nullptr;
         cudaEvent_t ev = nullptr;
-        std::vector<int64_t> take;
+        std::vector<int64_t> take;  // its graphs not yet taken back
         double t0 = 0;
     };
-    const int kMaxInflight = 4;
+    // launches in flight at once: a launch runs its graphs' searches to the
+    // end (or to a phase it cannot take), so it stays in flight as long as
+    // its longest search
+    const int kMaxInflight = 16;
+    const double kMaxWait = 0.002;
     std::vector<Launch> pool((size_t)kMaxInflight);
     std::vector<int> free_slots, inflight;
-    int *h_k = nullptr;
-    double *h_dl = nullptr;
-    size_t cap = 0;  // entries of the mapped result arrays
     int rc = SBP_OK;
     auto engine_fail = [&](int code, const std::string &msg) {
         std::lock_guard<std::mutex> lk(mu);
@@ -265,104 +373,112 @@ int Engine::loop() {
             engine_fail(rc, "batch engine: stream or event creation failed");
         }
     }
-    // mapped result slots are indexed by graph; grown (when nothing is in
-    // flight) as graphs are submitted
-    auto ensure_cap = [&](size_t need) -> bool {
-        if (need <= cap) return true;
-        size_t c = std::max<size_t>(need, 2 * cap + 64);
-        int *nk = nullptr;
-        double *nd = nullptr;
-        if (cudaHostAlloc((void **)&nk, c * 4, cudaHostAllocMapped) != cudaSuccess ||
-            cudaHostAlloc((void **)&nd, c * 8, cudaHostAllocMapped) != cudaSuccess) {
-            cudaGetLastError();
-            if (nk) cudaFreeHost(nk);
-            return false;
-        }
-        if (h_k) cudaFreeHost(h_k);
-        if (h_dl) cudaFreeHost(h_dl);
-        h_k = nk;
-        h_dl = nd;
-        cap = c;
-        return true;
-    };
+    std::vector<Item *> ended;
     {
         std::unique_lock<std::mutex> lk(mu);
         while (rc == SBP_OK) {
-            cv.wait_for(lk, std::chrono::microseconds(500), [&]() {
-                return aborting || (closing && running == 0) || ready.size() >= full_batch ||
-                       (!ready.empty() && cpu_q.empty() && busy < W && !free_slots.empty());
-            });
+            // a launch is due when a GPU's worth of searches is ready, when
+            // the workers have nothing else to do, or when the oldest ready
+            // search has waited kMaxWait: searches start soon after they
+            // become batchable without a launch per search
+            auto due = [&]() {
+                if (ready.empty() || free_slots.empty()) return false;
+                if (ready.size() >= full_batch || (cpu_q.empty() && busy < W)) return true;
+                return now_s() - items[(size_t)ready.front()]->t_ready >= kMaxWait;
+            };
+            cv.wait_for(lk, std::chrono::microseconds(500),
+                        [&]() { return aborting || (closing && running == 0) || due(); });
             for (size_t q = 0; q < inflight.size();) {
                 Launch &L = pool[(size_t)inflight[q]];
                 const cudaError_t e = cudaEventQuery(L.ev);
-                if (e == cudaErrorNotReady) {
-                    ++q;
-                    continue;
-                }
-                if (e != cudaSuccess) {
+                if (e != cudaSuccess && e != cudaErrorNotReady) {
                     rc = cuda_fail(e, "persistent launch");
                     lk.unlock();
-                    engine_fail(rc, std::string("batched phase: ") + cudaGetErrorString(e));
+                    engine_fail(rc, std::string("batched search: ") + cudaGetErrorString(e));
                     lk.lock();
                     break;
                 }
-                st.s_batched += now_s() - L.t0;
+                const bool over = e == cudaSuccess;
+                // searches taken back: while the launch runs, the ended ones
+                // (their outcome is all in host-mapped memory, and their
+                // model is only freed after), once it is over, the rest
+                std::vector<int64_t> back, keep;
                 for (int64_t idx : L.take) {
                     Item &it = *items[(size_t)idx];
-                    it.run.after_sweeps(h_k[idx], h_dl[idx]);
-                    it.after_batch = true;
-                    cpu_q.push_back(idx);
+                    const int32_t ok = __atomic_load_n(&it.rec()->ok, __ATOMIC_ACQUIRE);
+                    if (over || (ok == 1 && it.rec()->done)) back.push_back(idx);
+                    else keep.push_back(idx);
                 }
-                L.take.clear();
-                free_slots.push_back(inflight[q]);
-                inflight.erase(inflight.begin() + (long)q);
+                L.take.swap(keep);
+                if (over) {
+                    st.s_batched += now_s() - L.t0;
+                    free_slots.push_back(inflight[q]);
+                    inflight.erase(inflight.begin() + (long)q);
+                } else {
+                    ++q;
+                }
+                if (back.empty()) continue;
+                // each search is taken back (the bracket's labels copied out of
+                // the mapped slots) and plans its next phase, outside the
+                // lock: these graphs are the launcher's until queued again
+                ended.clear();
+                for (int64_t idx : back) ended.push_back(items[(size_t)idx].get());
+                lk.unlock();
+                bool bad = false;
+                int64_t ph = 0, mg = 0, sts = 0;
+                for (Item *ip : ended) {
+                    Item &it = *ip;
+                    const SearchRec rec = *it.rec();
+                    if (rec.ok != 1) {
+                        bad = true;
+                        break;
+                    }
+                    it.run.import_search(rec, it.slots());
+                    it.bounced = rec.phases == 0;
+                    it.job = 0;
+                    ph += rec.phases;
+                    mg += rec.merged;
+                    sts += rec.starts;
+                }
+                if (bad) {
+                    rc = SBP_ESTATE;
+                    engine_fail(rc, "batched search: a phase did not fit the launch's bounds");
+                    lk.lock();
+                    break;
+                }
+                lk.lock();
+                st.phases_batched += ph;
+                st.merges_batched += mg;
+                st.starts_batched += sts;
+                for (int64_t idx : back) cpu_q.push_back(idx);
                 cv.notify_all();
             }
             if (aborting || rc != SBP_OK) break;
             if (closing && running == 0 && inflight.empty()) break;
-            const bool starving = cpu_q.empty() && busy < W;
-            if (ready.empty() || free_slots.empty() || (ready.size() < full_batch && !starving)) continue;
-            if (!ensure_cap(items.size())) {
-                if (!inflight.empty()) continue;  // grow once nothing reads the old slots
-                rc = SBP_ENOMEM;
-                lk.unlock();
-                engine_fail(rc, "batch engine: mapped host memory");
-                lk.lock();
-                break;
-            }
-            int *d_k = nullptr;
-            double *d_dl = nullptr;
-            if (cudaHostGetDevicePointer((void **)&d_k, h_k, 0) != cudaSuccess ||
-                cudaHostGetDevicePointer((void **)&d_dl, h_dl, 0) != cudaSuccess) {
-                rc = cuda_fail(cudaGetLastError(), "cudaHostGetDevicePointer");
-                lk.unlock();
-                engine_fail(rc, "batch engine: mapped host memory");
-                lk.lock();
-                break;
-            }
+            if (!due()) continue;
             const int slot = free_slots.back();
             free_slots.pop_back();
             Launch &L = pool[(size_t)slot];
             L.take.swap(ready);
             ready.clear();
             inflight.push_back(slot);
-            std::vector<sbp_model *> ms;
-            std::vector<uint64_t> s0;
-            std::vector<double> tt, h0;
-            std::vector<int *> kr;
-            std::vector<double *> dr;
-            for (int64_t idx : L.take) {
-                Item &it = *items[(size_t)idx];
-                ms.push_back(it.m);
-                s0.push_back(it.run.sweep_id);
-                tt.push_back(it.run.t);
-                h0.push_back(it.run.hist[0]);
-                kr.push_back(d_k + idx);
-                dr.push_back(d_dl + idx);
-            }
+            ended.clear();
+            for (int64_t idx : L.take) ended.push_back(items[(size_t)idx].get());
             lk.unlock();
+            // each graph's search goes to its mapped record and label slots
+            std::vector<BatchSpec> specs(L.take.size());
+            for (size_t u = 0; u < L.take.size(); ++u) {
+                Item &it = *ended[u];
+                it.run.export_search(*it.rec(), it.slots(), it.job == 1);
+                BatchSpec &sp = specs[u];
+                sp.m = it.m;
+                sp.rec = reinterpret_cast<SearchRec *>(it.xfer_dev);
+                sp.slots = reinterpret_cast<int32_t *>(it.xfer_dev + Item::kRecBytes);
+                sp.lim_from = batch_lim_from(it.m);
+                sp.started = it.job == 1 ? 1 : 0;
+            }
             L.t0 = now_s();
-            int r = batch_enqueue(ms, s0, tt, h0, kr, dr, opt.tune, L.st);
+            int r = batch_enqueue(specs, prm, opt.tune, L.st);
             if (r == SBP_OK && cudaEventRecord(L.ev, L.st) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "cudaEventRecord");
             std::string msg;
             if (r != SBP_OK) {
@@ -372,7 +488,6 @@ int Engine::loop() {
             }
             lk.lock();
             ++st.rounds;
-            st.phases_batched += (int64_t)L.take.size();
             if (r != SBP_OK) {
                 rc = r;
                 lk.unlock();
@@ -387,8 +502,6 @@ int Engine::loop() {
         if (L.ev) cudaEventDestroy(L.ev);
         if (L.st) cudaStreamDestroy(L.st);
     }
-    if (h_k) cudaFreeHost(h_k);
-    if (h_dl) cudaFreeHost(h_dl);
     return rc;
 }
 
@@ -407,11 +520,16 @@ void Engine::close_and_join() {
     for (auto &t : workers)
         if (t.joinable()) t.join();
     workers.clear();
-    for (auto &p : items)
+    for (auto &p : items) {
         if (p->m) {
             sbp_free_model(p->m);
             p->m = nullptr;
         }
+        release_xfer(*p);
+    }
+    for (unsigned char *h : xfer_all) cudaFreeHost(h);
+    xfer_all.clear();
+    xfer_free.clear();
     for (auto &s : streams)
         if (s) cudaStreamDestroy(s);
     streams.clear();
@@ -534,7 +652,6 @@ extern "C" int sbp_autotune_batch(const sbp_graph_t *const *graphs, int32_t coun
         std::vector<int32_t> values;
     };
     const Knob knobs[] = {
-        {&sbp_batch_options::workers, {8, 16, 32}},
         {&sbp_batch_options::movers_per_warp, {1, 2, 4}},
         {&sbp_batch_options::ctas_per_sm, {1, 2, 3, 4}},
         {&sbp_batch_options::max_B, {128, 256, 512, 1024}},

@@ -74,6 +74,25 @@ def test_batch_equals_plain(opts):
         assert 0.0 <= ta <= td
 
 
+def test_whole_phases_in_the_launch_match_the_oracle():
+    # graphs of at most 1024 vertices: every phase of the search, from the
+    # first merge at B = N on, runs whole in the persistent launch (start
+    # state, merge rounds, sweeps, compaction), including the phases that
+    # start from a bracket state the model no longer holds
+    gs, pgs = _graphs(12, 1000, seed=21)
+    params = P.Params.default(seed=6)
+    st = P.BatchStats()
+    out = P.partition_batch(pgs, params, P.BatchOptions.default(max_B=1024, max_n=1024), st)
+    ref = oracle_runs("n1000", gs, 6)
+    for pg, (b, B, dl, ns, ta, td), o in zip(pgs, out, ref):
+        assert_matches_oracle((b, B, dl, ns), o)
+        pb, pB, pdl, pns = _plain(pg, params)
+        assert B == pB and dl == pdl and ns == pns and np.array_equal(b, pb)
+    assert st.phases_per_graph == 0
+    assert st.merges_batched == st.phases_batched > 0
+    assert st.starts_batched > 0
+
+
 def test_batch_dense_switch_does_not_change_results():
     # the batch's dense/sparse switch is a schedule choice: the same graph
     # partitioned with dense rows up to 4096 or sparse rows above 64 agrees
