@@ -127,7 +127,8 @@ __device__ bool search_next(const SearchRec &r, double reduction, int &start, in
     return true;
 }
 
-// the label slot no bracket position uses
+// the label slot no bracket position uses (three positions, four slots: one
+// is always free)
 __device__ int search_free_slot(const SearchRec &r) {
     for (int f = 0; f < 4; ++f) {
         bool used = false;
