@@ -65,6 +65,10 @@ def test_served_results_equal_alone(opts):
         assert np.array_equal(b, pb)
         assert ts <= ta <= td
     assert st.phases_batched + st.phases_per_graph > 0
+    if not opts:
+        # with the default limits every request's search goes to the
+        # persistent kernel once it is down to B <= 1024, merges included
+        assert st.merges_batched > 0
 
 
 def test_server_poll_and_order():
