@@ -489,6 +489,51 @@ def run_partition(args):
     print(json.dumps(res))
 
 
+def forms_summary(args, batch_every=64):
+    """Small runs of the other forms, reported beside the sweep line: the
+    full runs (golden-ratio search from B = N) of the 1k and 200k plain
+    configurations, and every batch_every-th graph of the batching workload
+    partitioned by one batch call against one sbp_partition per graph."""
+    import torch
+
+    import paper_2305_18663_gb300 as P
+    from synth.dcsbm import batch_specs
+
+    out = {}
+    params = P.Params.default(seed=args.seed)
+    for name in ("plain_1k", "plain_200k"):
+        try:
+            g = make_config(name, seed=0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            graph = P.Graph(g.n, g.src, g.dst)
+            b, B, dl, sweeps = graph.partition(params)
+            out["full_run_" + name] = {"seconds": time.perf_counter() - t0, "n": g.n, "e": g.m, "B": B, "dl": dl,
+                                       "sweeps": sweeps, "nmi_vs_planted": nmi(b, g.planted),
+                                       "planted_B": CONFIGS[name]["n_blocks"], "graph_upload_included": True}
+        except Exception as e:  # reported, not fatal to the sweep line
+            out["full_run_" + name] = {"error": str(e)}
+    try:
+        specs = batch_specs(4096, seed=args.seed)[::batch_every]
+        graphs = [P.Graph(n, src, dst) for n, src, dst in gen_graphs(specs)]
+        bp = P.Params.default(seed=args.seed, dense_max_B=P.BatchOptions.default().dense_max_B)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = P.partition_batch(graphs, bp)
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        plain = [g.partition(bp) for g in graphs]
+        tp = time.perf_counter() - t0
+        equal = all(B == pB and dl == pdl and ns == pns and np.array_equal(b, pb)
+                    for (b, B, dl, ns, _, _), (pb, pB, pdl, pns) in zip(res, plain))
+        out["batch_sample"] = {"graphs": len(graphs), "of": 4096, "every": batch_every,
+                               "batched_graphs_per_s": len(graphs) / tb, "plain_graphs_per_s": len(graphs) / tp,
+                               "results_equal": equal, "options": "defaults"}
+    except Exception as e:
+        out["batch_sample"] = {"error": str(e)}
+    return out
+
+
 def _gen(spec):
     from synth.dcsbm import dcsbm
 
@@ -661,6 +706,8 @@ def main():
     ap.add_argument("--clock-window", type=float, default=2.0,
                     help="seconds of replayed sweeps (same chain, same start) the clock sampler also covers")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the small full-run and batch runs reported under 'forms'")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "partition", "batch", "serve"])
     ap.add_argument("--serve-count", type=int, default=24)
     ap.add_argument("--serve-n-hi", type=int, default=2_000_000)
@@ -718,6 +765,8 @@ def main():
         dist.init_process_group("nccl")
     res = run_ours(args, rank, world, local_rank)
     if rank == 0:
+        if world == 1 and not args.no_forms:
+            res["forms"] = forms_summary(args)
         if not args.no_cpu_baseline:
             cb, _, _ = run_cpu_oracle(args, args.config, args.scale, steps=args.oracle_sweeps, B=args.B)
             res["cpu_baseline"] = cb
