@@ -258,7 +258,7 @@ __device__ void cta_relabel(int32_t *b, int32_t *bnew, int n, const int *map) {
 // blk_cap: a power of two >= every job's lim_from (the merge rounds' and the
 // compaction's shared arrays)
 template <bool DL32, int G>
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_mcmc(const BatchJob *__restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_search(const BatchJob *__restrict__ jobs, int njobs,
                                                                   unsigned *__restrict__ queue, int group_words,
                                                                   int blk_cap) {
     extern __shared__ __align__(16) unsigned char bsm[];
@@ -734,11 +734,11 @@ int batch_enqueue(const std::vector<BatchSpec> &specs, const sbp_params &p, cons
         return SBP_OK;
     };
     if (p.dl_fp32) {
-        SBP_TRY(V == 4 ? launch(k_batch_mcmc<true, 8>) : V == 2 ? launch(k_batch_mcmc<true, 16>)
-                                                          : launch(k_batch_mcmc<true, 32>));
+        SBP_TRY(V == 4 ? launch(k_batch_search<true, 8>) : V == 2 ? launch(k_batch_search<true, 16>)
+                                                          : launch(k_batch_search<true, 32>));
     } else {
-        SBP_TRY(V == 4 ? launch(k_batch_mcmc<false, 8>) : V == 2 ? launch(k_batch_mcmc<false, 16>)
-                                                           : launch(k_batch_mcmc<false, 32>));
+        SBP_TRY(V == 4 ? launch(k_batch_search<false, 8>) : V == 2 ? launch(k_batch_search<false, 16>)
+                                                           : launch(k_batch_search<false, 32>));
     }
     SBP_CUDA(cudaFreeAsync(buf, st));
     return SBP_OK;
