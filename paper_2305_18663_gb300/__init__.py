@@ -26,7 +26,8 @@ __all__ = [
     "sbp_nodal_sweep", "sbp_nodal_decide", "sbp_commit", "sbp_merge_proposals", "sbp_merge_blocks",
     "sbp_compact", "sbp_partition", "sbp_get_assignment", "sbp_get_pending", "sbp_set_pending", "sbp_get_B", "sbp_get_dl",
     "sbp_get_blockmodel_dense", "sbp_get_degrees", "sbp_get_blockmodel_coo", "sbp_sync", "sbp_free_model", "sbp_philox_check",
-    "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_dxlogx32_check", "sbp_default_batch_options", "sbp_partition_batch",
+    "sbp_dense_dl_noalloc", "sbp_kernel_launches", "sbp_dxlogx32_check", "sbp_bracket_check",
+    "sbp_default_batch_options", "sbp_partition_batch",
     "BatchOptions", "BatchResult", "BatchStats", "partition_batch", "Server", "sbp_autotune_batch", "autotune_batch",
     "sbp_server_create", "sbp_server_submit", "sbp_server_poll", "sbp_server_wait", "sbp_server_stats",
     "sbp_server_destroy",
@@ -181,6 +182,7 @@ def load(path: str | None = None):
         "sbp_philox_check": (C.c_int, [u64, u64, u64, u64, u64, u64, i32, vp]),
         "sbp_dense_dl_noalloc": (C.c_int, [vp, i32, vp, vp, i64, i64, vp, vp]),
         "sbp_kernel_launches": (C.c_int, [P(u64)]),
+        "sbp_bracket_check": (C.c_int, [vp, vp, i32, C.c_double, vp, P(i32)]),
         "sbp_default_batch_options": (C.c_int, [P(BatchOptions)]),
         "sbp_dxlogx32_check": (C.c_int, [vp, vp, i32, vp, vp]),
         "sbp_partition_batch": (C.c_int, [vp, i32, P(Params), P(BatchOptions), vp, P(BatchResult), P(BatchStats)]),
@@ -405,6 +407,20 @@ def sbp_dxlogx32_check(x, k):
     am = np.zeros(x.size, np.float32)
     _check(lib().sbp_dxlogx32_check(x.ctypes.data, k.ctypes.data, int(x.size), val.ctypes.data, am.ctypes.data))
     return val, am
+
+
+def sbp_bracket_check(B, dl, reduction: float = 0.5):
+    """(out, n_bad): the persistent kernel's bracket code, run on the host,
+    against the host driver's bracket over the states (B[i], dl[i]) inserted
+    in order; out has 12 entries per state (host: position B values, next
+    phase exists, start, target; then the same from the kernel's code)."""
+    B = np.ascontiguousarray(B, np.int32)
+    dl = np.ascontiguousarray(dl, np.float64)
+    out = np.zeros((B.size, 12), np.int32)
+    bad = C.c_int32(0)
+    _check(lib().sbp_bracket_check(B.ctypes.data, dl.ctypes.data, int(B.size), float(reduction), out.ctypes.data,
+                                   C.byref(bad)))
+    return out, int(bad.value)
 
 
 def sbp_kernel_launches() -> int:

@@ -81,7 +81,7 @@ struct BatchJob {
 
 // Bracket::insert on the kernel's copy of the bracket (positions move with
 // their label slots)
-__device__ void search_insert(SearchRec &r, const SearchState &x) {
+__host__ __device__ void search_insert(SearchRec &r, const SearchState &x) {
     if (r.s[1].B == 0) {
         r.s[1] = x;
         return;
@@ -98,7 +98,7 @@ __device__ void search_insert(SearchRec &r, const SearchState &x) {
 
 // Bracket::next on the kernel's copy: the next phase's start position and
 // target, false when the search has ended
-__device__ bool search_next(const SearchRec &r, double reduction, int &start, int &target) {
+__host__ __device__ bool search_next(const SearchRec &r, double reduction, int &start, int &target) {
     const SearchState *s = r.s;
     if (s[2].B == 0) {
         int64_t nm = (int64_t)floor((double)s[1].B * reduction);
@@ -129,7 +129,7 @@ __device__ bool search_next(const SearchRec &r, double reduction, int &start, in
 
 // the label slot no bracket position uses (three positions, four slots: one
 // is always free)
-__device__ int search_free_slot(const SearchRec &r) {
+__host__ __device__ int search_free_slot(const SearchRec &r) {
     for (int f = 0; f < 4; ++f) {
         bool used = false;
         for (int p = 0; p < 3; ++p) used |= r.s[p].B != 0 && r.s[p].slot == f;
@@ -745,6 +745,61 @@ int batch_enqueue(const std::vector<BatchSpec> &specs, const sbp_params &p, cons
 }
 
 }  // namespace sbp
+
+// The kernel's bracket code (run here on the host) against Bracket: states
+// (B[i], dl[i]) inserted in order into both; after each insert, out[12 i ..]
+// holds Bracket's position B values, next()'s result, start and target, then
+// the same six from the kernel's code.  *n_bad counts the steps where they
+// differ, or where the positions' ids or label slots disagree.
+extern "C" int sbp_bracket_check(const int32_t *B, const double *dl, int32_t count, double reduction, int32_t *out,
+                                 int32_t *n_bad) {
+    if (count < 0 || !n_bad || (count > 0 && (!B || !dl || !out)))
+        return sbp::fail(SBP_EINVAL, "sbp_bracket_check: bad count or NULL array");
+    if (!(reduction > 0 && reduction < 1)) return sbp::fail(SBP_EINVAL, "sbp_bracket_check: reduction must be in (0, 1)");
+    sbp::Bracket hb;
+    sbp::SearchRec dr;
+    int32_t bad = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (B[i] < 1) return sbp::fail(SBP_EINVAL, "sbp_bracket_check: B must be >= 1");
+        sbp::State x;
+        x.B = B[i];
+        x.dl = dl[i];
+        x.id = (uint64_t)i + 1;
+        hb.insert(std::move(x));
+        sbp::SearchState y;
+        y.B = B[i];
+        y.dl = dl[i];
+        y.id = (uint64_t)i + 1;
+        y.slot = sbp::search_free_slot(dr);
+        sbp::search_insert(dr, y);
+        int hs = 0, ds = 0;
+        int32_t ht = 0;
+        int dt = 0;
+        const bool hok = hb.next(reduction, hs, ht);
+        const bool dok = sbp::search_next(dr, reduction, ds, dt);
+        int32_t *o = out + (size_t)i * 12;
+        bool same = hok == dok && (!hok || (hs == ds && ht == dt)) && y.slot >= 0;
+        bool used[4] = {false, false, false, false};
+        for (int p = 0; p < 3; ++p) {
+            o[p] = hb.s[p].B;
+            o[6 + p] = dr.s[p].B;
+            same = same && hb.s[p].B == dr.s[p].B && (hb.s[p].B == 0 || hb.s[p].id == dr.s[p].id);
+            if (dr.s[p].B != 0) {
+                same = same && dr.s[p].slot >= 0 && dr.s[p].slot < 4 && !used[dr.s[p].slot];
+                if (dr.s[p].slot >= 0 && dr.s[p].slot < 4) used[dr.s[p].slot] = true;
+            }
+        }
+        o[3] = hok ? 1 : 0;
+        o[4] = hok ? hs : 0;
+        o[5] = hok ? ht : 0;
+        o[9] = dok ? 1 : 0;
+        o[10] = dok ? ds : 0;
+        o[11] = dok ? dt : 0;
+        if (!same) ++bad;
+    }
+    *n_bad = bad;
+    return SBP_OK;
+}
 
 extern "C" int sbp_default_batch_options(sbp_batch_options *o) {
     if (!o) return sbp::fail(SBP_EINVAL, "sbp_default_batch_options: NULL");

@@ -78,3 +78,58 @@ def test_binding_signatures_match_the_header():
         fn = getattr(lib, name)
         assert fn.argtypes is not None, name
         assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+
+
+def _search_like_sequence(rng, n0, reduction=0.5):
+    """States in the order a golden-ratio search visits them: the next B
+    from the host bracket's own plan (read back after each insert), DL a
+    noisy convex function of B with its minimum at a random block count."""
+    import numpy as np
+
+    import paper_2305_18663_gb300 as P
+
+    best = int(rng.integers(2, max(3, n0 // 4)))
+    Bs, dls = [n0], [1e6 * (1 + (np.log(n0) - np.log(best)) ** 2)]
+    for _ in range(60):
+        out, bad = P.sbp_bracket_check(Bs, dls, reduction)
+        assert bad == 0
+        if not out[-1, 3]:
+            break
+        B = int(out[-1, 5])
+        Bs.append(B)
+        dls.append(1e6 * (1 + (np.log(B) - np.log(best)) ** 2) + rng.normal(0, 1e3))
+    return Bs, dls
+
+
+def test_kernel_bracket_follows_the_host_bracket():
+    # the persistent kernel's copy of the golden-ratio bracket (compiled for
+    # the host as well) against the host driver's Bracket: the same positions
+    # and ids after every insert, the same next phase (start and target), and
+    # label slots that never collide; on search-like sequences, on random
+    # ones, and with equal DL values (ties go to the same side)
+    import numpy as np
+
+    import paper_2305_18663_gb300 as P
+
+    rng = np.random.default_rng(7)
+    for trial in range(200):
+        n0 = int(rng.integers(2, 5000))
+        red = float(rng.choice([0.5, 0.3, 0.7]))
+        Bs, dls = _search_like_sequence(rng, n0, red)
+        out, bad = P.sbp_bracket_check(Bs, dls, red)
+        assert bad == 0, (trial, Bs)
+        assert np.array_equal(out[:, :6], out[:, 6:])
+        # the search ends: the last plan says no next phase, or the bracket
+        # is down to adjacent block counts
+        assert not out[-1, 3] or len(Bs) == 61
+    for trial in range(200):
+        k = int(rng.integers(1, 30))
+        Bs = rng.integers(1, 3000, k)
+        dls = rng.choice([1.0, 2.0, 3.0], k) if trial % 2 else rng.normal(1e6, 1e4, k)
+        out, bad = P.sbp_bracket_check(Bs, dls, 0.5)
+        assert bad == 0, trial
+    # first insert of B = N with reduction 0.5: merge to ceil(N / 2)
+    out, bad = P.sbp_bracket_check([1000], [5.0], 0.5)
+    assert bad == 0 and out[0, 3] == 1 and out[0, 4] == 1 and out[0, 5] == 500
+    out, bad = P.sbp_bracket_check([1], [5.0], 0.5)
+    assert bad == 0 and out[0, 3] == 0  # one block: nothing left to merge
