@@ -104,9 +104,6 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-cudaMemcpyKind kind_to_dev(const void *src) {
-    return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-}
 cudaMemcpyKind kind_from_dev(const void *dst) {
     return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
