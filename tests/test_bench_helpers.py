@@ -1,6 +1,9 @@
 """Host-side helpers of bench.py (no GPU): the code hash that keys the
 committed DRAM-traffic figure to the kernels it was measured on, and the
-algorithmic-bytes formula of the roofline."""
+algorithmic-bytes formula of the roofline, and the NMI of the full-run
+reports."""
+import pytest
+
 import bench
 
 
@@ -36,3 +39,24 @@ def test_algorithmic_bytes_formula():
     dec_s, streamed_s, _ = bench.algorithmic_bytes(n, m, B, me, ent, sparse=True, nnz=40)
     assert streamed_s == streamed
     assert dec_s == streamed + 4 * 3 * n + ent * (4 * 8 + 8)  # rows and columns of 8 entries on average
+
+
+def test_nmi_of_the_full_run_reports():
+    # the NMI the full-run lines report: 1 for the same partition under any
+    # relabelling, near 0 for independent labels, symmetric, and equal to
+    # the textbook value on a small hand-worked case
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 8, 5000)
+    perm = rng.permutation(8)
+    assert bench.nmi(a, perm[a]) == pytest.approx(1.0, abs=1e-12)
+    b = rng.integers(0, 8, 5000)
+    assert bench.nmi(a, b) < 0.01
+    assert bench.nmi(a, b) == pytest.approx(bench.nmi(b, a), abs=1e-12)
+    # a = [0,0,1,1], b = [0,0,0,1]: H(a) = ln 2, H(b) = H(1/4), I = H(b) - H(b|a)
+    h = lambda p: -sum(x * np.log(x) for x in p if x > 0)  # noqa: E731
+    hb = h([0.75, 0.25])
+    mi = hb - 0.5 * h([0.5, 0.5])
+    assert bench.nmi([0, 0, 1, 1], [0, 0, 0, 1]) == pytest.approx(2 * mi / (np.log(2) + hb), rel=1e-12)
+    assert bench.nmi([3, 3, 3], [1, 1, 1]) == 1.0  # one block on both sides
