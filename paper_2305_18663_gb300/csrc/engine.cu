@@ -101,7 +101,7 @@ struct Engine {
     std::deque<std::unique_ptr<Item>> items;
     size_t next_admit = 0;          // first graph not yet admitted
     std::vector<int64_t> cpu_q;     // graphs needing per-graph work
-    std::vector<int64_t> ready;     // graphs waiting for a batched MCMC phase
+    std::vector<int64_t> ready;     // graphs whose search waits for a persistent launch
     int busy = 0;
     int64_t running = 0;            // admitted, not finished
     size_t used = 0;
@@ -117,7 +117,8 @@ struct Engine {
     // oldest request (the server: requests finish closer to arrival order,
     // which keeps the median latency down when the device is saturated)
     bool oldest_first = false;
-    // host-mapped label buffers, reused by size once their graph is done
+    // host-mapped search records with their label slots, reused by size once
+    // their graph is done
     std::mutex xfer_mu;
     std::multimap<size_t, unsigned char *> xfer_free;
     std::vector<unsigned char *> xfer_all;
