@@ -329,7 +329,8 @@ typedef struct sbp_batch_result {
 /* Where a batch call spent its time: rounds: persistent launches;
  * s_per_graph: worker-seconds of per-graph work (summed over the workers),
  * of which s_merge in set-up, merge phases and compaction and s_sweeps in
- * per-graph MCMC sweeps; s_batched: wall seconds of the persistent launches;
+ * per-graph MCMC sweeps; s_batched: wall seconds of the persistent launches,
+ * summed over launches (up to 16 are in flight at once);
  * phases_batched: phases run in the persistent launches, of which
  * merges_batched with their merge phase (the others had theirs run per
  * graph) and starts_batched from a search state the model no longer held;
