@@ -408,17 +408,6 @@ void sbp_server_destroy(sbp_server_t *s);
  * 0 <= x + k < 2^31. */
 int sbp_dxlogx32_check(const int32_t *x, const int32_t *k, int32_t count, float *val, float *am);
 
-/* The persistent kernel's copy of the golden-ratio bracket (run on the
- * host) against the host driver's: the states (B[i] >= 1, dl[i]) are
- * inserted in order into both; after each insert, out[12 i + 0..5] holds the
- * host bracket's three position B values (0: empty), whether a next phase
- * exists, its start position and target, and out[12 i + 6..11] the same
- * from the kernel's copy (host arrays, count * 12 entries).  *n_bad counts
- * the steps where the two differ or the kernel's label slots collide.  No
- * device is needed.  reduction: (0, 1), as in sbp_params. */
-int sbp_bracket_check(const int32_t *B, const double *dl, int32_t count, double reduction, int32_t *out,
-                      int32_t *n_bad);
-
 /* Number of kernel launches the library has issued in this process, over
  * all handles and devices (a host-side counter, incremented as each launch
  * is enqueued, whether or not the kernel then finds work to do).  For

@@ -42,6 +42,7 @@
 #include <vector>
 
 #include "apply.cuh"
+#include "sbp_check.h"
 #include "batch.h"
 #include "driver.h"
 #include "merge_dev.cuh"
